@@ -1,0 +1,205 @@
+/*
+ * exactmap.h -- C ABI of the GB300 (sm_103a) library for the pseudo-particle
+ * Exact mapping of Lau, Petkova & Bonnell (2024), "Hybrid radiation
+ * hydrodynamics scheme with adaptive gravity-tree-based pseudo-particles".
+ *
+ * The pipeline the paper describes (Section 2.3, flowchart of the code
+ * overview): build the gravity tree, walk it to select pseudo-particles and
+ * solve their smoothing lengths, build the Voronoi grid on the generation
+ * sites, map the (pseudo-)particle density onto the grid with the Exact
+ * mapping, and map per-cell results back onto the particles.
+ *
+ * Conventions (every entry point):
+ *   - returns an int status (EM_OK = 0 on success, see em_status); no call
+ *     aborts, traps the device or throws; em_last_error() returns a message
+ *     for the calling thread's last failure.
+ *   - arrays named "d_*" are DEVICE pointers on the context's device; arrays
+ *     named "h_*" are HOST pointers.  Doubles are IEEE FP64.
+ *   - the caller owns every array it passes.  Opaque handles (em_tree,
+ *     em_pseudo, em_voronoi, em_pairs) own the device memory the library
+ *     allocates for them; release it with the matching *_destroy call.
+ *   - all GPU work is enqueued on the context's stream.  Calls whose output
+ *     size is data dependent (tree, pseudo-particles, cells, pairs) synchronise
+ *     that stream once to read the size; the others do not synchronise.
+ *   - results are deterministic: the same inputs give bit-identical outputs.
+ *   - indices are 0-based.  Particle and cell counts must be < 2^31.
+ */
+#ifndef EXACTMAP_H
+#define EXACTMAP_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    EM_OK = 0,
+    EM_EINVAL = 1,      /* bad argument (null pointer, size out of range) */
+    EM_ENOMEM = 2,      /* device allocation failed */
+    EM_ECUDA = 3,       /* a CUDA runtime call failed */
+    EM_ECAPACITY = 4,   /* a fixed per-item capacity was exceeded; see message */
+    EM_ENOTCONV = 5,    /* informational: some h-solves fell back (per-item status set) */
+    EM_ETIMEOUT = 6     /* a bounded device loop ran out of iterations */
+} em_status;
+
+typedef struct em_ctx em_ctx;
+typedef struct em_tree em_tree;
+typedef struct em_pseudo em_pseudo;
+typedef struct em_voronoi em_voronoi;
+typedef struct em_pairs em_pairs;
+
+/* Parameters of the method.  em_params_default() fills the values used in
+ * the paper's tests where it gives them. */
+typedef struct {
+    double r_part;          /* radius around a source inside which leaves are replaced by their particles (Section 2.4.1) */
+    double r_leaf;          /* radius inside which nodes are opened down to leaves (Section 2.4.1) */
+    double theta;           /* opening angle: a node is opened if theta^2 < (s_node / r_node)^2 (Eq. 4) */
+    double h_fact;          /* h = h_fact n^(-1/3) (Eq. 6); default 1.2 */
+    double h_tol;           /* Newton stopping tolerance |dh| / h_0 (Section 2.4.2); paper 1e-2, parity 1e-13 */
+    int max_newton;         /* Newton iterations before bisection; default 50 */
+    int precision;          /* map_exact arithmetic: 0 = FP64, 1 = mixed FP32 with FP64 recompute of flagged pairs */
+    double fp64_threshold;  /* mixed mode: recompute a pair in FP64 when its estimated FP32 relative error exceeds this */
+    int knn_k;              /* build_voronoi: neighbours staged per generator before the exact fallback; default 48 */
+    int leaf_max;           /* build_tree: particles per leaf; default 8 */
+    int block_pairs;        /* map_exact launch shape: threads per block (0 = default) */
+    int reserved[5];
+} em_params;
+
+void em_params_default(em_params *p);
+
+/* ---- context ------------------------------------------------------------ */
+
+/* Create a context on `device` that enqueues all work on `stream` (a
+ * cudaStream_t; NULL = the legacy default stream). */
+int em_ctx_create(em_ctx **ctx, int device, void *stream);
+int em_ctx_destroy(em_ctx *ctx);
+/* Block until all work enqueued on the context's stream has finished. */
+int em_ctx_sync(em_ctx *ctx);
+/* Message of the calling thread's last failed call ("" if none). */
+const char *em_last_error(void);
+/* Number of kernels the library has launched through this context so far. */
+int64_t em_ctx_launch_count(const em_ctx *ctx);
+
+/* ---- build_tree ------------------------------------------------------------
+ * Morton-ordered octree of n particles (the paper's gravity tree, Section
+ * 2.2.1, with an octree in place of the k-d tree; the method is independent
+ * of the tree type, Section 2.4.1).
+ *   d_x, d_y, d_z, d_m: n particle positions and masses (device)
+ *   h_box: [xlo, xhi, ylo, yhi, zlo, zhi] (host); keys quantise 21 bits per axis
+ *   leaf_max: split nodes holding more than this many particles (<= 64)
+ * Node mass, centre of mass (position of the node) and size s_node =
+ * largest distance from the COM to a constituent (Section 2.2.1).  Node
+ * labels: root 1, child = 8 * parent + octant, so the ancestor k levels up is
+ * label >> 3k (the octree form of the label arithmetic of Section 2.2.1).
+ * Nodes are numbered breadth first (level, then key). */
+int build_tree(em_ctx *ctx, int64_t n, const double *d_x, const double *d_y, const double *d_z,
+               const double *d_m, const double *h_box, int leaf_max, em_tree **out);
+int tree_info(const em_tree *t, int64_t *n_particles, int64_t *n_nodes, int32_t *depth);
+/* Copy node arrays into caller device buffers (any pointer may be NULL):
+ * d_perm[n]: original index of the k-th particle in Morton order;
+ * per node: label (uint64), level, parent, first, count, first_child, nchild
+ * (int32), mass, size (double), com (3 doubles per node, xyz interleaved). */
+int tree_get(em_ctx *ctx, const em_tree *t, int32_t *d_perm, uint64_t *d_label, int32_t *d_level,
+             int32_t *d_parent, int32_t *d_first, int32_t *d_count, int32_t *d_first_child,
+             int32_t *d_nchild, double *d_mass, double *d_com, double *d_size);
+int tree_destroy(em_tree *t);
+
+/* ---- make_pseudo_particles ------------------------------------------------
+ * Adaptive tree-walk (Section 2.4.1): leaves whose COM is within r_part of
+ * the nearest source are replaced by their particles (which keep their own
+ * h); nodes within r_leaf are opened down to leaves; beyond, a node is
+ * opened when theta^2 < (s/r)^2 (Eq. 4).  Then node neighbour-finding
+ * (Section 2.4.3) and the node smoothing-length solver (Section 2.4.2,
+ * Eqs. 6-11): Newton from h_0 = 2 h_fact s_node, bisection on
+ * [1e-2 h_0, 1e2 h_0], else h_0.  Particles inside r_part are represented by
+ * their leaves in the solver's neighbour sums (Section 2.4.2).
+ *   d_h_particle: n particle smoothing lengths (device, original order)
+ *   h_src: nsrc source positions (host, xyz interleaved), nsrc >= 1
+ * Pseudo-particles are ordered by their first constituent in Morton order.
+ * Returns EM_ENOTCONV (with outputs valid) when some solve fell back to h_0. */
+int make_pseudo_particles(em_ctx *ctx, const em_tree *t, const double *d_h_particle, int nsrc,
+                          const double *h_src, const em_params *p, em_pseudo **out);
+/* n_pseudo; n_status[4]: counts of solver status 0 Newton, 1 bisection,
+ * 2 fallback h_0, 3 individual particle (may be NULL). */
+int pseudo_info(const em_pseudo *ps, int64_t *n_pseudo, int64_t *n_status);
+/* Copy out (device buffers, any may be NULL): positions (COM or particle),
+ * h, mass, origin (node label > 0, or -(particle index + 1)), Morton range
+ * [first, first + count) of constituents, solver status. */
+int pseudo_get(em_ctx *ctx, const em_pseudo *ps, double *d_x, double *d_y, double *d_z, double *d_h,
+               double *d_m, int64_t *d_origin, int32_t *d_first, int32_t *d_count, int32_t *d_status);
+int pseudo_destroy(em_pseudo *ps);
+
+/* ---- build_voronoi ---------------------------------------------------------
+ * Voronoi cells of ngen generation sites clipped to the box (the grid of
+ * Section 2.3).  Each cell is the box clipped by bisector half-spaces of its
+ * neighbours, staged as a bounded k-nearest list, then completed exactly by a
+ * tree search for any generator closer than twice the cell's radius.
+ *   d_gx, d_gy, d_gz: generator positions (device); h_box as in build_tree.
+ * Coincident generators are rejected with EM_EINVAL. */
+int build_voronoi(em_ctx *ctx, int64_t ngen, const double *d_gx, const double *d_gy, const double *d_gz,
+                  const double *h_box, const em_params *p, em_voronoi **out);
+/* Import cells given as faces (e.g. from another grid code):
+ *   d_gen: ncell generator positions (xyz interleaved)
+ *   d_cell_face_off[ncell+1], d_face_vert_off[nface+1] (int64 CSR offsets)
+ *   d_verts: 3 doubles per face vertex, counter-clockwise seen from outside
+ *   d_normals: 3 doubles per face (unit, outward); d_nbr: neighbour cell or < 0
+ *   d_volume: ncell volumes. */
+int voronoi_from_cells(em_ctx *ctx, int64_t ncell, int64_t nface, int64_t nfv, const double *d_gen,
+                       const int64_t *d_cell_face_off, const int64_t *d_face_vert_off,
+                       const double *d_verts, const double *d_normals, const int64_t *d_nbr,
+                       const double *d_volume, em_voronoi **out);
+int voronoi_info(const em_voronoi *v, int64_t *ncell, int64_t *nface, int64_t *nfv);
+/* Copy out in the same layout as voronoi_from_cells (any may be NULL). */
+int voronoi_get(em_ctx *ctx, const em_voronoi *v, int64_t *d_cell_face_off, int64_t *d_face_vert_off,
+                double *d_verts, double *d_normals, int64_t *d_nbr, double *d_volume);
+int voronoi_destroy(em_voronoi *v);
+
+/* ---- find_pairs --------------------------------------------------------------
+ * All particle-cell pairs whose kernel support meets the cell:
+ * dist(x_i, V_j) < 2 h_i (the "particle-cell pairs" whose number sets the
+ * mapping cost, Section 1).  Pairs are sorted by (cell j, particle i).
+ *   d_x, d_y, d_z, d_h: np (pseudo-)particles (device). */
+int find_pairs(em_ctx *ctx, int64_t np, const double *d_x, const double *d_y, const double *d_z,
+               const double *d_h, const em_voronoi *v, em_pairs **out, int64_t *npairs);
+/* Import a pair list sorted by (j, i) (device int32 arrays). */
+int pairs_from_list(em_ctx *ctx, int64_t npairs, const int32_t *d_pair_i, const int32_t *d_pair_j,
+                    int64_t np, const em_voronoi *v, em_pairs **out);
+int pairs_info(const em_pairs *pr, int64_t *npairs, int64_t *np, int64_t *ncell);
+/* Copy out: pair_i, pair_j (int32, sorted by (j, i)), d_near (uint8: 1 when
+ * |dist - 2h| < 1e-9 h), d_cell_pair_off[ncell + 1] (int64). */
+int pairs_get(em_ctx *ctx, const em_pairs *pr, int32_t *d_pair_i, int32_t *d_pair_j, uint8_t *d_near,
+              int64_t *d_cell_pair_off);
+int pairs_destroy(em_pairs *pr);
+
+/* ---- map_exact ---------------------------------------------------------------
+ * Exact mapping (Section 1 and 2.3): for every pair,
+ *   w_ij = int_{V_j} W(|r - x_i|, h_i) d^3r
+ * with the M4 cubic spline truncated at 2h (Section 2.4.2), integrated
+ * analytically by the signed decomposition of the cell into face pyramids
+ * and right sub-triangles; then
+ *   rho_j = sum_i m_i w_ij / V_j   (deterministic, ascending i)
+ *   u_i   = sum_j w_ij             (partition-of-unity check, ascending j).
+ *   d_w_out[npairs], d_rho_out[ncell] (device); d_wsum_out[np] may be NULL.
+ *   p->precision: 0 FP64; 1 FP32 bulk with compensated sums, pairs whose
+ *   estimated error exceeds p->fp64_threshold recomputed in FP64.
+ *   h_nfp64 (host, may be NULL): number of pairs recomputed in FP64. */
+int map_exact(em_ctx *ctx, const em_pairs *pr, const double *d_x, const double *d_y, const double *d_z,
+              const double *d_h, const double *d_m, const em_voronoi *v, const em_params *p,
+              double *d_w_out, double *d_rho_out, double *d_wsum_out, int64_t *h_nfp64);
+
+/* ---- map_back -------------------------------------------------------------------
+ * Inverse mapping of a per-cell field onto the (pseudo-)particles
+ * (Section 2.3): f_i = sum_j w_ij f_j / sum_j w_ij (NaN when particle i has
+ * no pair); with a pseudo-particle set and its tree, every SPH particle then
+ * inherits the value of the pseudo-particle it belongs to (Section 2.5).
+ *   d_f_cell[ncell], d_f_out[np] (device)
+ *   ps, t, d_f_particle_out[n particles, original order]: all NULL, or all set. */
+int map_back(em_ctx *ctx, const em_pairs *pr, const double *d_w, const double *d_f_cell, double *d_f_out,
+             const em_pseudo *ps, const em_tree *t, double *d_f_particle_out);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* EXACTMAP_H */

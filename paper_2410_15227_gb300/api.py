@@ -1,0 +1,287 @@
+"""Python binding of the C ABI, with the same call names.
+
+PyTorch supplies device memory and the CUDA stream; every computation runs in
+``libexactmap.so``.  Inputs are CUDA tensors (float64 for coordinates,
+masses, smoothing lengths; int32 for pair indices); outputs are new CUDA
+tensors allocated by torch.
+"""
+from __future__ import annotations
+
+import ctypes as C
+from dataclasses import dataclass, fields
+
+import torch
+
+from . import _native as N
+
+
+@dataclass
+class Params:
+    """Method parameters (see em_params in include/exactmap.h)."""
+    r_part: float = 0.05
+    r_leaf: float = 0.1
+    theta: float = 0.1
+    h_fact: float = 1.2
+    h_tol: float = 1e-13
+    max_newton: int = 50
+    precision: int = 0            # 0 FP64, 1 mixed FP32 / FP64
+    fp64_threshold: float = 1e-5
+    knn_k: int = 48
+    leaf_max: int = 8
+    block_pairs: int = 0
+
+    def native(self) -> N.EmParams:
+        p = N.EmParams()
+        for f in fields(self):
+            setattr(p, f.name, getattr(self, f.name))
+        return p
+
+
+def _ptr(t: torch.Tensor | None, dtype=None, n=None, name="tensor"):
+    if t is None:
+        return None
+    if not t.is_cuda:
+        raise ValueError(f"{name} must be a CUDA tensor")
+    if dtype is not None and t.dtype != dtype:
+        raise TypeError(f"{name} must be {dtype}, got {t.dtype}")
+    if not t.is_contiguous():
+        raise ValueError(f"{name} must be contiguous")
+    if n is not None and t.numel() != n:
+        raise ValueError(f"{name} must have {n} elements, got {t.numel()}")
+    return C.c_void_p(t.data_ptr())
+
+
+def _box(box):
+    b = (C.c_double * 6)(*[float(v) for v in box])
+    return C.cast(b, C.c_void_p), b
+
+
+class Context:
+    """Library context bound to a device and the current torch stream."""
+
+    def __init__(self, device: int = 0, stream: torch.cuda.Stream | None = None):
+        self.device = torch.device("cuda", device)
+        self.stream = stream or torch.cuda.current_stream(self.device)
+        h = C.c_void_p()
+        N.call("em_ctx_create", C.byref(h), device, C.c_void_p(self.stream.cuda_stream))
+        self.handle = h
+
+    @property
+    def launches(self) -> int:
+        return int(N.lib().em_ctx_launch_count(self.handle))
+
+    def sync(self):
+        N.call("em_ctx_sync", self.handle)
+
+    def close(self):
+        if getattr(self, "handle", None):
+            N.lib().em_ctx_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def empty(self, n, dtype=torch.float64):
+        return torch.empty(int(n), dtype=dtype, device=self.device)
+
+
+class _Handle:
+    _destroy = ""
+
+    def __init__(self, ctx: Context, handle: C.c_void_p):
+        self.ctx = ctx
+        self.handle = handle
+
+    def close(self):
+        if getattr(self, "handle", None):
+            getattr(N.lib(), self._destroy)(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class Tree(_Handle):
+    _destroy = "tree_destroy"
+
+    def info(self):
+        n, nn, depth = C.c_int64(), C.c_int64(), C.c_int32()
+        N.call("tree_info", self.handle, C.byref(n), C.byref(nn), C.byref(depth))
+        return n.value, nn.value, depth.value
+
+    def get(self):
+        n, nn, _ = self.info()
+        e = self.ctx.empty
+        out = dict(perm=e(n, torch.int32), label=e(nn, torch.int64), level=e(nn, torch.int32),
+                   parent=e(nn, torch.int32), first=e(nn, torch.int32), count=e(nn, torch.int32),
+                   first_child=e(nn, torch.int32), nchild=e(nn, torch.int32), mass=e(nn),
+                   com=e(3 * nn), size=e(nn))
+        N.call("tree_get", self.ctx.handle, self.handle,
+               *[_ptr(out[k]) for k in ("perm", "label", "level", "parent", "first", "count",
+                                        "first_child", "nchild", "mass", "com", "size")])
+        out["com"] = out["com"].view(nn, 3)
+        return out
+
+
+class Pseudo(_Handle):
+    _destroy = "pseudo_destroy"
+
+    def info(self):
+        n = C.c_int64()
+        st = (C.c_int64 * 4)()
+        N.call("pseudo_info", self.handle, C.byref(n), st)
+        return n.value, list(st)
+
+    def get(self):
+        n, _ = self.info()
+        e = self.ctx.empty
+        out = dict(x=e(n), y=e(n), z=e(n), h=e(n), m=e(n), origin=e(n, torch.int64),
+                   first=e(n, torch.int32), count=e(n, torch.int32), status=e(n, torch.int32))
+        N.call("pseudo_get", self.ctx.handle, self.handle,
+               *[_ptr(out[k]) for k in ("x", "y", "z", "h", "m", "origin", "first", "count",
+                                        "status")])
+        return out
+
+
+class Voronoi(_Handle):
+    _destroy = "voronoi_destroy"
+
+    def info(self):
+        a, b, c = C.c_int64(), C.c_int64(), C.c_int64()
+        N.call("voronoi_info", self.handle, C.byref(a), C.byref(b), C.byref(c))
+        return a.value, b.value, c.value
+
+    def get(self):
+        nc, nf, nfv = self.info()
+        e = self.ctx.empty
+        out = dict(cell_face_off=e(nc + 1, torch.int64), face_vert_off=e(nf + 1, torch.int64),
+                   verts=e(3 * nfv), normals=e(3 * nf), nbr=e(nf, torch.int64), volume=e(nc))
+        N.call("voronoi_get", self.ctx.handle, self.handle,
+               *[_ptr(out[k]) for k in ("cell_face_off", "face_vert_off", "verts", "normals",
+                                        "nbr", "volume")])
+        out["verts"] = out["verts"].view(nfv, 3)
+        out["normals"] = out["normals"].view(nf, 3)
+        return out
+
+
+class Pairs(_Handle):
+    _destroy = "pairs_destroy"
+
+    def info(self):
+        a, b, c = C.c_int64(), C.c_int64(), C.c_int64()
+        N.call("pairs_info", self.handle, C.byref(a), C.byref(b), C.byref(c))
+        return a.value, b.value, c.value
+
+    @property
+    def n(self) -> int:
+        return self.info()[0]
+
+    def get(self):
+        npairs, _, nc = self.info()
+        e = self.ctx.empty
+        out = dict(pair_i=e(npairs, torch.int32), pair_j=e(npairs, torch.int32),
+                   near=e(npairs, torch.uint8), cell_pair_off=e(nc + 1, torch.int64))
+        N.call("pairs_get", self.ctx.handle, self.handle,
+               *[_ptr(out[k]) for k in ("pair_i", "pair_j", "near", "cell_pair_off")])
+        return out
+
+
+f64 = torch.float64
+
+
+def build_tree(ctx: Context, x, y, z, m, box, leaf_max: int = 8) -> Tree:
+    n = x.numel()
+    h = C.c_void_p()
+    bp, _keep = _box(box)
+    N.call("build_tree", ctx.handle, n, _ptr(x, f64, n, "x"), _ptr(y, f64, n, "y"),
+           _ptr(z, f64, n, "z"), _ptr(m, f64, n, "m"), bp, int(leaf_max), C.byref(h))
+    return Tree(ctx, h)
+
+
+def make_pseudo_particles(ctx: Context, tree: Tree, h_particle, sources, params: Params) -> Pseudo:
+    src = [float(v) for v in torch.as_tensor(sources, dtype=torch.float64).reshape(-1).tolist()]
+    arr = (C.c_double * len(src))(*src)
+    p = params.native()
+    h = C.c_void_p()
+    n, _, _ = tree.info()
+    N.call("make_pseudo_particles", ctx.handle, tree.handle, _ptr(h_particle, f64, n, "h"),
+           len(src) // 3, C.cast(arr, C.c_void_p), C.byref(p), C.byref(h),
+           allow=(N.EM_OK, N.EM_ENOTCONV))
+    return Pseudo(ctx, h)
+
+
+def build_voronoi(ctx: Context, gx, gy, gz, box, params: Params | None = None) -> Voronoi:
+    n = gx.numel()
+    p = (params or Params()).native()
+    h = C.c_void_p()
+    bp, _keep = _box(box)
+    N.call("build_voronoi", ctx.handle, n, _ptr(gx, f64, n, "gx"), _ptr(gy, f64, n, "gy"),
+           _ptr(gz, f64, n, "gz"), bp, C.byref(p), C.byref(h))
+    return Voronoi(ctx, h)
+
+
+def voronoi_from_cells(ctx: Context, gen, cell_face_off, face_vert_off, verts, normals, nbr,
+                       volume) -> Voronoi:
+    nc = cell_face_off.numel() - 1
+    nf = face_vert_off.numel() - 1
+    nfv = verts.numel() // 3
+    h = C.c_void_p()
+    N.call("voronoi_from_cells", ctx.handle, nc, nf, nfv, _ptr(gen, f64, 3 * nc, "gen"),
+           _ptr(cell_face_off, torch.int64, nc + 1), _ptr(face_vert_off, torch.int64, nf + 1),
+           _ptr(verts, f64, 3 * nfv), _ptr(normals, f64, 3 * nf),
+           _ptr(nbr, torch.int64, nf) if nbr is not None else None, _ptr(volume, f64, nc),
+           C.byref(h))
+    return Voronoi(ctx, h)
+
+
+def find_pairs(ctx: Context, x, y, z, h_, vor: Voronoi) -> Pairs:
+    n = x.numel()
+    h = C.c_void_p()
+    npairs = C.c_int64()
+    N.call("find_pairs", ctx.handle, n, _ptr(x, f64, n, "x"), _ptr(y, f64, n, "y"),
+           _ptr(z, f64, n, "z"), _ptr(h_, f64, n, "h"), vor.handle, C.byref(h), C.byref(npairs))
+    return Pairs(ctx, h)
+
+
+def pairs_from_list(ctx: Context, pair_i, pair_j, np_: int, vor: Voronoi) -> Pairs:
+    n = pair_i.numel()
+    h = C.c_void_p()
+    N.call("pairs_from_list", ctx.handle, n, _ptr(pair_i, torch.int32, n, "pair_i"),
+           _ptr(pair_j, torch.int32, n, "pair_j"), int(np_), vor.handle, C.byref(h))
+    return Pairs(ctx, h)
+
+
+def map_exact(ctx: Context, pairs: Pairs, x, y, z, h_, m, vor: Voronoi, params: Params,
+              want_wsum: bool = True, out=None):
+    """Returns (w per pair, rho per cell, sum_j w_ij per particle or None, #pairs in FP64)."""
+    npairs, np_, nc = pairs.info()
+    if out is None:
+        out = (ctx.empty(npairs), ctx.empty(nc), ctx.empty(np_) if want_wsum else None)
+    w, rho, wsum = out
+    nfp64 = C.c_int64()
+    p = params.native()
+    N.call("map_exact", ctx.handle, pairs.handle, _ptr(x, f64, np_, "x"), _ptr(y, f64, np_, "y"),
+           _ptr(z, f64, np_, "z"), _ptr(h_, f64, np_, "h"), _ptr(m, f64, np_, "m"), vor.handle,
+           C.byref(p), _ptr(w, f64, npairs), _ptr(rho, f64, nc), _ptr(wsum), C.byref(nfp64))
+    return w, rho, wsum, nfp64.value
+
+
+def map_back(ctx: Context, pairs: Pairs, w, f_cell, pseudo: Pseudo | None = None,
+             tree: Tree | None = None):
+    """Returns (f per (pseudo-)particle, f per SPH particle or None)."""
+    npairs, np_, nc = pairs.info()
+    f = ctx.empty(np_)
+    fp = None
+    if pseudo is not None:
+        n, _, _ = tree.info()
+        fp = ctx.empty(n)
+    N.call("map_back", ctx.handle, pairs.handle, _ptr(w, f64, npairs), _ptr(f_cell, f64, nc),
+           _ptr(f), pseudo.handle if pseudo is not None else None,
+           tree.handle if tree is not None else None, _ptr(fp))
+    return f, fp

@@ -1,0 +1,195 @@
+// Internal definitions shared by the library's translation units: context,
+// handles, device-memory ownership, error reporting and launch accounting.
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <cstdarg>
+#include <cstdint>
+#include <cstdio>
+#include <vector>
+
+#include "../../include/exactmap.h"
+
+#define EM_EXPORT extern "C" __attribute__((visibility("default")))
+
+struct em_ctx {
+    int device;
+    cudaStream_t stream;
+    int64_t launches;
+};
+
+void em_set_error(const char *fmt, ...);
+
+#define EM_CUDA(call)                                                                              \
+    do {                                                                                           \
+        cudaError_t e_ = (call);                                                                   \
+        if (e_ != cudaSuccess) {                                                                   \
+            em_set_error("%s:%d %s: %s", __FILE__, __LINE__, #call, cudaGetErrorString(e_));       \
+            return e_ == cudaErrorMemoryAllocation ? EM_ENOMEM : EM_ECUDA;                         \
+        }                                                                                          \
+    } while (0)
+
+#define EM_TRY(expr)                                                                               \
+    do {                                                                                           \
+        int s_ = (expr);                                                                           \
+        if (s_ != EM_OK) return s_;                                                                \
+    } while (0)
+
+#define EM_CHECK_ARG(cond)                                                                         \
+    do {                                                                                           \
+        if (!(cond)) {                                                                             \
+            em_set_error("%s: invalid argument (%s)", __func__, #cond);                            \
+            return EM_EINVAL;                                                                      \
+        }                                                                                          \
+    } while (0)
+
+// Count a kernel launch on the context and surface launch errors.
+#define EM_LAUNCHED(ctx)                                                                           \
+    do {                                                                                           \
+        (ctx)->launches++;                                                                         \
+        cudaError_t e_ = cudaGetLastError();                                                       \
+        if (e_ != cudaSuccess) {                                                                   \
+            em_set_error("%s:%d launch: %s", __FILE__, __LINE__, cudaGetErrorString(e_));          \
+            return EM_ECUDA;                                                                       \
+        }                                                                                          \
+    } while (0)
+
+// Stream-ordered device allocations released together (handle memory, or a
+// call's scratch when used as a local).
+struct DevArena {
+    cudaStream_t stream = nullptr;
+    std::vector<void *> ptrs;
+    bool scoped = false;
+
+    explicit DevArena(cudaStream_t s = nullptr, bool scoped_ = false) : stream(s), scoped(scoped_) {}
+    DevArena(const DevArena &) = delete;
+    DevArena &operator=(const DevArena &) = delete;
+    ~DevArena()
+    {
+        if (scoped) release();
+    }
+
+    template <class T>
+    int alloc(T **p, size_t n)
+    {
+        *p = nullptr;
+        size_t bytes = (n ? n : 1) * sizeof(T);
+        cudaError_t e = cudaMallocAsync((void **)p, bytes, stream);
+        if (e != cudaSuccess) {
+            em_set_error("device allocation of %zu bytes failed: %s", bytes, cudaGetErrorString(e));
+            cudaGetLastError();
+            return EM_ENOMEM;
+        }
+        ptrs.push_back((void *)*p);
+        return EM_OK;
+    }
+
+    void release()
+    {
+        for (void *p : ptrs) cudaFreeAsync(p, stream);
+        ptrs.clear();
+    }
+};
+
+// ---- handles ------------------------------------------------------------------
+
+struct em_tree {
+    int device;
+    DevArena mem;
+    int64_t n = 0, nnode = 0;
+    int depth = 0;
+    double box[6];
+    std::vector<int64_t> level_off;   // host: first node index of each level, + end
+    int32_t *perm = nullptr;          // [n] original index of Morton position k
+    uint64_t *key = nullptr;          // [n] sorted keys
+    double *xs = nullptr, *ys = nullptr, *zs = nullptr, *ms = nullptr;   // [n] Morton order
+    uint64_t *label = nullptr;
+    int32_t *level = nullptr, *parent = nullptr, *first = nullptr, *count = nullptr;
+    int32_t *first_child = nullptr, *nchild = nullptr;
+    double *mass = nullptr, *mx = nullptr, *my = nullptr, *mz = nullptr;
+    double *cx = nullptr, *cy = nullptr, *cz = nullptr, *size = nullptr;
+    explicit em_tree(cudaStream_t s) : mem(s) {}
+};
+
+struct em_pseudo {
+    int device;
+    DevArena mem;
+    int64_t n = 0, npop = 0;
+    int64_t nstatus[4] = {0, 0, 0, 0};
+    double *x = nullptr, *y = nullptr, *z = nullptr, *h = nullptr, *m = nullptr;
+    int64_t *origin = nullptr;
+    int32_t *first = nullptr, *count = nullptr, *status = nullptr;
+    explicit em_pseudo(cudaStream_t s) : mem(s) {}
+};
+
+// One face-edge of a cell, in the frame of the cell's generator g:
+// m = in-plane outward edge normal, cm = m.(V_k - g); e = unit edge
+// direction, ce = e.(V_k - g); L = edge length.
+struct __align__(32) PlaneD {
+    double x, y, z, w;   // unit outward normal (x, y, z), offset w = n.(V_0 - g)
+};
+struct __align__(16) PlaneF {
+    float x, y, z, w;
+};
+struct __align__(16) EdgeD {
+    double mx, my, mz, cm, ex, ey, ez, ce, L, pad;
+};
+struct __align__(16) EdgeF {
+    float mx, my, mz, cm, ex, ey, ez, ce, L, pad0, pad1, pad2;
+};
+
+struct em_voronoi {
+    int device;
+    DevArena mem;
+    int64_t ncell = 0, nface = 0, nfv = 0;
+    double box[6];
+    double *gen = nullptr;              // [3 ncell]
+    int64_t *cell_face_off = nullptr;   // [ncell + 1]
+    int64_t *face_vert_off = nullptr;   // [nface + 1]
+    double *verts = nullptr;            // [3 nfv]
+    double *normals = nullptr;          // [3 nface]
+    int64_t *nbr = nullptr;             // [nface]
+    double *volume = nullptr;           // [ncell]
+    // derived geometry for map_exact (generator frame)
+    double *radius = nullptr;           // [ncell] largest |V - g|
+    PlaneD *plane = nullptr;            // [nface] (n, c = n.(V_0 - g))
+    EdgeD *edge = nullptr;              // [nfv]
+    PlaneF *plane_f = nullptr;
+    EdgeF *edge_f = nullptr;
+    explicit em_voronoi(cudaStream_t s) : mem(s) {}
+};
+
+struct em_pairs {
+    int device;
+    DevArena mem;
+    int64_t npairs = 0, np = 0, ncell = 0;
+    int32_t *pair_i = nullptr, *pair_j = nullptr;   // sorted by (j, i)
+    uint8_t *near = nullptr;
+    int64_t *cell_pair_off = nullptr;               // [ncell + 1]
+    int64_t *part_pair_off = nullptr;               // [np + 1]
+    int32_t *part_pair_idx = nullptr;               // [npairs] pair ids sorted by (i, j)
+    explicit em_pairs(cudaStream_t s) : mem(s) {}
+};
+
+// ---- helpers shared across translation units -------------------------------------
+
+int em_prepare_cells(em_ctx *ctx, em_voronoi *v);                 // derived geometry
+int em_build_pair_index(em_ctx *ctx, em_pairs *pr);               // CSR offsets + transpose
+int em_exclusive_scan_i64(em_ctx *ctx, const int64_t *in, int64_t *out, int64_t n);
+int em_exclusive_scan_i32(em_ctx *ctx, const int32_t *in, int32_t *out, int64_t n);
+int em_sort_pairs_u64(em_ctx *ctx, uint64_t *keys, int32_t *vals, int64_t n, int end_bit);
+int em_sort_pairs_u32(em_ctx *ctx, uint32_t *keys, int32_t *vals, int64_t n, int end_bit);
+
+static inline int em_grid(int64_t n, int block)
+{
+    int64_t g = (n + block - 1) / block;
+    return (int)(g < 1 ? 1 : g);
+}
+
+static inline int em_nbits(uint64_t v)
+{
+    int b = 0;
+    while (b < 64 && (v >> b)) ++b;
+    return b < 1 ? 1 : b;
+}

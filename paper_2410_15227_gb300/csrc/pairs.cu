@@ -1,0 +1,246 @@
+// find_pairs: every (particle i, cell j) whose kernel support meets the cell,
+// dist(x_i, V_j) < 2 h_i, sorted by (j, i).
+//
+// The particles are Morton-sorted and bounded by a 32-ary box hierarchy of
+// their support spheres.  One warp per cell walks it with the cell's bounding
+// ball (generator g_j, radius R_j); each lane then applies the exact test to
+// one candidate.  Hits are compacted with a warp ballot, first counted, then
+// written at the cell's scanned offset.
+#include "common.cuh"
+#include "tree_util.cuh"
+
+namespace {
+
+// Squared distance from p (r = p - g) to the convex cell, 0 if inside.  The
+// closest point lies on a face whose plane has p on its outer side; on such a
+// face it is the foot of p if that foot is inside the polygon, else the
+// nearest point of an edge segment.  Returns early once it is certain the
+// distance is at least lim2.
+__device__ __forceinline__ double cell_dist2(double rx, double ry, double rz, int64_t f0, int64_t f1,
+                                             const int64_t *__restrict__ fvo, const PlaneD *__restrict__ plane,
+                                             const EdgeD *__restrict__ edge, double lim)
+{
+    bool outside = false;
+    for (int64_t f = f0; f < f1; ++f) {
+        PlaneD pl = plane[f];
+        double s = pl.w - (pl.x * rx + pl.y * ry + pl.z * rz);
+        if (s < 0.0) {
+            outside = true;
+            if (-s >= lim) return lim * lim;   // a separating plane at least lim away
+        }
+    }
+    if (!outside) return 0.0;
+    double best = INFINITY;
+    for (int64_t f = f0; f < f1; ++f) {
+        PlaneD pl = plane[f];
+        double s = pl.w - (pl.x * rx + pl.y * ry + pl.z * rz);
+        if (s >= 0.0) continue;
+        double s2 = s * s;
+        if (s2 >= best) continue;
+        bool in_poly = true;
+        double e2 = INFINITY;
+        for (int64_t e = fvo[f]; e < fvo[f + 1]; ++e) {
+            EdgeD E = edge[e];
+            double a = E.cm - (E.mx * rx + E.my * ry + E.mz * rz);
+            in_poly = in_poly && (a >= 0.0);
+            double t0 = E.ce - (E.ex * rx + E.ey * ry + E.ez * rz);
+            double t1 = t0 + E.L;
+            double tc = t0 > 0.0 ? t0 : (t1 < 0.0 ? t1 : 0.0);
+            double q = a * a + tc * tc;
+            e2 = q < e2 ? q : e2;
+        }
+        double d2 = in_poly ? s2 : s2 + e2;
+        best = d2 < best ? d2 : best;
+    }
+    return best;
+}
+
+// One warp per cell: candidate particles from the sphere hierarchy, exact
+// test, ballot compaction.  Pass 1 (keys == NULL) writes counts; pass 2
+// writes (j << 32 | i) keys and near flags at the cell's offset.
+__global__ void __launch_bounds__(128) k_cell_pairs(int64_t ncell, em::ChunkTree T, const double *__restrict__ xs,
+                                                     const double *__restrict__ ys, const double *__restrict__ zs,
+                                                     const double *__restrict__ hs, const int32_t *__restrict__ perm,
+                                                     const double *__restrict__ gen, const double *__restrict__ radius,
+                                                     const int64_t *__restrict__ cfo, const int64_t *__restrict__ fvo,
+                                                     const PlaneD *__restrict__ plane, const EdgeD *__restrict__ edge,
+                                                     float margin, int64_t *__restrict__ count,
+                                                     const int64_t *__restrict__ offset, uint64_t *__restrict__ keys,
+                                                     int32_t *__restrict__ nearf)
+{
+    int64_t j = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
+    if (j >= ncell) return;
+    const int lane = threadIdx.x & 31;
+    const double gx = gen[3 * j], gy = gen[3 * j + 1], gz = gen[3 * j + 2];
+    const double Rj = radius[j];
+    const int64_t f0 = cfo[j], f1 = cfo[j + 1];
+    const float R = (float)Rj + margin;
+    int64_t n = 0;
+    const int64_t base = keys ? offset[j] : 0;
+    em::warp_traverse(T, (float)gx, (float)gy, (float)gz, R * R, INT64_MAX, [&](int64_t k, bool valid) {
+        bool hit = false, nearb = false;
+        if (valid) {
+            double rx = xs[k] - gx, ry = ys[k] - gy, rz = zs[k] - gz;
+            double h2 = 2.0 * hs[k];
+            double rr = sqrt(rx * rx + ry * ry + rz * rz);
+            if (rr < Rj + h2 * (1.0 + 1e-12)) {
+                double d2 = cell_dist2(rx, ry, rz, f0, f1, fvo, plane, edge, 2.0 * h2);
+                hit = d2 < h2 * h2;
+                if (hit) nearb = fabs(sqrt(d2) - h2) < 0.5e-9 * h2;
+            }
+        }
+        uint32_t b = __ballot_sync(0xffffffffu, hit);
+        if (keys && hit) {
+            int64_t pos = base + n + __popc(b & ((1u << lane) - 1u));
+            keys[pos] = ((uint64_t)j << 32) | (uint32_t)perm[k];
+            nearf[pos] = nearb ? 1 : 0;
+        }
+        n += __popc(b);
+    });
+    if (!keys && lane == 0) count[j] = n;
+}
+
+__global__ void k_split_keys(int64_t n, const uint64_t *__restrict__ keys, const int32_t *__restrict__ nearf,
+                             int32_t *__restrict__ pi, int32_t *__restrict__ pj, uint8_t *__restrict__ nearo)
+{
+    int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (k >= n) return;
+    uint64_t key = keys[k];
+    pi[k] = (int32_t)(key & 0xffffffffull);
+    pj[k] = (int32_t)(key >> 32);
+    nearo[k] = (uint8_t)nearf[k];
+}
+
+__global__ void k_bbox(int64_t n, const double *__restrict__ x, const double *__restrict__ y,
+                       const double *__restrict__ z, double *__restrict__ out)
+{
+    __shared__ double red[6][256];
+    double v[6] = {INFINITY, -INFINITY, INFINITY, -INFINITY, INFINITY, -INFINITY};
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+        v[0] = fmin(v[0], x[i]);
+        v[1] = fmax(v[1], x[i]);
+        v[2] = fmin(v[2], y[i]);
+        v[3] = fmax(v[3], y[i]);
+        v[4] = fmin(v[4], z[i]);
+        v[5] = fmax(v[5], z[i]);
+    }
+    for (int c = 0; c < 6; ++c) red[c][threadIdx.x] = v[c];
+    __syncthreads();
+    for (int s = blockDim.x / 2; s > 0; s >>= 1) {
+        if (threadIdx.x < s)
+            for (int c = 0; c < 6; ++c)
+                red[c][threadIdx.x] = (c & 1) ? fmax(red[c][threadIdx.x], red[c][threadIdx.x + s])
+                                              : fmin(red[c][threadIdx.x], red[c][threadIdx.x + s]);
+        __syncthreads();
+    }
+    if (threadIdx.x == 0)
+        for (int c = 0; c < 6; ++c) out[6 * blockIdx.x + c] = red[c][0];
+}
+
+}  // namespace
+
+// Bounding box of n points (host result).
+int em_point_bbox(em_ctx *ctx, int64_t n, const double *x, const double *y, const double *z, double *box)
+{
+    DevArena tmp(ctx->stream, true);
+    const int nb = 64;
+    double *part;
+    EM_TRY(tmp.alloc(&part, 6 * nb));
+    k_bbox<<<nb, 256, 0, ctx->stream>>>(n, x, y, z, part);
+    EM_LAUNCHED(ctx);
+    double h[6 * nb];
+    EM_CUDA(cudaMemcpyAsync(h, part, sizeof h, cudaMemcpyDeviceToHost, ctx->stream));
+    EM_CUDA(cudaStreamSynchronize(ctx->stream));
+    for (int c = 0; c < 6; ++c) box[c] = (c & 1) ? -INFINITY : INFINITY;
+    for (int b = 0; b < nb; ++b)
+        for (int c = 0; c < 6; ++c) box[c] = (c & 1) ? fmax(box[c], h[6 * b + c]) : fmin(box[c], h[6 * b + c]);
+    for (int c = 0; c < 6; c += 2)
+        if (!(box[c + 1] > box[c])) {
+            double mid = box[c];
+            box[c] = mid - 1.0;
+            box[c + 1] = mid + 1.0;
+        }
+    return EM_OK;
+}
+
+static int find_pairs_impl(em_ctx *ctx, int64_t np, const double *x, const double *y, const double *z,
+                           const double *h, const em_voronoi *v, em_pairs *pr)
+{
+    cudaStream_t st = ctx->stream;
+    DevArena tmp(st, true);
+    double box[6];
+    EM_TRY(em_point_bbox(ctx, np, x, y, z, box));
+    uint64_t *mkey;
+    int32_t *perm;
+    double *xs, *ys, *zs, *hs;
+    EM_TRY(tmp.alloc(&mkey, np));
+    EM_TRY(tmp.alloc(&perm, np));
+    EM_TRY(tmp.alloc(&xs, np));
+    EM_TRY(tmp.alloc(&ys, np));
+    EM_TRY(tmp.alloc(&zs, np));
+    EM_TRY(tmp.alloc(&hs, np));
+    EM_TRY(em_morton_sort(ctx, np, x, y, z, box, mkey, perm));
+    EM_TRY(em_gather_sorted(ctx, np, perm, x, y, z, h, xs, ys, zs, hs));
+    em::ChunkTree T;
+    EM_TRY(em_chunk_tree_build(ctx, tmp, np, xs, ys, zs, hs, 2.0, &T));
+    double ext = 0.0;
+    for (int c = 0; c < 6; ++c) ext = fmax(ext, fabs(box[c]));
+    const float margin = (float)(4e-7 * (ext + 1.0));
+    const int64_t nc = v->ncell;
+    int64_t *count, *offset;
+    EM_TRY(tmp.alloc(&count, nc + 1));
+    EM_TRY(tmp.alloc(&offset, nc + 1));
+    EM_CUDA(cudaMemsetAsync(count + nc, 0, sizeof(int64_t), st));
+    k_cell_pairs<<<em_grid(nc * 32, 128), 128, 0, st>>>(nc, T, xs, ys, zs, hs, perm, v->gen, v->radius,
+                                                         v->cell_face_off, v->face_vert_off, v->plane, v->edge, margin,
+                                                         count, nullptr, nullptr, nullptr);
+    EM_LAUNCHED(ctx);
+    EM_TRY(em_exclusive_scan_i64(ctx, count, offset, nc + 1));
+    int64_t total = 0;
+    EM_CUDA(cudaMemcpyAsync(&total, offset + nc, sizeof(int64_t), cudaMemcpyDeviceToHost, st));
+    EM_CUDA(cudaStreamSynchronize(st));
+    if (total >= INT32_MAX) {
+        em_set_error("find_pairs: %lld pairs exceed the 2^31 limit of one pair list", (long long)total);
+        return EM_ECAPACITY;
+    }
+    pr->npairs = total;
+    uint64_t *keys;
+    int32_t *nearf;
+    EM_TRY(tmp.alloc(&keys, total));
+    EM_TRY(tmp.alloc(&nearf, total));
+    if (total) {
+        k_cell_pairs<<<em_grid(nc * 32, 128), 128, 0, st>>>(nc, T, xs, ys, zs, hs, perm, v->gen, v->radius,
+                                                             v->cell_face_off, v->face_vert_off, v->plane, v->edge,
+                                                             margin, count, offset, keys, nearf);
+        EM_LAUNCHED(ctx);
+        EM_TRY(em_sort_pairs_u64(ctx, keys, nearf, total, 32 + em_nbits((uint64_t)nc)));
+    }
+    EM_TRY(pr->mem.alloc(&pr->pair_i, total));
+    EM_TRY(pr->mem.alloc(&pr->pair_j, total));
+    EM_TRY(pr->mem.alloc(&pr->near, total));
+    if (total) {
+        k_split_keys<<<em_grid(total, 256), 256, 0, st>>>(total, keys, nearf, pr->pair_i, pr->pair_j, pr->near);
+        EM_LAUNCHED(ctx);
+    }
+    return em_build_pair_index(ctx, pr);
+}
+
+EM_EXPORT int find_pairs(em_ctx *ctx, int64_t np, const double *d_x, const double *d_y, const double *d_z,
+                         const double *d_h, const em_voronoi *v, em_pairs **out, int64_t *npairs)
+{
+    EM_CHECK_ARG(ctx && v && out && np >= 1 && np < INT32_MAX && d_x && d_y && d_z && d_h);
+    *out = nullptr;
+    em_pairs *pr = new em_pairs(ctx->stream);
+    pr->device = ctx->device;
+    pr->np = np;
+    pr->ncell = v->ncell;
+    int rc = find_pairs_impl(ctx, np, d_x, d_y, d_z, d_h, v, pr);
+    if (rc) {
+        pr->mem.release();
+        delete pr;
+        return rc;
+    }
+    if (npairs) *npairs = pr->npairs;
+    *out = pr;
+    return EM_OK;
+}

@@ -1,0 +1,335 @@
+// make_pseudo_particles: adaptive tree-walk selection (Section 2.4.1, Eq. 4),
+// node neighbour search and the node smoothing-length solver (Section 2.4.2,
+// Eqs. 6-11).
+//
+// Selection is evaluated per node instead of by a sequential walk: a node is
+// reached when every ancestor is opened; a reached internal node that is not
+// opened, or a reached leaf outside r_part, becomes a pseudo-particle; a
+// reached leaf inside r_part is replaced by its particles.  The predicates use
+// explicit round-to-nearest products, so the selected set is bit-identical to
+// a sequential walk with the same arithmetic.
+//
+// The neighbour search runs inside every solver iteration: a warp walks a
+// 32-ary box hierarchy over the solver population (selected nodes plus the
+// leaves of extracted particles, Morton order) with radius 2h, so the sum
+// n(h) = sum_b W(r_ab, h) always covers every neighbour of the current h.
+#include <cmath>
+
+#include "common.cuh"
+#include "tree_util.cuh"
+
+namespace {
+
+enum : uint8_t { F_LEAF = 1, F_EXTRACT = 2, F_OPEN = 4, F_REACHED = 8 };
+
+__global__ void k_node_flags(int64_t nnode, const int32_t *__restrict__ nchild, const double *__restrict__ cx,
+                             const double *__restrict__ cy, const double *__restrict__ cz,
+                             const double *__restrict__ size, int nsrc, const double *__restrict__ src, double rp2,
+                             double rl2, double th2, uint8_t *__restrict__ flags)
+{
+    int64_t a = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (a >= nnode) return;
+    double r2 = INFINITY;
+    for (int s = 0; s < nsrc; ++s) {
+        double dx = __dsub_rn(cx[a], src[3 * s]), dy = __dsub_rn(cy[a], src[3 * s + 1]),
+               dz = __dsub_rn(cz[a], src[3 * s + 2]);
+        double q = __dadd_rn(__dadd_rn(__dmul_rn(dx, dx), __dmul_rn(dy, dy)), __dmul_rn(dz, dz));
+        r2 = q < r2 ? q : r2;
+    }
+    uint8_t f = 0;
+    if (nchild[a] == 0) {
+        f |= F_LEAF;
+        if (r2 < rp2) f |= F_EXTRACT;
+    } else {
+        // open inside r_leaf, or when theta^2 < (s/r)^2 (Eq. 4)
+        if (r2 < rl2 || __dmul_rn(size[a], size[a]) > __dmul_rn(th2, r2)) f |= F_OPEN;
+    }
+    flags[a] = f;
+}
+
+__global__ void k_reached(int64_t nnode, const int32_t *__restrict__ parent, uint8_t *__restrict__ flags)
+{
+    int64_t a = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (a >= nnode) return;
+    bool r = true;
+    for (int32_t p = parent[a]; p >= 0 && r; p = parent[p]) r = (flags[p] & F_OPEN) != 0;
+    if (r) flags[a] |= F_REACHED;
+}
+
+// Mark Morton positions that start a pseudo-particle / a population entry.
+__global__ void k_mark(int64_t nnode, const uint8_t *__restrict__ flags, const int32_t *__restrict__ first,
+                       const int32_t *__restrict__ count, int32_t *__restrict__ start, int32_t *__restrict__ owner,
+                       int32_t *__restrict__ popstart)
+{
+    int64_t a = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (a >= nnode) return;
+    uint8_t f = flags[a];
+    if (!(f & F_REACHED)) return;
+    bool leaf = f & F_LEAF;
+    if (leaf && (f & F_EXTRACT)) {
+        for (int32_t k = first[a]; k < first[a] + count[a]; ++k) {
+            start[k] = 1;
+            owner[k] = -1 - (int32_t)a;
+        }
+        popstart[first[a]] = 1;
+    } else if (leaf || !(f & F_OPEN)) {
+        start[first[a]] = 1;
+        owner[first[a]] = (int32_t)a;
+        popstart[first[a]] = 1;
+    }
+}
+
+__global__ void k_emit(int64_t n, const int32_t *__restrict__ start, const int32_t *__restrict__ pidx,
+                       const int32_t *__restrict__ owner, const int32_t *__restrict__ popstart,
+                       const int32_t *__restrict__ popidx, const uint64_t *__restrict__ label,
+                       const int32_t *__restrict__ first, const int32_t *__restrict__ count,
+                       const double *__restrict__ mass, const double *__restrict__ cx, const double *__restrict__ cy,
+                       const double *__restrict__ cz, const double *__restrict__ size, const double *__restrict__ xs,
+                       const double *__restrict__ ys, const double *__restrict__ zs, const double *__restrict__ ms,
+                       const int32_t *__restrict__ perm, const double *__restrict__ hpart, double h_fact,
+                       double *__restrict__ px, double *__restrict__ py, double *__restrict__ pz,
+                       double *__restrict__ ph, double *__restrict__ pm, int64_t *__restrict__ origin,
+                       int32_t *__restrict__ pfirst, int32_t *__restrict__ pcount, int32_t *__restrict__ status,
+                       double *__restrict__ popx, double *__restrict__ popy, double *__restrict__ popz)
+{
+    int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (k >= n) return;
+    if (start[k]) {
+        int32_t q = pidx[k];
+        int32_t a = owner[k];
+        if (a >= 0) {
+            px[q] = cx[a];
+            py[q] = cy[a];
+            pz[q] = cz[a];
+            pm[q] = mass[a];
+            origin[q] = (int64_t)label[a];
+            pfirst[q] = first[a];
+            pcount[q] = count[a];
+            status[q] = -1;   // to be solved
+            // h_0 = h_fact (2 s_node) (Eq. 11); a one-particle node starts from its particle's h
+            ph[q] = (count[a] == 1 || size[a] == 0.0) ? hpart[perm[first[a]]] : (2.0 * h_fact) * size[a];
+        } else {
+            px[q] = xs[k];
+            py[q] = ys[k];
+            pz[q] = zs[k];
+            pm[q] = ms[k];
+            origin[q] = -(int64_t)perm[k] - 1;
+            pfirst[q] = (int32_t)k;
+            pcount[q] = 1;
+            status[q] = 3;
+            ph[q] = hpart[perm[k]];
+        }
+    }
+    if (popstart[k]) {
+        // the population entry at this position is the node whose range starts here
+        int32_t a = owner[k];
+        if (a < 0) a = -1 - a;
+        int32_t q = popidx[k];
+        popx[q] = cx[a];
+        popy[q] = cy[a];
+        popz[q] = cz[a];
+    }
+}
+
+struct Density {
+    double n, dn;
+};
+
+// n(h) and dn/dh for the pseudo-particle at (xa, ya, za), summed over the
+// population inside 2h; the result is identical on all lanes.
+__device__ Density warp_density(const em::ChunkTree &T, const double *__restrict__ qx,
+                                const double *__restrict__ qy, const double *__restrict__ qz, double xa, double ya,
+                                double za, double h, float margin)
+{
+    double s = 0.0, ds = 0.0;
+    const double ih = 1.0 / h;
+    const double norm = ih * ih * ih * 0.31830988618379067154;   // 1/(pi h^3)
+    float R = (float)(2.0 * h) + margin;
+    em::warp_traverse(T, (float)xa, (float)ya, (float)za, R * R, INT64_MAX, [&](int64_t k, bool valid) {
+        if (!valid) return;
+        double dx = qx[k] - xa, dy = qy[k] - ya, dz = qz[k] - za;
+        double q = sqrt(dx * dx + dy * dy + dz * dz) * ih;
+        if (q < 2.0) {
+            double w = em::m4_w(q);
+            s += w * norm;
+            ds += -(3.0 * w + q * em::m4_dw(q)) * norm * ih;
+        }
+    });
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        s += __shfl_xor_sync(0xffffffffu, s, o);
+        ds += __shfl_xor_sync(0xffffffffu, ds, o);
+    }
+    return Density{s, ds};
+}
+
+// One warp per pseudo-particle: Newton (Eq. 10) from h_0 (Eq. 11) until
+// |dh|/h_0 < tol, bisection on [1e-2 h_0, 1e2 h_0], else h_0.
+__global__ void k_h_solve(int64_t npseudo, em::ChunkTree T, const double *__restrict__ qx,
+                          const double *__restrict__ qy, const double *__restrict__ qz, const double *__restrict__ px,
+                          const double *__restrict__ py, const double *__restrict__ pz, double h_fact, double tol,
+                          int max_newton, float margin, double *__restrict__ ph, int32_t *__restrict__ status)
+{
+    int64_t a = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
+    if (a >= npseudo) return;
+    if (status[a] != -1) return;   // extracted particles keep their own h
+    const double xa = px[a], ya = py[a], za = pz[a];
+    const double h0 = ph[a];
+    double h = h0;
+    bool ok = false;
+    for (int it = 0; it < max_newton; ++it) {
+        Density d = warp_density(T, qx, qy, qz, xa, ya, za, h, margin);
+        double f = h_fact * pow(d.n, -1.0 / 3.0) - h;                      // Eq. 8
+        double fp = -h_fact * d.dn * pow(d.n, -4.0 / 3.0) / 3.0 - 1.0;      // Eq. 9
+        double hn = h - f / fp;                                             // Eq. 10
+        if (!(hn >= 1e-2 * h0 && hn <= 1e2 * h0)) break;   // left the bracket: Newton failed
+        double step = fabs(hn - h) / h0;
+        h = hn;
+        if (step < tol) {
+            ok = true;
+            break;
+        }
+    }
+    int st = 0;
+    if (!ok) {
+        double lo = 1e-2 * h0, hi = 1e2 * h0;
+        Density dl = warp_density(T, qx, qy, qz, xa, ya, za, lo, margin);
+        Density dh = warp_density(T, qx, qy, qz, xa, ya, za, hi, margin);
+        double flo = h_fact * pow(dl.n, -1.0 / 3.0) - lo;
+        double fhi = h_fact * pow(dh.n, -1.0 / 3.0) - hi;
+        if (flo * fhi > 0.0) {
+            h = h0;
+            st = 2;
+        } else {
+            for (int k = 0; k < 200 && (hi - lo) > tol * h0; ++k) {
+                double mid = 0.5 * (lo + hi);
+                Density dm = warp_density(T, qx, qy, qz, xa, ya, za, mid, margin);
+                double fm = h_fact * pow(dm.n, -1.0 / 3.0) - mid;
+                if ((fm > 0.0) == (flo > 0.0)) {
+                    lo = mid;
+                    flo = fm;
+                } else {
+                    hi = mid;
+                }
+            }
+            h = 0.5 * (lo + hi);
+            st = 1;
+        }
+    }
+    if ((threadIdx.x & 31) == 0) {
+        ph[a] = h;
+        status[a] = st;
+    }
+}
+
+__global__ void k_status_count(int64_t n, const int32_t *__restrict__ status, unsigned long long *__restrict__ cnt)
+{
+    int64_t a = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (a >= n) return;
+    int s = status[a];
+    if (s >= 0 && s < 4) atomicAdd(&cnt[s], 1ull);
+}
+
+}  // namespace
+
+static int pseudo_impl(em_ctx *ctx, const em_tree *t, const double *d_hp, int nsrc, const double *h_src,
+                       const em_params *p, em_pseudo *ps)
+{
+    cudaStream_t st = ctx->stream;
+    const int64_t n = t->n, nn = t->nnode;
+    DevArena tmp(st, true);
+    double *src;
+    uint8_t *flags;
+    int32_t *start, *owner, *popstart, *pidx, *popidx;
+    EM_TRY(tmp.alloc(&src, 3 * nsrc));
+    EM_TRY(tmp.alloc(&flags, nn));
+    EM_TRY(tmp.alloc(&start, n));
+    EM_TRY(tmp.alloc(&owner, n));
+    EM_TRY(tmp.alloc(&popstart, n));
+    EM_TRY(tmp.alloc(&pidx, n));
+    EM_TRY(tmp.alloc(&popidx, n));
+    EM_CUDA(cudaMemcpyAsync(src, h_src, 3 * nsrc * sizeof(double), cudaMemcpyHostToDevice, st));
+    EM_CUDA(cudaMemsetAsync(start, 0, n * sizeof(int32_t), st));
+    EM_CUDA(cudaMemsetAsync(popstart, 0, n * sizeof(int32_t), st));
+    const double rp2 = p->r_part * p->r_part, rl2 = p->r_leaf * p->r_leaf, th2 = p->theta * p->theta;
+    k_node_flags<<<em_grid(nn, 256), 256, 0, st>>>(nn, t->nchild, t->cx, t->cy, t->cz, t->size, nsrc, src, rp2, rl2,
+                                                   th2, flags);
+    EM_LAUNCHED(ctx);
+    k_reached<<<em_grid(nn, 256), 256, 0, st>>>(nn, t->parent, flags);
+    EM_LAUNCHED(ctx);
+    k_mark<<<em_grid(nn, 256), 256, 0, st>>>(nn, flags, t->first, t->count, start, owner, popstart);
+    EM_LAUNCHED(ctx);
+    EM_TRY(em_exclusive_scan_i32(ctx, start, pidx, n));
+    EM_TRY(em_exclusive_scan_i32(ctx, popstart, popidx, n));
+    int32_t h4[4];
+    cudaMemcpyAsync(&h4[0], pidx + n - 1, sizeof(int32_t), cudaMemcpyDeviceToHost, st);
+    cudaMemcpyAsync(&h4[1], start + n - 1, sizeof(int32_t), cudaMemcpyDeviceToHost, st);
+    cudaMemcpyAsync(&h4[2], popidx + n - 1, sizeof(int32_t), cudaMemcpyDeviceToHost, st);
+    cudaMemcpyAsync(&h4[3], popstart + n - 1, sizeof(int32_t), cudaMemcpyDeviceToHost, st);
+    EM_CUDA(cudaStreamSynchronize(st));
+    const int64_t np = (int64_t)h4[0] + h4[1], npop = (int64_t)h4[2] + h4[3];
+    ps->n = np;
+    ps->npop = npop;
+    DevArena &m = ps->mem;
+    EM_TRY(m.alloc(&ps->x, np));
+    EM_TRY(m.alloc(&ps->y, np));
+    EM_TRY(m.alloc(&ps->z, np));
+    EM_TRY(m.alloc(&ps->h, np));
+    EM_TRY(m.alloc(&ps->m, np));
+    EM_TRY(m.alloc(&ps->origin, np));
+    EM_TRY(m.alloc(&ps->first, np));
+    EM_TRY(m.alloc(&ps->count, np));
+    EM_TRY(m.alloc(&ps->status, np));
+    double *qx, *qy, *qz;
+    EM_TRY(tmp.alloc(&qx, npop));
+    EM_TRY(tmp.alloc(&qy, npop));
+    EM_TRY(tmp.alloc(&qz, npop));
+    k_emit<<<em_grid(n, 256), 256, 0, st>>>(n, start, pidx, owner, popstart, popidx, t->label, t->first, t->count,
+                                            t->mass, t->cx, t->cy, t->cz, t->size, t->xs, t->ys, t->zs, t->ms,
+                                            t->perm, d_hp, p->h_fact, ps->x, ps->y, ps->z, ps->h, ps->m, ps->origin,
+                                            ps->first, ps->count, ps->status, qx, qy, qz);
+    EM_LAUNCHED(ctx);
+    em::ChunkTree T;
+    EM_TRY(em_chunk_tree_build(ctx, tmp, npop, qx, qy, qz, nullptr, 0.0, &T));
+    double ext = 0.0;
+    for (int k = 0; k < 6; ++k) ext = fmax(ext, fabs(t->box[k]));
+    // float rounding of positions and boxes: widen the search radius
+    const float margin = (float)(4e-7 * (ext + 1.0));
+    if (np) {
+        k_h_solve<<<em_grid(np * 32, 128), 128, 0, st>>>(np, T, qx, qy, qz, ps->x, ps->y, ps->z, p->h_fact, p->h_tol,
+                                                          p->max_newton, margin, ps->h, ps->status);
+        EM_LAUNCHED(ctx);
+    }
+    unsigned long long *cnt;
+    EM_TRY(tmp.alloc(&cnt, 4));
+    EM_CUDA(cudaMemsetAsync(cnt, 0, 4 * sizeof(unsigned long long), st));
+    if (np) {
+        k_status_count<<<em_grid(np, 256), 256, 0, st>>>(np, ps->status, cnt);
+        EM_LAUNCHED(ctx);
+    }
+    unsigned long long hc[4];
+    EM_CUDA(cudaMemcpyAsync(hc, cnt, sizeof hc, cudaMemcpyDeviceToHost, st));
+    EM_CUDA(cudaStreamSynchronize(st));
+    for (int k = 0; k < 4; ++k) ps->nstatus[k] = (int64_t)hc[k];
+    return EM_OK;
+}
+
+EM_EXPORT int make_pseudo_particles(em_ctx *ctx, const em_tree *t, const double *d_h_particle, int nsrc,
+                                    const double *h_src, const em_params *p, em_pseudo **out)
+{
+    EM_CHECK_ARG(ctx && t && d_h_particle && h_src && p && out);
+    EM_CHECK_ARG(nsrc >= 1 && nsrc <= 4096);
+    EM_CHECK_ARG(p->theta >= 0.0 && p->r_part >= 0.0 && p->r_leaf >= 0.0 && p->h_fact > 0.0);
+    EM_CHECK_ARG(p->h_tol > 0.0 && p->max_newton >= 0);
+    *out = nullptr;
+    em_pseudo *ps = new em_pseudo(ctx->stream);
+    ps->device = ctx->device;
+    int rc = pseudo_impl(ctx, t, d_h_particle, nsrc, h_src, p, ps);
+    if (rc) {
+        ps->mem.release();
+        delete ps;
+        return rc;
+    }
+    *out = ps;
+    return ps->nstatus[2] ? EM_ENOTCONV : EM_OK;
+}

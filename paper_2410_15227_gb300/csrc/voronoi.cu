@@ -1,0 +1,253 @@
+// build_voronoi: Voronoi cells of the generation sites, clipped to the box.
+//
+// Each cell is built by one thread in the generator's frame (g at the
+// origin).  The convex cell is held in dual form: its planes (n.x <= d) and
+// its vertices, each a triangle of three plane indices ordered
+// counter-clockwise seen from outside, with the vertex position.  Clipping by
+// a bisector removes the vertices beyond it and replaces each edge that
+// crossed the plane by a new vertex (the kept neighbour across an edge (a, b)
+// is the vertex holding (b, a)).
+//
+// Candidates come first from the K nearest generators (a bounded list kept
+// sorted while walking the generators' box hierarchy).  The cell is exact
+// once 2 R_max < d_K, R_max being its farthest vertex: no generator farther
+// than 2 R_max can cut it.  Otherwise every generator within 2 R_max that was
+// not in the list is clipped in as well, shrinking R_max as it goes.
+// Pass 1 records the bisectors that actually cut; pass 2 replays exactly
+// those clips (bit-identical state) and writes the faces.
+#include <cmath>
+
+#include "common.cuh"
+#include "tree_util.cuh"
+
+#include "voronoi_cell.cuh"
+
+namespace {
+
+using namespace emv;
+
+__global__ void __launch_bounds__(64) k_voronoi_count(int64_t ngen, em::ChunkTree T, const double *__restrict__ xs,
+                                                      const double *__restrict__ ys, const double *__restrict__ zs,
+                                                      const int32_t *__restrict__ perm, double xlo, double xhi,
+                                                      double ylo, double yhi, double zlo, double zhi, int K,
+                                                      int64_t *__restrict__ nface, int64_t *__restrict__ nfv,
+                                                      int32_t *__restrict__ clips, int32_t *__restrict__ nclips,
+                                                      int *__restrict__ status_or)
+{
+    int64_t s = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (s >= ngen) return;
+    const int64_t j = perm[s];
+    if (j < 0 || j >= ngen) {
+        atomicOr(status_or, VS_BOUNDS);
+        return;
+    }
+    const double box[6] = {xlo, xhi, ylo, yhi, zlo, zhi};
+    VCell c;
+    int nclip = 0;
+    int st = build_cell(c, T, xs, ys, zs, perm, s, box, K, clips + s * MAXCLIP, nclip);
+    int64_t nf = 0, nv = 0;
+    if (!st) {
+        uint8_t loop[MAXV];
+        for (int q = 0; q < c.np; ++q) {
+            int n = face_loop(c, q, loop);
+            if (n < 0) {
+                st |= VS_TOPOLOGY;
+                break;
+            }
+            if (n >= 3) {
+                ++nf;
+                nv += n;
+            }
+        }
+    }
+    nclips[s] = nclip;
+    nface[j] = nf;
+    nfv[j] = nv;
+    if (st) atomicOr(status_or, st);
+}
+
+__global__ void __launch_bounds__(64) k_voronoi_emit(int64_t ngen, const double *__restrict__ xs,
+                                                     const double *__restrict__ ys, const double *__restrict__ zs,
+                                                     const int32_t *__restrict__ perm, double xlo, double xhi,
+                                                     double ylo, double yhi, double zlo, double zhi,
+                                                     const int32_t *__restrict__ clips,
+                                                     const int32_t *__restrict__ nclips,
+                                                     const int64_t *__restrict__ cell_face_off,
+                                                     const int64_t *__restrict__ cell_fv_off,
+                                                     int64_t *__restrict__ face_vert_off, double *__restrict__ verts,
+                                                     double *__restrict__ normals, int64_t *__restrict__ nbr,
+                                                     double *__restrict__ volume, double *__restrict__ gen,
+                                                     int *__restrict__ status_or)
+{
+    int64_t s = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (s >= ngen) return;
+    const double box[6] = {xlo, xhi, ylo, yhi, zlo, zhi};
+    const double gx = xs[s], gy = ys[s], gz = zs[s];
+    VCell c;
+    cell_box(c, box, gx, gy, gz);
+    const int32_t *cl = clips + s * MAXCLIP;
+    const int ncl = nclips[s];
+    const int64_t j = perm[s];
+    if (ncl < 0 || ncl > MAXCLIP || j < 0 || j >= ngen) {
+        atomicOr(status_or, VS_BOUNDS);
+        return;
+    }
+    for (int q = 0; q < ncl; ++q) {
+        int k = cl[q];
+        if (k < 0 || k >= ngen) {
+            atomicOr(status_or, VS_BOUNDS);
+            return;
+        }
+        clip_by(c, xs[k] - gx, ys[k] - gy, zs[k] - gz, perm[k]);
+    }
+    gen[3 * j] = gx;
+    gen[3 * j + 1] = gy;
+    gen[3 * j + 2] = gz;
+    int64_t f = cell_face_off[j], fv = cell_fv_off[j];
+    const int64_t f_end = cell_face_off[j + 1], fv_end = cell_fv_off[j + 1];
+    double vol = 0.0;
+    uint8_t loop[MAXV];
+    for (int q = 0; q < c.np; ++q) {
+        int n = face_loop(c, q, loop);
+        if (n < 3) continue;
+        if (f >= f_end || fv + n > fv_end) {   // must agree with the counting pass
+            atomicOr(status_or, VS_BOUNDS);
+            return;
+        }
+        double nx = c.pl[q][0], ny = c.pl[q][1], nz = c.pl[q][2];
+        double ln = sqrt(nx * nx + ny * ny + nz * nz);
+        nx /= ln;
+        ny /= ln;
+        nz /= ln;
+        normals[3 * f] = nx;
+        normals[3 * f + 1] = ny;
+        normals[3 * f + 2] = nz;
+        nbr[f] = c.pid[q];
+        face_vert_off[f] = fv;
+        double ax = 0.0, ay = 0.0, az = 0.0;   // twice the vector area
+        for (int i = 0; i < n; ++i) {
+            const double *a = c.v[loop[i]], *b = c.v[loop[(i + 1) % n]];
+            ax += a[1] * b[2] - a[2] * b[1];
+            ay += a[2] * b[0] - a[0] * b[2];
+            az += a[0] * b[1] - a[1] * b[0];
+            verts[3 * (fv + i)] = a[0] + gx;
+            verts[3 * (fv + i) + 1] = a[1] + gy;
+            verts[3 * (fv + i) + 2] = a[2] + gz;
+        }
+        double area = 0.5 * (ax * nx + ay * ny + az * nz);
+        vol += area * (c.pl[q][3] / ln) / 3.0;
+        fv += n;
+        ++f;
+    }
+    volume[j] = vol;
+}
+
+__global__ void k_finish_offsets(int64_t *face_vert_off, int64_t nface, int64_t nfv)
+{
+    face_vert_off[nface] = nfv;
+}
+
+}  // namespace
+
+static int voronoi_impl(em_ctx *ctx, int64_t ngen, const double *gx, const double *gy, const double *gz,
+                        const em_params *p, em_voronoi *v)
+{
+    cudaStream_t st = ctx->stream;
+    DevArena tmp(st, true);
+    uint64_t *key;
+    int32_t *perm;
+    double *xs, *ys, *zs;
+    EM_TRY(tmp.alloc(&key, ngen));
+    EM_TRY(tmp.alloc(&perm, ngen));
+    EM_TRY(tmp.alloc(&xs, ngen));
+    EM_TRY(tmp.alloc(&ys, ngen));
+    EM_TRY(tmp.alloc(&zs, ngen));
+    EM_TRY(em_morton_sort(ctx, ngen, gx, gy, gz, v->box, key, perm));
+    EM_TRY(em_gather_sorted(ctx, ngen, perm, gx, gy, gz, nullptr, xs, ys, zs, nullptr));
+    em::ChunkTree T;
+    EM_TRY(em_chunk_tree_build(ctx, tmp, ngen, xs, ys, zs, nullptr, 0.0, &T));
+    int K = p->knn_k > 0 ? p->knn_k : 48;
+    if (K > MAXK) K = MAXK;
+    int64_t *nface, *nfv, *cfo, *cfvo;
+    int32_t *clips, *nclips;
+    int *status;
+    EM_TRY(tmp.alloc(&nface, ngen + 1));
+    EM_TRY(tmp.alloc(&nfv, ngen + 1));
+    EM_TRY(tmp.alloc(&cfvo, ngen + 1));
+    EM_TRY(tmp.alloc(&clips, ngen * MAXCLIP));
+    EM_TRY(tmp.alloc(&nclips, ngen));
+    EM_TRY(tmp.alloc(&status, 1));
+    EM_TRY(v->mem.alloc(&cfo, ngen + 1));
+    EM_CUDA(cudaMemsetAsync(status, 0, sizeof(int), st));
+    EM_CUDA(cudaMemsetAsync(nface + ngen, 0, sizeof(int64_t), st));
+    EM_CUDA(cudaMemsetAsync(nfv + ngen, 0, sizeof(int64_t), st));
+    const double *b = v->box;
+    k_voronoi_count<<<em_grid(ngen, 64), 64, 0, st>>>(ngen, T, xs, ys, zs, perm, b[0], b[1], b[2], b[3], b[4], b[5], K,
+                                                       nface, nfv, clips, nclips, status);
+    EM_LAUNCHED(ctx);
+    EM_TRY(em_exclusive_scan_i64(ctx, nface, cfo, ngen + 1));
+    EM_TRY(em_exclusive_scan_i64(ctx, nfv, cfvo, ngen + 1));
+    int64_t tot[2];
+    int hstatus = 0;
+    EM_CUDA(cudaMemcpyAsync(&tot[0], cfo + ngen, sizeof(int64_t), cudaMemcpyDeviceToHost, st));
+    EM_CUDA(cudaMemcpyAsync(&tot[1], cfvo + ngen, sizeof(int64_t), cudaMemcpyDeviceToHost, st));
+    EM_CUDA(cudaMemcpyAsync(&hstatus, status, sizeof(int), cudaMemcpyDeviceToHost, st));
+    EM_CUDA(cudaStreamSynchronize(st));
+    if (hstatus & (VS_COINCIDENT | VS_OUTSIDE)) {
+        em_set_error("build_voronoi: %s", (hstatus & VS_COINCIDENT) ? "coincident generators"
+                                                                      : "a generator lies outside the box");
+        return EM_EINVAL;
+    }
+    if (hstatus & VS_BOUNDS) {
+        em_set_error("build_voronoi: an index check failed (status %d)", hstatus);
+        return EM_ECUDA;
+    }
+    if (hstatus) {
+        em_set_error("build_voronoi: a cell exceeded the per-cell capacity (%d planes, %d vertices) or "
+                     "lost its topology (status %d)", MAXP, MAXV, hstatus);
+        return EM_ECAPACITY;
+    }
+    v->ncell = ngen;
+    v->nface = tot[0];
+    v->nfv = tot[1];
+    v->cell_face_off = cfo;
+    EM_TRY(v->mem.alloc(&v->gen, 3 * ngen));
+    EM_TRY(v->mem.alloc(&v->face_vert_off, v->nface + 1));
+    EM_TRY(v->mem.alloc(&v->verts, 3 * v->nfv));
+    EM_TRY(v->mem.alloc(&v->normals, 3 * v->nface));
+    EM_TRY(v->mem.alloc(&v->nbr, v->nface));
+    EM_TRY(v->mem.alloc(&v->volume, ngen));
+    k_voronoi_emit<<<em_grid(ngen, 64), 64, 0, st>>>(ngen, xs, ys, zs, perm, b[0], b[1], b[2], b[3], b[4], b[5], clips,
+                                                      nclips, cfo, cfvo, v->face_vert_off, v->verts, v->normals,
+                                                      v->nbr, v->volume, v->gen, status);
+    EM_LAUNCHED(ctx);
+    EM_CUDA(cudaMemcpyAsync(&hstatus, status, sizeof(int), cudaMemcpyDeviceToHost, st));
+    EM_CUDA(cudaStreamSynchronize(st));
+    if (hstatus) {
+        em_set_error("build_voronoi: face output disagreed with the counting pass (status %d)", hstatus);
+        return EM_ECAPACITY;
+    }
+    k_finish_offsets<<<1, 1, 0, st>>>(v->face_vert_off, v->nface, v->nfv);
+    EM_LAUNCHED(ctx);
+    return em_prepare_cells(ctx, v);
+}
+
+EM_EXPORT int build_voronoi(em_ctx *ctx, int64_t ngen, const double *d_gx, const double *d_gy, const double *d_gz,
+                            const double *h_box, const em_params *p, em_voronoi **out)
+{
+    EM_CHECK_ARG(ctx && out && h_box && p && d_gx && d_gy && d_gz);
+    EM_CHECK_ARG(ngen >= 1 && ngen < INT32_MAX);
+    EM_CHECK_ARG(h_box[1] > h_box[0] && h_box[3] > h_box[2] && h_box[5] > h_box[4]);
+    *out = nullptr;
+    em_voronoi *v = new em_voronoi(ctx->stream);
+    v->device = ctx->device;
+    for (int k = 0; k < 6; ++k) v->box[k] = h_box[k];
+    int rc = voronoi_impl(ctx, ngen, d_gx, d_gy, d_gz, p, v);
+    if (rc) {
+        v->mem.release();
+        delete v;
+        return rc;
+    }
+    *out = v;
+    return EM_OK;
+}
