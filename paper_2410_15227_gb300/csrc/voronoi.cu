@@ -21,125 +21,169 @@
 #include "tree_util.cuh"
 
 #include "voronoi_cell.cuh"
+#include "voronoi_warp.cuh"
+
+constexpr int WMAXV_LOOP = emv::MAXV;
 
 namespace {
 
 using namespace emv;
+using emw::WCell;
 
-__global__ void __launch_bounds__(64) k_voronoi_count(int64_t ngen, em::ChunkTree T, const double *__restrict__ xs,
-                                                      const double *__restrict__ ys, const double *__restrict__ zs,
-                                                      const int32_t *__restrict__ perm, double xlo, double xhi,
-                                                      double ylo, double yhi, double zlo, double zhi, int K,
-                                                      int64_t *__restrict__ nface, int64_t *__restrict__ nfv,
-                                                      int32_t *__restrict__ clips, int32_t *__restrict__ nclips,
-                                                      int *__restrict__ status_or)
+constexpr int VW = 2;   // warps (cells) per block
+
+__global__ void __launch_bounds__(32 * VW) k_voronoi_count(int64_t ngen, em::ChunkTree T, const double *__restrict__ xs,
+                                                           const double *__restrict__ ys, const double *__restrict__ zs,
+                                                           const int32_t *__restrict__ perm, double xlo, double xhi,
+                                                           double ylo, double yhi, double zlo, double zhi, int K,
+                                                           float margin, int64_t *__restrict__ nface,
+                                                           int64_t *__restrict__ nfv, int32_t *__restrict__ clips,
+                                                           int32_t *__restrict__ nclips, int *__restrict__ status_or)
 {
-    int64_t s = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    __shared__ WCell cells[VW];
+    const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int64_t s = blockIdx.x * (int64_t)VW + w;
     if (s >= ngen) return;
+    WCell &c = cells[w];
     const int64_t j = perm[s];
     if (j < 0 || j >= ngen) {
-        atomicOr(status_or, VS_BOUNDS);
+        if (lane == 0) atomicOr(status_or, VS_BOUNDS);
         return;
     }
     const double box[6] = {xlo, xhi, ylo, yhi, zlo, zhi};
-    VCell c;
     int nclip = 0;
-    int st = build_cell(c, T, xs, ys, zs, perm, s, box, K, clips + s * MAXCLIP, nclip);
+    int st = emw::wbuild_cell(c, T, xs, ys, zs, perm, s, box, K, margin, clips + s * MAXCLIP, nclip);
     int64_t nf = 0, nv = 0;
     if (!st) {
-        uint8_t loop[MAXV];
-        for (int q = 0; q < c.np; ++q) {
-            int n = face_loop(c, q, loop);
-            if (n < 0) {
-                st |= VS_TOPOLOGY;
-                break;
-            }
+        uint8_t loop[WMAXV_LOOP];
+        bool bad = false;
+        for (int q = lane; q < c.np; q += 32) {
+            int n = emw::wface_loop(c, q, loop, WMAXV_LOOP);
+            if (n < 0) bad = true;
             if (n >= 3) {
                 ++nf;
                 nv += n;
             }
         }
+        if (__any_sync(0xffffffffu, bad)) st |= VS_TOPOLOGY;
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            nf += __shfl_xor_sync(0xffffffffu, nf, o);
+            nv += __shfl_xor_sync(0xffffffffu, nv, o);
+        }
     }
-    nclips[s] = nclip;
-    nface[j] = nf;
-    nfv[j] = nv;
-    if (st) atomicOr(status_or, st);
+    if (lane == 0) {
+        nclips[s] = nclip;
+        nface[j] = nf;
+        nfv[j] = nv;
+        if (st) {
+            atomicOr(status_or, st);
+            atomicMin(status_or + 1, (int)s);   // first failing cell (sorted index)
+        }
+    }
 }
 
-__global__ void __launch_bounds__(64) k_voronoi_emit(int64_t ngen, const double *__restrict__ xs,
-                                                     const double *__restrict__ ys, const double *__restrict__ zs,
-                                                     const int32_t *__restrict__ perm, double xlo, double xhi,
-                                                     double ylo, double yhi, double zlo, double zhi,
-                                                     const int32_t *__restrict__ clips,
-                                                     const int32_t *__restrict__ nclips,
-                                                     const int64_t *__restrict__ cell_face_off,
-                                                     const int64_t *__restrict__ cell_fv_off,
-                                                     int64_t *__restrict__ face_vert_off, double *__restrict__ verts,
-                                                     double *__restrict__ normals, int64_t *__restrict__ nbr,
-                                                     double *__restrict__ volume, double *__restrict__ gen,
-                                                     int *__restrict__ status_or)
+__global__ void __launch_bounds__(32 * VW) k_voronoi_emit(int64_t ngen, const double *__restrict__ xs,
+                                                          const double *__restrict__ ys, const double *__restrict__ zs,
+                                                          const int32_t *__restrict__ perm, double xlo, double xhi,
+                                                          double ylo, double yhi, double zlo, double zhi,
+                                                          const int32_t *__restrict__ clips,
+                                                          const int32_t *__restrict__ nclips,
+                                                          const int64_t *__restrict__ cell_face_off,
+                                                          const int64_t *__restrict__ cell_fv_off,
+                                                          int64_t *__restrict__ face_vert_off, double *__restrict__ verts,
+                                                          double *__restrict__ normals, int64_t *__restrict__ nbr,
+                                                          double *__restrict__ volume, double *__restrict__ gen,
+                                                          int *__restrict__ status_or)
 {
-    int64_t s = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    __shared__ WCell cells[VW];
+    const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int64_t s = blockIdx.x * (int64_t)VW + w;
     if (s >= ngen) return;
+    WCell &c = cells[w];
     const double box[6] = {xlo, xhi, ylo, yhi, zlo, zhi};
     const double gx = xs[s], gy = ys[s], gz = zs[s];
-    VCell c;
-    cell_box(c, box, gx, gy, gz);
-    const int32_t *cl = clips + s * MAXCLIP;
     const int ncl = nclips[s];
     const int64_t j = perm[s];
     if (ncl < 0 || ncl > MAXCLIP || j < 0 || j >= ngen) {
-        atomicOr(status_or, VS_BOUNDS);
+        if (lane == 0) atomicOr(status_or, VS_BOUNDS);
         return;
     }
+    emw::wcell_box(c, box, gx, gy, gz);
+    const int32_t *cl = clips + s * MAXCLIP;
     for (int q = 0; q < ncl; ++q) {
         int k = cl[q];
         if (k < 0 || k >= ngen) {
-            atomicOr(status_or, VS_BOUNDS);
+            if (lane == 0) atomicOr(status_or, VS_BOUNDS);
             return;
         }
-        clip_by(c, xs[k] - gx, ys[k] - gy, zs[k] - gz, perm[k]);
+        double dx = xs[k] - gx, dy = ys[k] - gy, dz = zs[k] - gz;
+        if (emw::wclip(c, dx, dy, dz, 0.5 * (dx * dx + dy * dy + dz * dz), perm[k]) < 0) {
+            if (lane == 0) atomicOr(status_or, VS_BOUNDS);
+            return;
+        }
     }
-    gen[3 * j] = gx;
-    gen[3 * j + 1] = gy;
-    gen[3 * j + 2] = gz;
-    int64_t f = cell_face_off[j], fv = cell_fv_off[j];
-    const int64_t f_end = cell_face_off[j + 1], fv_end = cell_fv_off[j + 1];
+    if (lane == 0) {
+        gen[3 * j] = gx;
+        gen[3 * j + 1] = gy;
+        gen[3 * j + 2] = gz;
+    }
+    const int64_t f0 = cell_face_off[j], f_end = cell_face_off[j + 1];
+    const int64_t fv0 = cell_fv_off[j], fv_end = cell_fv_off[j + 1];
+    int64_t fbase = f0, fvbase = fv0;
     double vol = 0.0;
-    uint8_t loop[MAXV];
-    for (int q = 0; q < c.np; ++q) {
-        int n = face_loop(c, q, loop);
-        if (n < 3) continue;
-        if (f >= f_end || fv + n > fv_end) {   // must agree with the counting pass
-            atomicOr(status_or, VS_BOUNDS);
-            return;
+    uint8_t loop[WMAXV_LOOP];
+    bool bad = false;
+    for (int r = 0; r < c.np; r += 32) {
+        int q = r + lane;
+        int n = q < c.np ? emw::wface_loop(c, q, loop, WMAXV_LOOP) : 0;
+        bool face = n >= 3;
+        unsigned m = __ballot_sync(0xffffffffu, face);
+        int64_t fi = fbase + __popc(m & emw::lanemask_lt());
+        // exclusive scan of loop lengths over the lanes
+        int len = face ? n : 0, incl = len;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            int t = __shfl_up_sync(0xffffffffu, incl, o);
+            if (lane >= o) incl += t;
         }
-        double nx = c.pl[q][0], ny = c.pl[q][1], nz = c.pl[q][2];
-        double ln = sqrt(nx * nx + ny * ny + nz * nz);
-        nx /= ln;
-        ny /= ln;
-        nz /= ln;
-        normals[3 * f] = nx;
-        normals[3 * f + 1] = ny;
-        normals[3 * f + 2] = nz;
-        nbr[f] = c.pid[q];
-        face_vert_off[f] = fv;
-        double ax = 0.0, ay = 0.0, az = 0.0;   // twice the vector area
-        for (int i = 0; i < n; ++i) {
-            const double *a = c.v[loop[i]], *b = c.v[loop[(i + 1) % n]];
-            ax += a[1] * b[2] - a[2] * b[1];
-            ay += a[2] * b[0] - a[0] * b[2];
-            az += a[0] * b[1] - a[1] * b[0];
-            verts[3 * (fv + i)] = a[0] + gx;
-            verts[3 * (fv + i) + 1] = a[1] + gy;
-            verts[3 * (fv + i) + 2] = a[2] + gz;
+        int64_t fvi = fvbase + incl - len;
+        if (face) {
+            if (fi >= f_end || fvi + n > fv_end) {
+                bad = true;
+            } else {
+                const int cur = c.cur;
+                double nx = c.pl[q][0], ny = c.pl[q][1], nz = c.pl[q][2];
+                double ln = sqrt(nx * nx + ny * ny + nz * nz);
+                nx /= ln;
+                ny /= ln;
+                nz /= ln;
+                normals[3 * fi] = nx;
+                normals[3 * fi + 1] = ny;
+                normals[3 * fi + 2] = nz;
+                nbr[fi] = c.pid[q];
+                face_vert_off[fi] = fvi;
+                double ax = 0.0, ay = 0.0, az = 0.0;   // twice the vector area
+                for (int i = 0; i < n; ++i) {
+                    const double *a = c.v[cur][loop[i]], *b = c.v[cur][loop[(i + 1) % n]];
+                    ax += a[1] * b[2] - a[2] * b[1];
+                    ay += a[2] * b[0] - a[0] * b[2];
+                    az += a[0] * b[1] - a[1] * b[0];
+                    verts[3 * (fvi + i)] = a[0] + gx;
+                    verts[3 * (fvi + i) + 1] = a[1] + gy;
+                    verts[3 * (fvi + i) + 2] = a[2] + gz;
+                }
+                double area = 0.5 * (ax * nx + ay * ny + az * nz);
+                vol += area * (c.pl[q][3] / ln) / 3.0;
+            }
         }
-        double area = 0.5 * (ax * nx + ay * ny + az * nz);
-        vol += area * (c.pl[q][3] / ln) / 3.0;
-        fv += n;
-        ++f;
+        fbase += __popc(m);
+        fvbase += __shfl_sync(0xffffffffu, incl, 31);
     }
-    volume[j] = vol;
+    if (__any_sync(0xffffffffu, bad) && lane == 0) atomicOr(status_or, VS_BOUNDS);
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) vol += __shfl_xor_sync(0xffffffffu, vol, o);
+    if (lane == 0) volume[j] = vol;
 }
 
 __global__ void k_finish_offsets(int64_t *face_vert_off, int64_t nface, int64_t nfv)
@@ -176,14 +220,18 @@ static int voronoi_impl(em_ctx *ctx, int64_t ngen, const double *gx, const doubl
     EM_TRY(tmp.alloc(&cfvo, ngen + 1));
     EM_TRY(tmp.alloc(&clips, ngen * MAXCLIP));
     EM_TRY(tmp.alloc(&nclips, ngen));
-    EM_TRY(tmp.alloc(&status, 1));
+    EM_TRY(tmp.alloc(&status, 2));
     EM_TRY(v->mem.alloc(&cfo, ngen + 1));
     EM_CUDA(cudaMemsetAsync(status, 0, sizeof(int), st));
+    EM_CUDA(cudaMemsetAsync(status + 1, 0x7f, sizeof(int), st));
     EM_CUDA(cudaMemsetAsync(nface + ngen, 0, sizeof(int64_t), st));
     EM_CUDA(cudaMemsetAsync(nfv + ngen, 0, sizeof(int64_t), st));
     const double *b = v->box;
-    k_voronoi_count<<<em_grid(ngen, 64), 64, 0, st>>>(ngen, T, xs, ys, zs, perm, b[0], b[1], b[2], b[3], b[4], b[5], K,
-                                                       nface, nfv, clips, nclips, status);
+    double ext = 0.0;
+    for (int k = 0; k < 6; ++k) ext = fmax(ext, fabs(b[k]));
+    const float margin = (float)(4e-7 * (ext + 1.0));
+    k_voronoi_count<<<em_grid(ngen, VW), 32 * VW, 0, st>>>(ngen, T, xs, ys, zs, perm, b[0], b[1], b[2], b[3], b[4], b[5],
+                                                            K, margin, nface, nfv, clips, nclips, status);
     EM_LAUNCHED(ctx);
     EM_TRY(em_exclusive_scan_i64(ctx, nface, cfo, ngen + 1));
     EM_TRY(em_exclusive_scan_i64(ctx, nfv, cfvo, ngen + 1));
@@ -203,8 +251,14 @@ static int voronoi_impl(em_ctx *ctx, int64_t ngen, const double *gx, const doubl
         return EM_ECUDA;
     }
     if (hstatus) {
+        int first[2] = {0, 0};
+        EM_CUDA(cudaMemcpyAsync(first, status + 1, sizeof(int), cudaMemcpyDeviceToHost, st));
+        EM_CUDA(cudaMemcpyAsync(first + 1, perm + first[0], sizeof(int), cudaMemcpyDeviceToHost, st));
+        EM_CUDA(cudaStreamSynchronize(st));
+        EM_CUDA(cudaMemcpyAsync(first + 1, perm + first[0], sizeof(int), cudaMemcpyDeviceToHost, st));
+        EM_CUDA(cudaStreamSynchronize(st));
         em_set_error("build_voronoi: a cell exceeded the per-cell capacity (%d planes, %d vertices) or "
-                     "lost its topology (status %d)", MAXP, MAXV, hstatus);
+                     "lost its topology (status %d, first at generator %d)", MAXP, MAXV, hstatus, first[1]);
         return EM_ECAPACITY;
     }
     v->ncell = ngen;
@@ -217,7 +271,7 @@ static int voronoi_impl(em_ctx *ctx, int64_t ngen, const double *gx, const doubl
     EM_TRY(v->mem.alloc(&v->normals, 3 * v->nface));
     EM_TRY(v->mem.alloc(&v->nbr, v->nface));
     EM_TRY(v->mem.alloc(&v->volume, ngen));
-    k_voronoi_emit<<<em_grid(ngen, 64), 64, 0, st>>>(ngen, xs, ys, zs, perm, b[0], b[1], b[2], b[3], b[4], b[5], clips,
+    k_voronoi_emit<<<em_grid(ngen, VW), 32 * VW, 0, st>>>(ngen, xs, ys, zs, perm, b[0], b[1], b[2], b[3], b[4], b[5], clips,
                                                       nclips, cfo, cfvo, v->face_vert_off, v->verts, v->normals,
                                                       v->nbr, v->volume, v->gen, status);
     EM_LAUNCHED(ctx);

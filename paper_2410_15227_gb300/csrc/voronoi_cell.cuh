@@ -18,10 +18,13 @@ namespace emv {
 constexpr int MAXP = 64;     // planes per cell (6 walls + cutting bisectors)
 constexpr int MAXV = 128;    // vertices per cell
 constexpr int MAXK = 64;     // nearest-neighbour list
-constexpr int MAXCLIP = 96;   // recorded cutting bisectors (planes are reclaimed)
+constexpr int MAXCLIP = 192;  // recorded cutting bisectors (planes are reclaimed)
 constexpr int STACK = 32 * em::kMaxLevels;
 
-enum : int { VS_OK = 0, VS_CAPACITY = 1, VS_TOPOLOGY = 2, VS_COINCIDENT = 4, VS_OUTSIDE = 8, VS_BOUNDS = 16 };
+enum : int {
+    VS_OK = 0, VS_CAPACITY = 1, VS_TOPOLOGY = 2, VS_COINCIDENT = 4, VS_OUTSIDE = 8, VS_BOUNDS = 16,
+    VS_CLIPS = 32, VS_CANDIDATES = 64, VS_ROUNDS = 128
+};
 
 struct VCell {
     int np, nt;

@@ -1,0 +1,504 @@
+// Warp-cooperative Voronoi cell construction (one warp per cell, the cell
+// in shared memory).  Same dual representation and the same clipping order
+// as the per-thread code in voronoi_cell.cuh: vertices beyond the bisector
+// are removed, kept vertices stay in order, and the new vertices are
+// appended in the order (removed vertex, edge) -- so both produce the same
+// cell.  Candidates: every generator within a radius R of the site (found by
+// a warp walk of the generators' box hierarchy), sorted by distance; the
+// cell is exact once 2 R_max < R, otherwise the shell up to 2 R_max is
+// clipped in as well.
+#pragma once
+
+#include <cstdint>
+
+#include "tree_util.cuh"
+#include "voronoi_cell.cuh"
+
+namespace emw {
+
+constexpr int WMAXP = emv::MAXP;
+constexpr int WMAXV = emv::MAXV;
+constexpr int WCAND = 256;   // candidate list (power of two for the bitonic sort)
+
+struct WCell {
+    double pl[WMAXP][4];
+    double v[2][WMAXV][3];
+    double f[WMAXV];
+    double cd2[WCAND];
+    int cid[WCAND];
+    int pid[WMAXP];
+    int out_list[WMAXV];
+    uint8_t tri[2][WMAXV][4];
+    int np, nt, cur, ncand, err;
+};
+
+__device__ __forceinline__ unsigned lanemask_lt() { return (1u << (threadIdx.x & 31)) - 1u; }
+
+__device__ __forceinline__ bool has_edge(const uint8_t *t, uint8_t a, uint8_t b)
+{
+    return (t[0] == a && t[1] == b) || (t[1] == a && t[2] == b) || (t[2] == a && t[0] == b);
+}
+
+__device__ void wcell_box(WCell &c, const double *box, double gx, double gy, double gz)
+{
+    const int lane = threadIdx.x & 31;
+    if (lane == 0) {
+        emv::VCell *dummy = nullptr;
+        (void)dummy;
+        const double lo[3] = {box[0] - gx, box[2] - gy, box[4] - gz};
+        const double hi[3] = {box[1] - gx, box[3] - gy, box[5] - gz};
+        c.np = 6;
+        for (int w = 0; w < 6; ++w) {
+            int ax = w >> 1;
+            c.pl[w][0] = c.pl[w][1] = c.pl[w][2] = 0.0;
+            c.pl[w][ax] = (w & 1) ? 1.0 : -1.0;
+            c.pl[w][3] = (w & 1) ? hi[ax] : -lo[ax];
+            c.pid[w] = -1 - w;
+        }
+        c.nt = 8;
+        c.cur = 0;
+        c.err = 0;
+        for (int i = 0; i < 8; ++i) {
+            int sx = i & 1, sy = (i >> 1) & 1, sz = (i >> 2) & 1;
+            uint8_t X = (uint8_t)sx, Y = (uint8_t)(2 + sy), Z = (uint8_t)(4 + sz);
+            bool pos = ((sx ? 1 : -1) * (sy ? 1 : -1) * (sz ? 1 : -1)) > 0;
+            c.tri[0][i][0] = X;
+            c.tri[0][i][1] = pos ? Y : Z;
+            c.tri[0][i][2] = pos ? Z : Y;
+            c.v[0][i][0] = sx ? hi[0] : lo[0];
+            c.v[0][i][1] = sy ? hi[1] : lo[1];
+            c.v[0][i][2] = sz ? hi[2] : lo[2];
+        }
+    }
+    __syncwarp();
+}
+
+// Drop planes no vertex refers to (one lane; rare).
+__device__ int wcompact(WCell &c)
+{
+    const int lane = threadIdx.x & 31;
+    if (lane == 0) {
+        int map[WMAXP];
+        for (int q = 0; q < c.np; ++q) map[q] = -1;
+        const int cur = c.cur;
+        for (int t = 0; t < c.nt; ++t)
+            for (int e = 0; e < 3; ++e) map[c.tri[cur][t][e]] = 0;
+        int n = 0;
+        for (int q = 0; q < c.np; ++q) {
+            if (map[q] < 0) continue;
+            map[q] = n;
+            if (n != q) {
+                for (int k = 0; k < 4; ++k) c.pl[n][k] = c.pl[q][k];
+                c.pid[n] = c.pid[q];
+            }
+            ++n;
+        }
+        for (int t = 0; t < c.nt; ++t)
+            for (int e = 0; e < 3; ++e) c.tri[cur][t][e] = (uint8_t)map[c.tri[cur][t][e]];
+        c.np = n;
+    }
+    __syncwarp();
+    return c.np;
+}
+
+// Clip by n.x <= d.  Returns 1 changed, 0 unchanged, < 0 error (all lanes).
+__device__ int wclip(WCell &c, double nx, double ny, double nz, double d, int id)
+{
+    const int lane = threadIdx.x & 31;
+    const int cur = c.cur, nxt = cur ^ 1, nt = c.nt;
+    bool any = false;
+    for (int t = lane; t < nt; t += 32) {
+        double f = nx * c.v[cur][t][0] + ny * c.v[cur][t][1] + nz * c.v[cur][t][2] - d;
+        c.f[t] = f;
+        any = any || f > 0.0;
+    }
+    if (!__any_sync(0xffffffffu, any)) return 0;
+    __syncwarp();
+    if (c.np >= WMAXP && wcompact(c) >= WMAXP) return -emv::VS_CAPACITY;
+    const int q = c.np;
+    // kept vertices, in order, into the other buffer; removed ones listed
+    int nk = 0, nout = 0;
+    for (int base = 0; base < nt; base += 32) {
+        int t = base + lane;
+        bool in = t < nt;
+        bool keep = in && !(c.f[t] > 0.0);
+        bool out = in && !keep;
+        unsigned mk = __ballot_sync(0xffffffffu, keep), mo = __ballot_sync(0xffffffffu, out);
+        if (keep) {
+            int pos = nk + __popc(mk & lanemask_lt());
+            for (int e = 0; e < 3; ++e) c.tri[nxt][pos][e] = c.tri[cur][t][e];
+            for (int e = 0; e < 3; ++e) c.v[nxt][pos][e] = c.v[cur][t][e];
+        }
+        if (out) c.out_list[nout + __popc(mo & lanemask_lt())] = t;
+        nk += __popc(mk);
+        nout += __popc(mo);
+    }
+    __syncwarp();
+    if (nk == 0) return -emv::VS_TOPOLOGY;
+    // one task per (removed vertex, edge): a new vertex where the kept neighbour lies
+    int nn = nk;
+    bool bad = false;
+    for (int base = 0; base < 3 * nout; base += 32) {
+        int k = base + lane;
+        bool newv = false;
+        uint8_t a = 0, b = 0;
+        double px = 0, py = 0, pz = 0;
+        if (k < 3 * nout) {
+            int t = c.out_list[k / 3], e = k % 3;
+            a = c.tri[cur][t][e];
+            b = c.tri[cur][t][(e + 1) % 3];
+            int u = -1;
+            for (int s = 0; s < nt; ++s)
+                if (has_edge(c.tri[cur][s], b, a)) {
+                    u = s;
+                    break;
+                }
+            if (u < 0) {
+                bad = true;
+            } else if (!(c.f[u] > 0.0)) {
+                newv = true;
+                double fu = c.f[u], ft = c.f[t];
+                double s = fu / (fu - ft);
+                px = c.v[cur][u][0] + s * (c.v[cur][t][0] - c.v[cur][u][0]);
+                py = c.v[cur][u][1] + s * (c.v[cur][t][1] - c.v[cur][u][1]);
+                pz = c.v[cur][u][2] + s * (c.v[cur][t][2] - c.v[cur][u][2]);
+            }
+        }
+        unsigned m = __ballot_sync(0xffffffffu, newv);
+        if (newv) {
+            int pos = nn + __popc(m & lanemask_lt());
+            if (pos < WMAXV) {
+                c.tri[nxt][pos][0] = a;
+                c.tri[nxt][pos][1] = b;
+                c.tri[nxt][pos][2] = (uint8_t)q;
+                c.v[nxt][pos][0] = px;
+                c.v[nxt][pos][1] = py;
+                c.v[nxt][pos][2] = pz;
+            }
+        }
+        nn += __popc(m);
+    }
+    if (__any_sync(0xffffffffu, bad)) return -emv::VS_TOPOLOGY;
+    if (nn > WMAXV) return -emv::VS_CAPACITY;
+    if (lane == 0) {
+        c.pl[q][0] = nx;
+        c.pl[q][1] = ny;
+        c.pl[q][2] = nz;
+        c.pl[q][3] = d;
+        c.pid[q] = id;
+        c.np = q + 1;
+        c.nt = nn;
+        c.cur = nxt;
+    }
+    __syncwarp();
+    return 1;
+}
+
+__device__ double wrmax2(const WCell &c)
+{
+    const int lane = threadIdx.x & 31;
+    double r2 = 0.0;
+    for (int t = lane; t < c.nt; t += 32) {
+        const double *v = c.v[c.cur][t];
+        double q = v[0] * v[0] + v[1] * v[1] + v[2] * v[2];
+        r2 = q > r2 ? q : r2;
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        double q = __shfl_xor_sync(0xffffffffu, r2, o);
+        r2 = q > r2 ? q : r2;
+    }
+    return r2;
+}
+
+// Gather every generator k != s with lo2 <= d^2 < hi2 into the candidate
+// list (sorted by (d^2, k) afterwards).  Returns the count, or -1 if it
+// exceeds WCAND.
+__device__ int gather(WCell &c, const em::ChunkTree &T, const double *__restrict__ xs, const double *__restrict__ ys,
+                      const double *__restrict__ zs, int64_t s, double gx, double gy, double gz, double lo2,
+                      double hi2, float margin, int &status)
+{
+    const int lane = threadIdx.x & 31;
+    int n = 0;
+    float R = (float)sqrt(hi2) + margin;
+    em::warp_traverse(T, (float)gx, (float)gy, (float)gz, R * R, INT64_MAX, [&](int64_t k, bool valid) {
+        bool hit = false;
+        double d2 = 0.0;
+        if (valid && k != s) {
+            double dx = xs[k] - gx, dy = ys[k] - gy, dz = zs[k] - gz;
+            d2 = dx * dx + dy * dy + dz * dz;
+            hit = d2 >= lo2 && d2 < hi2;
+            if (d2 == 0.0) status |= emv::VS_COINCIDENT;
+        }
+        unsigned m = __ballot_sync(0xffffffffu, hit);
+        if (hit) {
+            int pos = n + __popc(m & lanemask_lt());
+            if (pos < WCAND) {
+                c.cd2[pos] = d2;
+                c.cid[pos] = (int)k;
+            }
+        }
+        n += __popc(m);
+    });
+    status = __reduce_or_sync(0xffffffffu, status);
+    __syncwarp();
+    return n > WCAND ? -1 : n;
+}
+
+// Bitonic sort of the first n candidates by (d^2, index), padded to WCAND.
+__device__ void sort_cand(WCell &c, int n)
+{
+    const int lane = threadIdx.x & 31;
+    for (int i = n + lane; i < WCAND; i += 32) {
+        c.cd2[i] = INFINITY;
+        c.cid[i] = 0x7fffffff;
+    }
+    __syncwarp();
+    for (int size = 2; size <= WCAND; size <<= 1) {
+        for (int stride = size >> 1; stride > 0; stride >>= 1) {
+            for (int i = lane; i < WCAND / 2; i += 32) {
+                int lo = 2 * i - (i & (stride - 1));
+                int hi = lo + stride;
+                bool up = ((lo & size) == 0);
+                double a = c.cd2[lo], b = c.cd2[hi];
+                int ia = c.cid[lo], ib = c.cid[hi];
+                bool gt = (a > b) || (a == b && ia > ib);
+                if (gt == up) {
+                    c.cd2[lo] = b;
+                    c.cd2[hi] = a;
+                    c.cid[lo] = ib;
+                    c.cid[hi] = ia;
+                }
+            }
+            __syncwarp();
+        }
+    }
+}
+
+// Generators k != s whose bisector cuts the current cell (some vertex v has
+// f = r_k.v - |r_k|^2/2 > 0, r_k = g_k - g), excluding those nearer than
+// sqrt(skip2) (already applied).  Boxes are skipped when every vertex is at
+// least as close to the site as to the box.  Returns the count, -1 if it
+// exceeds WCAND (the first WCAND found are kept).
+__device__ int gather_cutting(WCell &c, const em::ChunkTree &T, const double *__restrict__ xs,
+                              const double *__restrict__ ys, const double *__restrict__ zs, int64_t s, double gx,
+                              double gy, double gz, double skip2, double hi2)
+{
+    const int lane = threadIdx.x & 31;
+    const int cur = c.cur, nt = c.nt;
+    auto box_can_cut = [&](const float4 lo, const float4 hi) -> bool {
+        const double lx = (double)lo.x - gx, ly = (double)lo.y - gy, lz = (double)lo.z - gz;
+        const double hx = (double)hi.x - gx, hy = (double)hi.y - gy, hz = (double)hi.z - gz;
+        {   // the whole box at or beyond the window's outer radius
+            double dx = fmax(fmax(lx, -hx), 0.0), dy = fmax(fmax(ly, -hy), 0.0), dz = fmax(fmax(lz, -hz), 0.0);
+            if (dx * dx + dy * dy + dz * dz >= hi2 * (1.0 + 1e-9)) return false;
+        }
+        for (int t = 0; t < nt; ++t) {
+            const double *v = c.v[cur][t];
+            double dx = fmax(fmax(lx - v[0], v[0] - hx), 0.0);
+            double dy = fmax(fmax(ly - v[1], v[1] - hy), 0.0);
+            double dz = fmax(fmax(lz - v[2], v[2] - hz), 0.0);
+            double db = dx * dx + dy * dy + dz * dz;
+            double dg = v[0] * v[0] + v[1] * v[1] + v[2] * v[2];
+            if (db < dg) return true;
+        }
+        return false;
+    };
+    uint32_t mask[em::kMaxLevels + 1];
+    int64_t base[em::kMaxLevels + 1];
+    const int top = T.nlev;
+    int n = 0;
+    {
+        bool hit = lane < T.count[top] && box_can_cut(T.lo[top][lane], T.hi[top][lane]);
+        mask[top] = __ballot_sync(0xffffffffu, hit);
+        base[top] = 0;
+    }
+    int lvl = top;
+    while (true) {
+        if (mask[lvl] == 0) {
+            if (lvl == top) break;
+            ++lvl;
+            continue;
+        }
+        int cidx = __ffs(mask[lvl]) - 1;
+        mask[lvl] &= mask[lvl] - 1;
+        int64_t node = base[lvl] * 32 + cidx;
+        if (lvl == 1) {
+            int64_t k = node * 32 + lane;
+            bool hit = false;
+            double d2 = 0.0;
+            if (k < T.count[0] && k != s) {
+                double rx = xs[k] - gx, ry = ys[k] - gy, rz = zs[k] - gz;
+                d2 = rx * rx + ry * ry + rz * rz;
+                if (d2 >= skip2 && d2 < hi2) {
+                    // a vertex beyond the bisector by more than rounding: vertices on an
+                    // already applied bisector sit at |f| ~ 1e-16 d and must not re-qualify
+                    double d = 0.5 * (rx * rx + ry * ry + rz * rz);
+                    const double tol = 1e-12 * d;
+                    for (int t = 0; t < nt && !hit; ++t) {
+                        const double *v = c.v[cur][t];
+                        hit = rx * v[0] + ry * v[1] + rz * v[2] - d > tol;
+                    }
+                }
+            }
+            unsigned m = __ballot_sync(0xffffffffu, hit);
+            if (hit) {
+                int pos = n + __popc(m & lanemask_lt());
+                if (pos < WCAND) {
+                    c.cd2[pos] = d2;
+                    c.cid[pos] = (int)k;
+                }
+            }
+            n += __popc(m);
+        } else {
+            int64_t child = node * 32 + lane;
+            bool hit = child < T.count[lvl - 1] && box_can_cut(T.lo[lvl - 1][child], T.hi[lvl - 1][child]);
+            mask[lvl - 1] = __ballot_sync(0xffffffffu, hit);
+            base[lvl - 1] = node;
+            --lvl;
+        }
+    }
+    __syncwarp();
+    return n > WCAND ? -1 : n;
+}
+
+// Clip by the first nc (sorted) candidates; records the cutting ones.
+__device__ int clip_sorted(WCell &c, const double *__restrict__ xs, const double *__restrict__ ys,
+                           const double *__restrict__ zs, const int32_t *__restrict__ perm, int64_t n, double gx,
+                           double gy, double gz, int nc, int32_t *clip_ids, int &nclip)
+{
+    for (int i = 0; i < nc; ++i) {
+        int k = c.cid[i];
+        if (k < 0 || k >= n) return emv::VS_BOUNDS;
+        double dx = xs[k] - gx, dy = ys[k] - gy, dz = zs[k] - gz;
+        int r = wclip(c, dx, dy, dz, 0.5 * (dx * dx + dy * dy + dz * dz), perm[k]);
+        if (r < 0) return -r;
+        if (r > 0) {
+            if (nclip >= emv::MAXCLIP) return emv::VS_CLIPS;
+            if ((threadIdx.x & 31) == 0) clip_ids[nclip] = k;
+            ++nclip;
+        }
+    }
+    return 0;
+}
+
+// Build the cell of sorted generator s; records the cutting bisectors.
+// Stage 1: every generator within a radius R chosen from the local spacing
+// (8th nearest of the site's 32-generator chunk), nearest first.  Stage 2
+// (exact completion): generators whose bisector still cuts the cell, in
+// distance windows [lo, hi) that shrink until they fit the candidate list,
+// nearest first, until the window passes 2 R_max.  Every generator nearer
+// than lo has been applied at each step.
+__device__ int wbuild_cell(WCell &c, const em::ChunkTree &T, const double *__restrict__ xs,
+                           const double *__restrict__ ys, const double *__restrict__ zs,
+                           const int32_t *__restrict__ perm, int64_t s, const double *box, int K, float margin,
+                           int32_t *clip_ids, int &nclip)
+{
+    const int lane = threadIdx.x & 31;
+    int status = 0;
+    nclip = 0;
+    const double gx = xs[s], gy = ys[s], gz = zs[s];
+    if (!(gx > box[0] && gx < box[1] && gy > box[2] && gy < box[3] && gz > box[4] && gz < box[5]))
+        return emv::VS_OUTSIDE;
+    wcell_box(c, box, gx, gy, gz);
+    const int64_t n = T.count[0];
+    // local spacing: the 8th smallest distance to the other members of the chunk
+    double R2;
+    {
+        int64_t k = (s / 32) * 32 + lane;
+        double d2 = INFINITY;
+        if (k < n && k != s) {
+            double dx = xs[k] - gx, dy = ys[k] - gy, dz = zs[k] - gz;
+            d2 = dx * dx + dy * dy + dz * dz;
+        }
+        double kth = INFINITY;
+        for (int r = 0; r < 8; ++r) {
+            double m = d2;
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) m = fmin(m, __shfl_xor_sync(0xffffffffu, m, o));
+            kth = m;
+            unsigned who = __ballot_sync(0xffffffffu, d2 == m);
+            if (lane == __ffs(who) - 1) d2 = INFINITY;
+        }
+        if (!(kth < INFINITY)) {
+            const double bx = box[1] - box[0], by = box[3] - box[2], bz = box[5] - box[4];
+            kth = 0.01 * (bx * bx + by * by + bz * bz);
+        }
+        R2 = kth * cbrt(1.5 * K / 8.0) * cbrt(1.5 * K / 8.0);
+    }
+    // stage 1: shrink or grow R until the candidates fit and number at least K
+    double lo_ok = 0.0, hi_bad = INFINITY;
+    int nc = -1;
+    for (int it = 0; it < 48; ++it) {
+        nc = gather(c, T, xs, ys, zs, s, gx, gy, gz, -1.0, R2, margin, status);
+        if (status & emv::VS_COINCIDENT) return status;
+        if (nc < 0) {
+            hi_bad = R2;
+            R2 = lo_ok > 0.0 ? sqrt(lo_ok * hi_bad) : 0.3 * R2;
+            continue;
+        }
+        if (nc < K && nc < n - 1 && hi_bad == INFINITY && it < 40) {
+            lo_ok = R2;
+            R2 *= 3.0;
+            continue;
+        }
+        break;
+    }
+    double skip2 = -1.0;
+    if (nc > 0) {
+        sort_cand(c, nc);
+        int st = clip_sorted(c, xs, ys, zs, perm, n, gx, gy, gz, nc, clip_ids, nclip);
+        if (st) return status | st;
+    }
+    if (nc >= 0) skip2 = R2;   // every generator nearer than R was applied
+    // stage 2: windows [skip2, hi2) of generators that still cut, nearest first
+    for (int round = 0; round < 256; ++round) {
+        const double lim2 = 4.0 * wrmax2(c) * (1.0 + 1e-12);   // no generator beyond 2 R_max can cut
+        if (skip2 >= lim2) return status;
+        double hi2 = lim2;
+        int m = -1;
+        for (int h = 0; h < 64; ++h) {
+            m = gather_cutting(c, T, xs, ys, zs, s, gx, gy, gz, skip2, hi2);
+            if (m >= 0) break;
+            hi2 = (skip2 > 0.0 ? skip2 : 0.0) + 0.5 * (hi2 - (skip2 > 0.0 ? skip2 : 0.0));
+        }
+        if (m < 0) return status | emv::VS_CANDIDATES;
+        if (m > 0) {
+            sort_cand(c, m);
+            int st = clip_sorted(c, xs, ys, zs, perm, n, gx, gy, gz, m, clip_ids, nclip);
+            if (st) return status | st;
+        }
+        skip2 = hi2;
+    }
+    return status | emv::VS_ROUNDS;
+}
+
+// Face loop of plane q (one lane): vertex indices counter-clockwise seen from
+// outside; returns the length (0 if the plane holds no vertex, -1 on error).
+__device__ int wface_loop(const WCell &c, int q, uint8_t *loop, int maxn)
+{
+    const int cur = c.cur, nt = c.nt;
+    int t0 = -1;
+    for (int t = 0; t < nt && t0 < 0; ++t)
+        if (c.tri[cur][t][0] == q || c.tri[cur][t][1] == q || c.tri[cur][t][2] == q) t0 = t;
+    if (t0 < 0) return 0;
+    int n = 0, t = t0;
+    do {
+        if (n >= maxn) return -1;
+        loop[n++] = (uint8_t)t;
+        const uint8_t *tr = c.tri[cur][t];
+        int r = tr[0] == q ? 0 : (tr[1] == q ? 1 : 2);
+        uint8_t y = tr[(r + 2) % 3];
+        int nx = -1;
+        for (int s = 0; s < nt; ++s)
+            if (has_edge(c.tri[cur][s], (uint8_t)q, y)) {
+                nx = s;
+                break;
+            }
+        if (nx < 0) return -1;
+        t = nx;
+    } while (t != t0);
+    return n;
+}
+
+}  // namespace emw
