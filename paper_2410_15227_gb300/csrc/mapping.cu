@@ -4,6 +4,7 @@
 
 #include "common.cuh"
 #include "exact.cuh"
+#include "quad32.cuh"
 
 using namespace em;
 
@@ -325,28 +326,105 @@ __global__ void __launch_bounds__(128) k_map_fp64(int64_t npairs, const int32_t 
                                cfo[j], cfo[j + 1], fvo, plane, edge, err);
 }
 
-// FP32 bulk pass: pairs whose estimated relative error exceeds tol are listed
-// for the FP64 pass.
+// FP32 bulk pass (quadrature form, see quad32.cuh).  Per face: the reference
+// R = distance from p to the face polygon (FP32 is enough: any value used
+// consistently for the face is exact when P is outside the polygon; inside,
+// R = D), then R, 2 - R, K(R) and K(1) - K(R) from FP64.  Per edge: D, A,
+// T0, T1, B^2, B^2 - 1, 4 - B^2 and A^2 - rho^2 in FP64 (one rounding each),
+// the quadrature nodes in FP32.  The estimated error 12 eps times the sum of
+// the magnitudes of the non-negative pieces flags the pair for the FP64 pass
+// when it exceeds tol |w| + 1e-14; so does a face plane through P.
 __global__ void __launch_bounds__(128) k_map_fp32(int64_t npairs, const int32_t *__restrict__ pi,
                                                   const int32_t *__restrict__ pj, const double *__restrict__ x,
                                                   const double *__restrict__ y, const double *__restrict__ z,
                                                   const double *__restrict__ h, const double *__restrict__ gen,
                                                   const double *__restrict__ radius, const int64_t *__restrict__ cfo,
-                                                  const int64_t *__restrict__ fvo, const PlaneF *__restrict__ plane,
-                                                  const EdgeF *__restrict__ edge, float tol, double *__restrict__ w,
+                                                  const int64_t *__restrict__ fvo, const PlaneD *__restrict__ plane,
+                                                  const EdgeD *__restrict__ edge, const PlaneF *__restrict__ plane_f,
+                                                  const EdgeF *__restrict__ edge_f, float tol, double *__restrict__ w,
                                                   int32_t *__restrict__ flagged, int *__restrict__ nflag)
 {
     int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     if (k >= npairs) return;
-    int i = pi[k], j = pj[k];
-    float err;
-    float wk = pair_weight<float, false>((float)(x[i] - gen[3 * j]), (float)(y[i] - gen[3 * j + 1]),
-                                  (float)(z[i] - gen[3 * j + 2]), (float)h[i], (float)radius[j], cfo[j], cfo[j + 1],
-                                  fvo, plane, edge, err);
-    // per-term relative error of a few ulp of FP32 (2^-24), times the summed magnitudes
-    const float est = 8.0f * 5.9604645e-8f * err;
-    w[k] = (double)wk;
-    if (!(est <= tol * fabsf(wk))) {
+    const int i = pi[k], j = pj[k];
+    const double rx = x[i] - gen[3 * j], ry = y[i] - gen[3 * j + 1], rz = z[i] - gen[3 * j + 2];
+    const double hh = h[i], ih = 1.0 / hh;
+    const float rxf = (float)rx, ryf = (float)ry, rzf = (float)rz, ihf = (float)ih;
+    const int64_t f0 = cfo[j], f1 = cfo[j + 1];
+    bool inside = true;
+    for (int64_t f = f0; f < f1; ++f) {
+        PlaneD pl = plane[f];
+        inside = inside && !(pl.w - (pl.x * rx + pl.y * ry + pl.z * rz) < 0.0);
+    }
+    const bool full = inside && (sqrt(rx * rx + ry * ry + rz * rz) + radius[j] < 2.0 * hh);
+    double acc = 0.0, mag = 0.0;
+    bool force = false;   // the FP32 form does not apply: recompute in FP64
+    for (int64_t f = f0; f < f1; ++f) {
+        PlaneD pl = plane[f];
+        const double sd = pl.w - (pl.x * rx + pl.y * ry + pl.z * rz);
+        const double D64 = fabs(sd) * ih;
+        // P in (or within underflow of) the face plane: in the complement
+        // form such a face would carry half of the kernel, so leave it to FP64
+        if (!full && D64 < 1e-30) force = true;
+        if (sd == 0.0 || (!full && D64 >= 2.0)) continue;
+        const int64_t e0 = fvo[f], e1 = fvo[f + 1];
+        // reference distance to the polygon (FP32)
+        bool inpoly = true;
+        float rho2 = INFINITY;
+        for (int64_t e = e0; e < e1; ++e) {
+            EdgeF E = edge_f[e];
+            float a = (E.cm - (E.mx * rxf + E.my * ryf + E.mz * rzf)) * ihf;
+            float t0 = (E.ce - (E.ex * rxf + E.ey * ryf + E.ez * rzf)) * ihf;
+            float t1 = t0 + E.L * ihf;
+            inpoly = inpoly && a > 0.f;
+            float tc = t0 > 0.f ? t0 : (t1 < 0.f ? t1 : 0.f);
+            rho2 = fminf(rho2, a * a + tc * tc);
+        }
+        const float Df = (float)D64;
+        const double rr2 = inpoly ? 0.0 : (double)rho2;
+        const double R2 = D64 * D64 + rr2;
+        if (!full && R2 >= 4.0) continue;   // the polygon lies entirely beyond 2h
+        const double R64 = sqrt(R2);
+        emq::FaceRef fr;
+        fr.tilde = !full;
+        fr.R = (float)R64;
+        fr.R2 = fr.R * fr.R;
+        fr.R3 = fr.R2 * fr.R;
+        fr.R4 = fr.R2 * fr.R2;
+        fr.v = (float)(2.0 - R64);
+        fr.v2 = fr.v * fr.v;
+        fr.v3 = fr.v2 * fr.v;
+        fr.v4 = fr.v2 * fr.v2;
+        fr.KR = (float)(full ? em::K_of(R64) : em::K_tilde(R64));
+        fr.C1 = R64 < 1.0 ? (float)(full ? em::K_of(1.0) - em::K_of(R64) : em::K_tilde(1.0) - em::K_tilde(R64)) : 0.f;
+        float fs = 0.f, fm = 0.f;
+        for (int64_t e = e0; e < e1; ++e) {
+            EdgeD E = edge[e];
+            const double a = (E.cm - (E.mx * rx + E.my * ry + E.mz * rz)) * ih;
+            if (a == 0.0) continue;
+            const double t0 = (E.ce - (E.ex * rx + E.ey * ry + E.ez * rz)) * ih;
+            const double t1 = t0 + E.L * ih;
+            const double B2 = D64 * D64 + a * a;
+            emq::EdgeRef er;
+            er.cc = (float)(a * a - rr2);
+            er.c1 = (float)(B2 - 1.0);
+            er.c4 = (float)(4.0 - B2);
+            float mg;
+            const float v = emq::edge_q(Df, (float)fabs(a), (float)t0, (float)t1, (float)B2, fr, er, mg);
+            fs += a > 0.0 ? v : -v;
+            fm += mg;
+        }
+        acc += sd > 0.0 ? (double)fs : -(double)fs;
+        mag += (double)fm;
+    }
+    const double wk = full ? acc : ((inside ? 1.0 : 0.0) - acc);
+    if (inside && !full) mag += 1.0;
+    w[k] = wk;
+    // error bound of the FP32 pass: 12 ulp of every non-negative piece it
+    // summed (pieces are relative-accurate to a few ulp; the factor carries a
+    // 1.5x margin over the largest error/bound ratio seen against FP64)
+    const double est = 12.0 * 5.9604644775390625e-8 * mag;
+    if (force || !(est <= (double)tol * fabs(wk) + 1e-14)) {
         int slot = atomicAdd(nflag, 1);
         flagged[slot] = (int32_t)k;
     }
@@ -406,7 +484,8 @@ EM_EXPORT int map_exact(em_ctx *ctx, const em_pairs *pr, const double *d_x, cons
             EM_CUDA(cudaMemsetAsync(nflag, 0, sizeof(int), ctx->stream));
             k_map_fp32<<<em_grid(n, block), block, 0, ctx->stream>>>(
                 n, pr->pair_i, pr->pair_j, d_x, d_y, d_z, d_h, v->gen, v->radius, v->cell_face_off,
-                v->face_vert_off, v->plane_f, v->edge_f, (float)p->fp64_threshold, d_w_out, flagged, nflag);
+                v->face_vert_off, v->plane, v->edge, v->plane_f, v->edge_f, (float)p->fp64_threshold, d_w_out,
+                flagged, nflag);
             EM_LAUNCHED(ctx);
             int hflag = 0;
             EM_CUDA(cudaMemcpyAsync(&hflag, nflag, sizeof(int), cudaMemcpyDeviceToHost, ctx->stream));
