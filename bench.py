@@ -25,10 +25,14 @@ ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
 METRIC = "particle-cell pairs mapped/s (mixed vs FP64) at stated max rel. err; % of roofline"
-WORKLOAD = "pseudo_1M_particles_262k_cells"
+# name -> (workload, whether the step builds pseudo-particles from a tree)
+WORKLOADS = {
+    "pseudo_1e6": ("pseudo_1M_particles_262k_cells", True),
+    "sphere_1e5": ("sphere_100k_particles_25k_cells", False),
+}
 # pseudo-particle selection: r_part, r_leaf from the paper's Table 1 runs; theta
-# chosen so that the cloud yields about 1e5 pseudo-particles
-THETA = 0.3
+# chosen so that the cloud yields about 1e5 pseudo-particles (102,908)
+THETA = 0.065
 L2_BYTES = 129 * 2 ** 20
 
 
@@ -38,6 +42,9 @@ def parse():
     ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=("ours", "reference"), default="ours")
+    ap.add_argument("--workload", choices=tuple(WORKLOADS), default="pseudo_1e6",
+                    help="pseudo_1e6: 1e6-particle cloud through the tree and pseudo-particles (the "
+                         "benchmark); sphere_1e5: 1e5 particles mapped directly (smaller case)")
     ap.add_argument("--precision", choices=("mixed", "fp64"), default="mixed")
     ap.add_argument("--theta", type=float, default=THETA)
     ap.add_argument("--fp64-threshold", type=float, default=1e-5)
@@ -49,8 +56,12 @@ def parse():
 
 def load_workload(args):
     from paper_2410_15227_gb300 import inputs
-    w = inputs.cached(inputs.workload_pseudo_1e6, cache_dir=args.cache)
-    w.params["theta"] = args.theta
+    if args.workload == "pseudo_1e6":
+        w = inputs.cached(inputs.workload_pseudo_1e6, cache_dir=args.cache)
+        w.params["theta"] = args.theta
+    else:
+        w = inputs.cached(inputs.workload_sphere_100k, cache_dir=args.cache)
+        w.params = dict(inputs.PSEUDO_PARAMS)
     return w
 
 
@@ -134,11 +145,17 @@ def run_ours(args, rank, world):
     stream = torch.cuda.current_stream(device)
     map_ms = []
 
+    pseudo = WORKLOADS[args.workload][1]
+
     def step(x, y, z, m, h, gx, gy, gz, fc, record=False):
-        tree = api.build_tree(ctx, x, y, z, m, w.box, 8)
-        ps = api.make_pseudo_particles(ctx, tree, h, src, P)
+        if pseudo:
+            tree = api.build_tree(ctx, x, y, z, m, w.box, 8)
+            ps = api.make_pseudo_particles(ctx, tree, h, src, P)
+            g = ps.get()
+        else:
+            tree = ps = None
+            g = dict(x=x, y=y, z=z, h=h, m=m)
         vor = api.build_voronoi(ctx, gx, gy, gz, w.box, P)
-        g = ps.get()
         pr = api.find_pairs(ctx, g["x"], g["y"], g["z"], g["h"], vor)
         if record:
             e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
@@ -148,7 +165,7 @@ def run_ours(args, rank, world):
             e1.record(stream)
             map_ms.append((e0, e1))
         f, fp = api.map_back(ctx, pr, wts, fc, ps, tree)
-        return dict(npairs=pr.info()[0], npseudo=ps.info()[0], nfp64=nf, rho=rho, fp=fp, wsum=wsum,
+        return dict(npairs=pr.info()[0], npseudo=ps.info()[0] if pseudo else w.n, nfp64=nf, rho=rho, fp=fp, wsum=wsum,
                     w=wts, pr=pr, g=g, vor=vor)
 
     flush = torch.empty(2 * L2_BYTES // 4, dtype=torch.float32, device=device)
@@ -163,11 +180,18 @@ def run_ours(args, rank, world):
         g = out["g"]
         w64, rho64, u64, _ = api.map_exact(ctx, out["pr"], g["x"], g["y"], g["z"], g["h"], g["m"],
                                            out["vor"], P64)
-        rel = (out["w"] - w64).abs() / w64.abs().clamp_min(1e-300)
+        # relative errors where the 1e-5 relative target applies, i.e. above
+        # the absolute floor 1e-14 / 1e-5; the absolute error over all pairs
+        dw = (out["w"] - w64).abs()
+        big = w64.abs() >= 1e-9
+        rel = dw[big] / w64[big].abs()
         rrel = (out["rho"] - rho64).abs() / rho64.abs().clamp_min(1e-300)
         inner = u64 > 1 - 1e-12
         tot64 = (rho64 * 1.0).sum()
         acc = {"max_rel_err_w_vs_fp64": float(rel.max()), "rms_rel_err_w_vs_fp64": float(rel.pow(2).mean().sqrt()),
+               "rel_err_over": "pairs with |w| >= 1e-9",
+               "max_abs_err_w_vs_fp64": float(dw.max()),
+               "pairs_over_1e-5_rel_plus_1e-14_abs": int((dw > 1e-5 * w64.abs() + 1e-14).sum()),
                "max_rel_err_rho_vs_fp64": float(rrel.max()),
                "max_abs_unity_err": float((out["wsum"][inner] - 1).abs().max()) if bool(inner.any()) else None,
                "fp64_recomputed_frac": out["nfp64"] / max(out["npairs"], 1)}
@@ -215,8 +239,8 @@ def run_ours(args, rank, world):
                warmup=args.warmup, ms_per_step=tmax / args.steps, higher_is_better=True,
                scaling="weak", vs_baseline=None,
                dtype="f32+f64" if args.precision == "mixed" else "f64", data="synthetic",
-               config={"workload": WORKLOAD, "particles": w.n, "cells": w.ngen,
-                       "pseudo_particles": out["npseudo"], "pairs_per_step": out["npairs"],
+               config={"workload": WORKLOADS[args.workload][0], "particles": w.n, "cells": w.ngen,
+                       "pseudo_particles": out["npseudo"] if pseudo else None, "pairs_per_step": out["npairs"],
                        "theta": args.theta, "r_part": w.params["r_part"], "r_leaf": w.params["r_leaf"],
                        "precision": args.precision, "fp64_threshold": args.fp64_threshold,
                        "l2": "flushed between steps (258 MiB write)", "parallelism": f"replicas x{world}"},
@@ -280,63 +304,100 @@ def run_e2e(args, w, step, device):
 # CPU oracle (baseline and reference arm)
 # ---------------------------------------------------------------------------
 
-def oracle_sample(w, ncell=48, seed=7):
-    """A bounded sample of the same workload for the FP64 CPU oracle: the
-    oracle's own brute-force cells for `ncell` random generators of the grid,
-    the cloud's particles that meet them (oracle all-pairs test), and their
-    pairs."""
+def oracle_sample(w, theta, ntarget=64, seed=7, pseudo=True):
+    """A bounded sample of the same workload, built by the FP64 CPU oracle
+    alone: `ntarget` random pseudo-particles from its own tree and selection
+    on the cloud (nodes get h from the oracle's h-solver against the whole
+    population) -- or random particles when the workload maps particles
+    directly -- the oracle's brute-force cells of every generator within 2h of
+    them, and the oracle's pairs among these."""
     import numpy as np
 
     import oracle
+    pr = w.params
     rng = np.random.default_rng(seed)
-    cells_idx = np.sort(rng.choice(w.ngen, ncell, replace=False))
-    cells = oracle.voronoi(w.gx, w.gy, w.gz, w.box, cells=cells_idx)
-    pairs = oracle.find_pairs(w.x, w.y, w.z, w.h, cells)
-    return cells, pairs
+    if not pseudo:      # the particles themselves
+        tg = np.sort(rng.choice(w.n, ntarget, replace=False))
+        px, py, pz, h = w.x[tg], w.y[tg], w.z[tg], w.h[tg]
+        return _sample_cells(w, px, py, pz, h)
+    ps, tree, sel = oracle.make_pseudo_particles(w.x, w.y, w.z, w.m, w.h, w.box, np.zeros((1, 3)),
+                                                 pr["r_part"], pr["r_leaf"], theta, h_fact=pr["h_fact"],
+                                                 solve=False)
+    tg = np.sort(rng.choice(ps.n, ntarget, replace=False))
+    h = ps.h[tg].copy()
+    node = ps.origin[tg] > 0
+    if node.any():
+        ids = sel.ref[tg[node]]
+        h0 = oracle.h_initial(tree, ids, w.h, pr["h_fact"])
+        h[node] = oracle.h_solve(tree.com[sel.pop_node], tree.com[ids], h0, pr["h_fact"], 1e-13, 50)[0]
+    return _sample_cells(w, ps.x[tg], ps.y[tg], ps.z[tg], h)
 
 
-def time_oracle(w, cells, pairs, reps=1):
+def _sample_cells(w, px, py, pz, h):
+    import numpy as np
+
+    import oracle
+    ntarget = px.shape[0]
+    gen = np.stack([w.gx, w.gy, w.gz], 1)
+    near = np.zeros(w.ngen, bool)
+    for a in range(ntarget):
+        near |= np.einsum("ij,ij->i", gen - (px[a], py[a], pz[a]), gen - (px[a], py[a], pz[a])) < 4 * h[a] ** 2
+    cells = oracle.voronoi(w.gx, w.gy, w.gz, w.box, cells=np.flatnonzero(near))
+    pairs = oracle.find_pairs(px, py, pz, h, cells)
+    return (px, py, pz, h), cells, pairs
+
+
+def time_oracle(parts, cells, pairs, reps=1):
     import oracle
     nt = oracle.nthreads_default()
     t0 = time.perf_counter()
     for _ in range(reps):
-        oracle.map_exact(pairs, w.x, w.y, w.z, w.h, cells, nthreads=nt)
+        oracle.map_exact(pairs, *parts, cells, nthreads=nt)
     dt = time.perf_counter() - t0
     return pairs.n * reps / dt, nt, dt
 
 
+def _sample_text(pairs, cells, nt, pseudo=True):
+    who = ("64 random pseudo-particles (oracle tree, selection and h-solver on the 1e6-particle cloud)"
+           if pseudo else "64 random particles of the cloud")
+    return (f"oracle map_exact (FP64, OpenMP, {nt} threads) on {pairs.n} pairs of {who} with the oracle's "
+            f"brute-force cells of the {cells.ncell} generators within their 2h")
+
+
 def cpu_baseline(args, w):
-    cells, pairs = oracle_sample(w)
-    v, nt, dt = time_oracle(w, cells, pairs, 1)
+    pseudo = WORKLOADS[args.workload][1]
+    parts, cells, pairs = oracle_sample(w, args.theta, pseudo=pseudo)
+    v, nt, dt = time_oracle(parts, cells, pairs, 1)
     reps = max(1, int(15.0 / max(dt, 1e-3)))
-    v, nt, dt = time_oracle(w, cells, pairs, reps)
+    v, nt, dt = time_oracle(parts, cells, pairs, reps)
     return {"value": v, "unit": "pairs/s", "cores": nt, "kind": "oracle",
-            "sample": f"oracle map_exact (FP64, OpenMP) on {pairs.n} pairs of {cells.ncell} "
-                      f"brute-force cells of the 262,144-cell grid with the cloud's SPH particles, "
-                      f"x{reps} in {dt:.1f} s"}
+            "sample": _sample_text(pairs, cells, nt, pseudo) + f", x{reps} in {dt:.1f} s"}
 
 
 def run_reference(args, rank, world):
     if rank != 0:
         return None
     w = load_workload(args)
-    cells, pairs = oracle_sample(w)
+    pseudo = WORKLOADS[args.workload][1]
+    parts, cells, pairs = oracle_sample(w, args.theta, pseudo=pseudo)
+    _, _, dt = time_oracle(parts, cells, pairs, 1)
+    reps = max(1, int(2.0 / max(dt, 1e-3)))    # about 2 s of oracle work per step
     for _ in range(max(args.warmup, 0)):
-        time_oracle(w, cells, pairs, 1)
+        time_oracle(parts, cells, pairs, reps)
     t0 = time.perf_counter()
     n = 0
     for _ in range(args.steps):
-        v, nt, dt = time_oracle(w, cells, pairs, 1)
-        n += pairs.n
+        v, nt, dt = time_oracle(parts, cells, pairs, reps)
+        n += pairs.n * reps
     t = time.perf_counter() - t0
     value = n / t
-    sample = (f"oracle map_exact (FP64, OpenMP, {nt} threads) on {pairs.n} pairs of {cells.ncell} "
-              f"brute-force cells of the 262,144-cell grid with the cloud's SPH particles per step")
+    sample = _sample_text(pairs, cells, nt, pseudo) + f", x{reps} per step"
     return dict(metric=METRIC, value=value, unit="pairs/s", n_gpus=world, steps=args.steps,
                 warmup=args.warmup, ms_per_step=t / args.steps * 1e3, higher_is_better=True,
                 scaling="weak", vs_baseline=None, dtype="f64", data="synthetic",
-                config={"workload": WORKLOAD, "particles": w.n, "cells": w.ngen, "sampled_cells": cells.ncell,
-                        "pairs_per_step": pairs.n, "theta": args.theta},
+                config={"workload": WORKLOADS[args.workload][0], "particles": w.n, "cells": w.ngen,
+                        "sampled_cells": cells.ncell,
+                        "pairs_per_step": pairs.n * reps, "theta": args.theta},
                 impl="reference",
                 cpu_baseline={"value": value, "unit": "pairs/s", "cores": nt, "kind": "oracle", "sample": sample},
                 e2e={"value": value, "unit": "pairs/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},

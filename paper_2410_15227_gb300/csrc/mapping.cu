@@ -326,97 +326,294 @@ __global__ void __launch_bounds__(128) k_map_fp64(int64_t npairs, const int32_t 
                                cfo[j], cfo[j + 1], fvo, plane, edge, err);
 }
 
-// FP32 bulk pass (quadrature form, see quad32.cuh).  Per face: the reference
-// R = distance from p to the face polygon (FP32 is enough: any value used
-// consistently for the face is exact when P is outside the polygon; inside,
-// R = D), then R, 2 - R, K(R) and K(1) - K(R) from FP64.  Per edge: D, A,
-// T0, T1, B^2, B^2 - 1, 4 - B^2 and A^2 - rho^2 in FP64 (one rounding each),
-// the quadrature nodes in FP32.  The estimated error 12 eps times the sum of
-// the magnitudes of the non-negative pieces flags the pair for the FP64 pass
-// when it exceeds tol |w| + 1e-14; so does a face plane through P.
-__global__ void __launch_bounds__(128) k_map_fp32(int64_t npairs, const int32_t *__restrict__ pi,
-                                                  const int32_t *__restrict__ pj, const double *__restrict__ x,
-                                                  const double *__restrict__ y, const double *__restrict__ z,
-                                                  const double *__restrict__ h, const double *__restrict__ gen,
-                                                  const double *__restrict__ radius, const int64_t *__restrict__ cfo,
-                                                  const int64_t *__restrict__ fvo, const PlaneD *__restrict__ plane,
-                                                  const EdgeD *__restrict__ edge, const PlaneF *__restrict__ plane_f,
-                                                  const EdgeF *__restrict__ edge_f, float tol, double *__restrict__ w,
-                                                  int32_t *__restrict__ flagged, int *__restrict__ nflag)
+// FP32 bulk pass (quadrature form, see quad32.cuh).
+//
+// A warp maps 32 consecutive pairs (mostly of one cell, since pairs are
+// sorted by cell), one pair per lane for the geometry: per face the FP64
+// plane distance D and an FP32 pass for the reference R = distance from p to
+// the face polygon (any value used consistently for the face is exact when P
+// is outside the polygon; inside, R = D), then R, 2 - R, K(R) and K(1) - K(R)
+// from FP64; per edge D, A, T0, T1, B^2, B^2 - 1, 4 - B^2 and A^2 - rho^2 in
+// FP64 (one rounding each).  Each edge yields up to four quadrature segments,
+// which the lane appends to its column of a per-warp queue in shared memory;
+// whenever a lane's column may overflow, the warp evaluates all queued
+// segments together, one segment per lane, so that the node loop runs with
+// the warp converged whatever the pairs' geometry.  Each lane then adds its
+// own segments' results in the order it queued them, which keeps the result
+// bit-reproducible.  The estimated error 12 eps times the sum of the
+// magnitudes of the non-negative pieces flags the pair for the FP64 pass when
+// it exceeds tol |w| + 1e-14; so does a face plane through P.
+namespace {
+
+constexpr int MQ_SLOTS = 12;   // segments a lane holds between evaluations
+constexpr int MQ_WARPS = 2;    // warps per block
+constexpr unsigned FULL_MASK = 0xffffffffu;
+
+struct SegQueue {
+    float sa[MQ_SLOTS][32], hl[MQ_SLOTS][32], A[MQ_SLOTS][32], B2[MQ_SLOTS][32], c4[MQ_SLOTS][32];
+    float dd[MQ_SLOTS][32], Rr[MQ_SLOTS][32], vv[MQ_SLOTS][32], add[MQ_SLOTS][32], scale[MQ_SLOTS][32];
+    float res[MQ_SLOTS][32];
+    int meta[MQ_SLOTS][32];
+    int pre[33];
+};
+
+// Evaluate every queued segment of the warp, then add each lane's own results
+// to its pair in queue order.  Called with the warp converged.
+__device__ __forceinline__ void mq_flush(SegQueue &q, int lane, int cnt, double &acc, double &mag)
 {
-    int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-    if (k >= npairs) return;
-    const int i = pi[k], j = pj[k];
-    const double rx = x[i] - gen[3 * j], ry = y[i] - gen[3 * j + 1], rz = z[i] - gen[3 * j + 2];
-    const double hh = h[i], ih = 1.0 / hh;
-    const float rxf = (float)rx, ryf = (float)ry, rzf = (float)rz, ihf = (float)ih;
-    const int64_t f0 = cfo[j], f1 = cfo[j + 1];
-    bool inside = true;
-    for (int64_t f = f0; f < f1; ++f) {
-        PlaneD pl = plane[f];
-        inside = inside && !(pl.w - (pl.x * rx + pl.y * ry + pl.z * rz) < 0.0);
+    int x = cnt;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        int y = __shfl_up_sync(FULL_MASK, x, o);
+        if (lane >= o) x += y;
     }
-    const bool full = inside && (sqrt(rx * rx + ry * ry + rz * rz) + radius[j] < 2.0 * hh);
+    const int total = __shfl_sync(FULL_MASK, x, 31);
+    q.pre[lane + 1] = x;
+    if (lane == 0) q.pre[0] = 0;
+    __syncwarp();
+    for (int t = lane; t < total; t += 32) {
+        int lo = 0, hi = 32;   // pre[lo] <= t < pre[hi]
+#pragma unroll
+        for (int it = 0; it < 5; ++it) {
+            const int mid = (lo + hi) >> 1;
+            if (q.pre[mid] <= t) lo = mid;
+            else hi = mid;
+        }
+        const int sl = t - q.pre[lo];
+        q.res[sl][lo] = emq::seg_eval(q.sa[sl][lo], q.hl[sl][lo], q.A[sl][lo], q.B2[sl][lo], q.c4[sl][lo],
+                                      q.dd[sl][lo], q.Rr[sl][lo], q.vv[sl][lo], q.add[sl][lo], q.meta[sl][lo]);
+    }
+    __syncwarp();
+    for (int sl = 0; sl < cnt; ++sl) {
+        const double v = (double)q.scale[sl][lane] * (double)q.res[sl][lane];
+        acc += v;
+        mag += fabs(v);
+    }
+    __syncwarp();
+}
+
+// Face constants of the lane's current face.
+struct FaceState {
+    double D64, rr2, dm1, d4;   // D, rho^2, D^2 - 1, 4 - D^2 (units of h)
+    float Df, R, v, KR, C1;     // v = 2 - R
+    float sign;   // orientation of the face as seen from P (sign of the signed distance)
+};
+
+// 1/x in FP64 from the FP32 reciprocal and one Newton step (relative error
+// about 1e-14; x is a positive O(1) quantity here)
+__device__ __forceinline__ double rcp64(double x)
+{
+    const double r = (double)(1.f / (float)x);
+    return r * (2.0 - x * r);
+}
+
+// Face constants from R^2 (FP64): R, v = 2 - R, K(R) (or K~(R)) and, for
+// R < 1, K(1) - K(R), evaluated in FP64 from factored forms (no FP64 divide
+// or square root: Newton steps from FP32 seeds) and rounded once.
+__device__ __forceinline__ void face_consts(double R2, bool tilde, FaceState &fs)
+{
+    const float Rf = sqrtf((float)R2);
+    const double R = Rf > 0.f ? (double)Rf + (R2 - (double)Rf * (double)Rf) * (double)(0.5f / Rf) : 0.0;
+    const double iR = R > 0.0 ? rcp64(R) : 0.0;
+    fs.R = (float)R;
+    if (R < 1.0) {
+        // K1(1) - K1(R) = (1 - R^2) [1/6 - 3 (1 + R^2)/40 + S5(1, R)/(40 (1 + R))]
+        const double i1 = rcp64(1.0 + R);
+        const double s5 = 1.0 + R * (1.0 + R * (1.0 + R * (1.0 + R)));
+        const double phf = (1.0 / 6.0) - 0.075 * (1.0 + R2) + 0.025 * s5 * i1;
+        const double om = 1.0 - R2;
+        fs.v = (float)(2.0 - R);
+        if (tilde) {
+            const double c1 = om * (0.25 * iR * i1 - phf);
+            fs.C1 = (float)c1;
+            fs.KR = (float)(-(1.0 / 60.0) - c1);
+        } else {
+            fs.C1 = (float)(om * phf);
+            fs.KR = (float)(R2 * ((1.0 / 6.0) - R2 * (0.075 - 0.025 * R)));
+        }
+        return;
+    }
+    fs.C1 = 0.f;
+    if (R >= 2.0) {
+        fs.v = 0.f;
+        fs.KR = tilde ? 0.f : (float)(0.35 - 0.25 * iR);
+        return;
+    }
+    const double v = (4.0 - R2) * rcp64(2.0 + R);
+    const double kt2 = -(v * v) * (v * v) * v * (1.0 + R) * iR * (1.0 / 120.0);
+    fs.v = (float)v;
+    fs.KR = (float)(tilde ? kt2 : 0.35 - 0.25 * iR - kt2);
+}
+
+// Queue the kernel pieces of (D/pi) int over |tau| in [ua, ub] (one g-integral
+// of an edge) with the signed factor sc; the part beyond 2h is added directly.
+__device__ __forceinline__ void mq_push_g(SegQueue &q, int lane, int &cnt, float ua, float ub, float A, float B2,
+                                          float c1, float c4, float cc, float sc, const FaceState &fs, bool tilde,
+                                          double &acc, double &mag)
+{
+    const float t1 = c1 < 0.f ? sqrtf(-c1) : 0.f;
+    const float t2 = c4 > 0.f ? sqrtf(c4) : 0.f;
+    const float iA = 1.f / A;
+    const int tflag = tilde ? emq::SEG_TILDE : 0;
+#pragma unroll
+    for (int piece = 1; piece <= 2; ++piece) {
+        const float a = piece == 1 ? ua : fmaxf(ua, t1);
+        const float b = piece == 1 ? fminf(ub, t1) : fminf(ub, t2);
+        if (b > a) {
+            const float s0 = asinhf(a * iA), s1 = asinhf(b * iA);
+            const float len = s1 - s0;
+            const int m = len > 2.f ? (int)ceilf(0.5f * len) : 1;
+            q.sa[cnt][lane] = s0;
+            q.hl[cnt][lane] = 0.5f * len / (float)m;
+            q.A[cnt][lane] = A;
+            q.B2[cnt][lane] = B2;
+            q.c4[cnt][lane] = c4;
+            const bool ref1 = piece == 2 && fs.R < 1.f;   // difference split at Q = 1
+            q.dd[cnt][lane] = ref1 ? c1 : cc;
+            q.Rr[cnt][lane] = ref1 ? 1.f : fs.R;
+            q.vv[cnt][lane] = ref1 ? 1.f : fs.v;
+            q.add[cnt][lane] = ref1 ? fs.C1 : 0.f;
+            q.scale[cnt][lane] = sc;
+            q.meta[cnt][lane] = m | (piece == 1 ? emq::SEG_PIECE1 : 0) | tflag;
+            ++cnt;
+        }
+    }
+    if (tilde) {   // beyond 2h: K~(Q) = 0, the integrand is -K~(R) >= 0
+        const float a = fmaxf(ua, t2), b = ub;
+        if (b > a) {
+            const double v = (double)sc * (double)(-fs.KR * atan2f((b - a) * A, A * A + a * b));
+            acc += v;
+            mag += fabs(v);
+        }
+    }
+}
+
+}  // namespace
+
+__global__ void __launch_bounds__(32 * MQ_WARPS) k_map_fp32(int64_t npairs, const int32_t *__restrict__ pi,
+                                                        const int32_t *__restrict__ pj, const double *__restrict__ x,
+                                                        const double *__restrict__ y, const double *__restrict__ z,
+                                                        const double *__restrict__ h, const double *__restrict__ gen,
+                                                        const double *__restrict__ radius,
+                                                        const int64_t *__restrict__ cfo, const int64_t *__restrict__ fvo,
+                                                        const PlaneD *__restrict__ plane,
+                                                        const EdgeD *__restrict__ edge,
+                                                        const EdgeF *__restrict__ edge_f, float tol,
+                                                        double *__restrict__ w, int32_t *__restrict__ flagged,
+                                                        int *__restrict__ nflag)
+{
+    __shared__ SegQueue queues[MQ_WARPS];
+    SegQueue &q = queues[threadIdx.x >> 5];
+    const int lane = threadIdx.x & 31;
+    const int64_t k0 = (blockIdx.x * (int64_t)MQ_WARPS + (threadIdx.x >> 5)) * 32;
+    if (k0 >= npairs) return;   // the whole warp
+    const int64_t k = k0 + lane;
+    const bool valid = k < npairs;
+
+    double rx = 0.0, ry = 0.0, rz = 0.0, hh = 1.0;
+    int64_t f = 0, f1 = 0;
+    bool inside = false, full = false;
+    if (valid) {
+        const int i = pi[k], j = pj[k];
+        rx = x[i] - gen[3 * j];
+        ry = y[i] - gen[3 * j + 1];
+        rz = z[i] - gen[3 * j + 2];
+        hh = h[i];
+        f = cfo[j];
+        f1 = cfo[j + 1];
+        inside = true;
+        for (int64_t g = f; g < f1; ++g) {
+            PlaneD pl = plane[g];
+            inside = inside && !(pl.w - (pl.x * rx + pl.y * ry + pl.z * rz) < 0.0);
+        }
+        full = inside && (sqrt(rx * rx + ry * ry + rz * rz) + radius[j] < 2.0 * hh);
+    }
+    const double ih = 1.0 / hh;
+    const float rxf = (float)rx, ryf = (float)ry, rzf = (float)rz, ihf = (float)ih;
+    const bool tilde = !full;
+
     double acc = 0.0, mag = 0.0;
     bool force = false;   // the FP32 form does not apply: recompute in FP64
-    for (int64_t f = f0; f < f1; ++f) {
-        PlaneD pl = plane[f];
-        const double sd = pl.w - (pl.x * rx + pl.y * ry + pl.z * rz);
-        const double D64 = fabs(sd) * ih;
-        // P in (or within underflow of) the face plane: in the complement
-        // form such a face would carry half of the kernel, so leave it to FP64
-        if (!full && D64 < 1e-30) force = true;
-        if (sd == 0.0 || (!full && D64 >= 2.0)) continue;
-        const int64_t e0 = fvo[f], e1 = fvo[f + 1];
-        // reference distance to the polygon (FP32)
-        bool inpoly = true;
-        float rho2 = INFINITY;
-        for (int64_t e = e0; e < e1; ++e) {
-            EdgeF E = edge_f[e];
-            float a = (E.cm - (E.mx * rxf + E.my * ryf + E.mz * rzf)) * ihf;
-            float t0 = (E.ce - (E.ex * rxf + E.ey * ryf + E.ez * rzf)) * ihf;
-            float t1 = t0 + E.L * ihf;
-            inpoly = inpoly && a > 0.f;
-            float tc = t0 > 0.f ? t0 : (t1 < 0.f ? t1 : 0.f);
-            rho2 = fminf(rho2, a * a + tc * tc);
+    int cnt = 0;
+    const int nface = valid ? (int)(f1 - f) : 0;
+    // faces and edges in lockstep across the warp: consecutive pairs mostly
+    // share their cell, so the FP64 geometry runs with the lanes converged
+    for (int fi = 0; __any_sync(FULL_MASK, fi < nface); ++fi) {
+        int64_t e0 = 0;
+        int ne = 0;
+        FaceState fs{};
+        if (fi < nface) {
+            const int64_t g = f + fi;
+            PlaneD pl = plane[g];
+            const double sd = pl.w - (pl.x * rx + pl.y * ry + pl.z * rz);
+            const double D64 = fabs(sd) * ih;
+            // P in (or within underflow of) the face plane: in the complement
+            // form such a face would carry half of the kernel
+            if (tilde && D64 < 1e-30) force = true;
+            if (!(sd == 0.0 || (tilde && D64 >= 2.0))) {
+                // reference distance to the polygon (FP32)
+                const int64_t g0 = fvo[g], g1 = fvo[g + 1];
+                bool inpoly = true;
+                float rho2 = INFINITY;
+                for (int64_t q1 = g0; q1 < g1; ++q1) {
+                    EdgeF E = edge_f[q1];
+                    float a = (E.cm - (E.mx * rxf + E.my * ryf + E.mz * rzf)) * ihf;
+                    float t0 = (E.ce - (E.ex * rxf + E.ey * ryf + E.ez * rzf)) * ihf;
+                    float t1 = t0 + E.L * ihf;
+                    inpoly = inpoly && a > 0.f;
+                    float tc = t0 > 0.f ? t0 : (t1 < 0.f ? t1 : 0.f);
+                    rho2 = fminf(rho2, a * a + tc * tc);
+                }
+                const double rr2 = inpoly ? 0.0 : (double)rho2;
+                const double R2 = D64 * D64 + rr2;
+                if (!(tilde && R2 >= 4.0)) {   // else the polygon lies entirely beyond 2h
+                    fs.D64 = D64;
+                    fs.rr2 = rr2;
+                    fs.dm1 = D64 * D64 - 1.0;
+                    fs.d4 = 4.0 - D64 * D64;
+                    fs.Df = (float)D64;
+                    face_consts(R2, tilde, fs);
+                    fs.sign = sd > 0.0 ? 1.f : -1.f;
+                    e0 = g0;
+                    ne = (int)(g1 - g0);
+                }
+            }
         }
-        const float Df = (float)D64;
-        const double rr2 = inpoly ? 0.0 : (double)rho2;
-        const double R2 = D64 * D64 + rr2;
-        if (!full && R2 >= 4.0) continue;   // the polygon lies entirely beyond 2h
-        const double R64 = sqrt(R2);
-        emq::FaceRef fr;
-        fr.tilde = !full;
-        fr.R = (float)R64;
-        fr.R2 = fr.R * fr.R;
-        fr.R3 = fr.R2 * fr.R;
-        fr.R4 = fr.R2 * fr.R2;
-        fr.v = (float)(2.0 - R64);
-        fr.v2 = fr.v * fr.v;
-        fr.v3 = fr.v2 * fr.v;
-        fr.v4 = fr.v2 * fr.v2;
-        fr.KR = (float)(full ? em::K_of(R64) : em::K_tilde(R64));
-        fr.C1 = R64 < 1.0 ? (float)(full ? em::K_of(1.0) - em::K_of(R64) : em::K_tilde(1.0) - em::K_tilde(R64)) : 0.f;
-        float fs = 0.f, fm = 0.f;
-        for (int64_t e = e0; e < e1; ++e) {
-            EdgeD E = edge[e];
-            const double a = (E.cm - (E.mx * rx + E.my * ry + E.mz * rz)) * ih;
-            if (a == 0.0) continue;
-            const double t0 = (E.ce - (E.ex * rx + E.ey * ry + E.ez * rz)) * ih;
-            const double t1 = t0 + E.L * ih;
-            const double B2 = D64 * D64 + a * a;
-            emq::EdgeRef er;
-            er.cc = (float)(a * a - rr2);
-            er.c1 = (float)(B2 - 1.0);
-            er.c4 = (float)(4.0 - B2);
-            float mg;
-            const float v = emq::edge_q(Df, (float)fabs(a), (float)t0, (float)t1, (float)B2, fr, er, mg);
-            fs += a > 0.0 ? v : -v;
-            fm += mg;
+        for (int ei = 0; __any_sync(FULL_MASK, ei < ne); ++ei) {
+            if (ei < ne) {
+                EdgeD E = edge[e0 + ei];
+                const double a = (E.cm - (E.mx * rx + E.my * ry + E.mz * rz)) * ih;
+                if (a != 0.0) {
+                    const double t0 = (E.ce - (E.ex * rx + E.ey * ry + E.ez * rz)) * ih;
+                    const double t1 = t0 + E.L * ih;
+                    const float A = (float)fabs(a), T0 = (float)t0, T1 = (float)t1;
+                    const float B2f = fs.Df * fs.Df + A * A;
+                    const float c1 = (float)(fs.dm1 + a * a), c4 = (float)(fs.d4 - a * a),
+                                cc = (float)(a * a - fs.rr2);
+                    // signed factor: D/pi, face orientation, side of the edge line, direction along it
+                    const float base = fs.sign * (a > 0.0 ? 1.f : -1.f) * fs.Df * 0.31830988618379067154f;
+                    if ((T0 >= 0.f && T1 >= 0.f) || (T0 <= 0.f && T1 <= 0.f)) {
+                        const float u0 = fabsf(T0), u1 = fabsf(T1);
+                        mq_push_g(q, lane, cnt, fminf(u0, u1), fmaxf(u0, u1), A, B2f, c1, c4, cc,
+                                  T1 >= T0 ? base : -base, fs, tilde, acc, mag);
+                    } else {
+                        const float sc = T1 > T0 ? base : -base;
+                        mq_push_g(q, lane, cnt, 0.f, fabsf(T0), A, B2f, c1, c4, cc, sc, fs, tilde, acc, mag);
+                        mq_push_g(q, lane, cnt, 0.f, fabsf(T1), A, B2f, c1, c4, cc, sc, fs, tilde, acc, mag);
+                    }
+                }
+            }
+            // an edge queues at most four segments
+            if (__any_sync(FULL_MASK, cnt > MQ_SLOTS - 4)) {
+                mq_flush(q, lane, cnt, acc, mag);
+                cnt = 0;
+            }
         }
-        acc += sd > 0.0 ? (double)fs : -(double)fs;
-        mag += (double)fm;
     }
+    if (__any_sync(FULL_MASK, cnt > 0)) mq_flush(q, lane, cnt, acc, mag);
+    if (!valid) return;
+    // the integrals were summed with their signs: w = sum (full kernel) or
+    // [P inside] - sum (complement kernel)
     const double wk = full ? acc : ((inside ? 1.0 : 0.0) - acc);
     if (inside && !full) mag += 1.0;
     w[k] = wk;
@@ -482,10 +679,9 @@ EM_EXPORT int map_exact(em_ctx *ctx, const em_pairs *pr, const double *d_x, cons
             EM_TRY(tmp.alloc(&flagged, n));
             EM_TRY(tmp.alloc(&nflag, 1));
             EM_CUDA(cudaMemsetAsync(nflag, 0, sizeof(int), ctx->stream));
-            k_map_fp32<<<em_grid(n, block), block, 0, ctx->stream>>>(
+            k_map_fp32<<<em_grid((n + 31) / 32, MQ_WARPS), 32 * MQ_WARPS, 0, ctx->stream>>>(
                 n, pr->pair_i, pr->pair_j, d_x, d_y, d_z, d_h, v->gen, v->radius, v->cell_face_off,
-                v->face_vert_off, v->plane, v->edge, v->plane_f, v->edge_f, (float)p->fp64_threshold, d_w_out,
-                flagged, nflag);
+                v->face_vert_off, v->plane, v->edge, v->edge_f, (float)p->fp64_threshold, d_w_out, flagged, nflag);
             EM_LAUNCHED(ctx);
             int hflag = 0;
             EM_CUDA(cudaMemcpyAsync(&hflag, nflag, sizeof(int), cudaMemcpyDeviceToHost, ctx->stream));

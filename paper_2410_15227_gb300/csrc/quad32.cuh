@@ -14,9 +14,9 @@
 // Substituting tau = A sinh(s) turns A dtau/(A^2 + tau^2) into ds/cosh(s):
 //     (D/pi) int [K~(Q(s)) - K~(R)] / cosh(s) ds,  Q(s)^2 = D^2 + A^2 cosh^2 s,
 // an integrand that is smooth on the scale of s = 1 however small A is; it is
-// integrated by 8-point Gauss-Legendre on pieces of length <= 2 in s, split
-// at the kernel's breakpoints Q = 1 and Q = 2.  Beyond Q = 2, K~(Q) = 0 and
-// the piece is -K~(R) times an angle, taken analytically.
+// integrated by 8-point Gauss-Legendre on sub-pieces of length <= 2 in s,
+// split at the kernel's breakpoints Q = 1 and Q = 2.  Beyond Q = 2, K~(Q) = 0
+// and the piece is -K~(R) times an angle, taken analytically.
 //
 // Every piece of the integrand K(Q) - K(R) is formed as an exact factored
 // difference, so that its FP32 value keeps a relative error of a few ulp
@@ -30,8 +30,8 @@
 //                                                  + v^4 (1 + 2/(Q R))],
 //              a sum of positive terms, and K2 = K3 - K~2 with
 //              K3(Q) - K3(R) = d/(4 Q R (Q + R));
-//   R < 1 <= Q: the difference is split at Q = 1, the constant
-//              K(1) - K(R) taken in FP64;
+//   R < 1 <= Q: the difference is split at Q = 1 (the same formula with R
+//              replaced by 1), the constant K(1) - K(R) taken in FP64;
 // where d = Q^2 - R^2 = c + tau^2 with c = A^2 - rho^2 per edge in FP64
 // (rho the in-plane distance from the foot to the polygon),
 // S4(u, v) = u^3 + u^2 v + u v^2 + v^3, S5(Q, R) = Q^4 + Q^3 R + ... + R^4,
@@ -40,6 +40,11 @@
 //
 // The same quadrature integrates the full kernel (K instead of K~) for a
 // particle inside a cell that lies entirely within 2h of it.
+//
+// Work is organised in segments: one segment is one kernel piece of one edge
+// (an s-interval cut into m sub-pieces of 8 nodes each) with everything its
+// integrand needs, so that a warp can evaluate the segments of 32 different
+// pairs side by side with one copy of the node loop.
 #pragma once
 
 #include <cuda_runtime.h>
@@ -57,58 +62,28 @@ __device__ __forceinline__ float gl_w(int i)
                                                                                   : 0.10122853629037706f;
 }
 
-// Reference data of one face: R (distance to the polygon, units of h),
-// powers of R and of v = 2 - R, K(R) (or K~(R)) and, for R < 1, the constant
-// K(1) - K(R), all from FP64.
-struct FaceRef {
-    float R, R2, R3, R4;
-    float v, v2, v3, v4;
-    float KR, C1;
-    bool tilde;   // complement kernel K~ (false: full kernel K)
-};
-// Per-edge constants from FP64: c = A^2 - rho^2, c1 = B^2 - 1, c4 = 4 - B^2.
-struct EdgeRef {
-    float cc, c1, c4;
-};
+// Segment fields (see the header comment):
+//   sa, hl  start of the first sub-piece, half-length of every sub-piece
+//   A, B2   A and B^2 of the edge;  c4 = 4 - B^2 (piece 2)
+//   dd      Q^2 - Rr^2 - tau^2: A^2 - rho^2, or B^2 - 1 when Rr = 1
+//   Rr      reference distance of the difference (R, or 1)
+//   v       2 - Rr, computed where it keeps its relative precision (piece 2)
+//   add     constant added to the difference: K(1) - K(R) when Rr = 1, else 0
+//   meta    m | piece1 << 8 | tilde << 9
+constexpr int SEG_PIECE1 = 1 << 8;
+constexpr int SEG_TILDE = 1 << 9;
 
-// K~2(Q) - K~2(Rr) for Q, Rr in [1, 2); u = 2 - Q, v = 2 - Rr, d = Q^2 - Rr^2
-__device__ __forceinline__ float dkt2(float Q, float iQ, float u, float d, float Rr, float v, float v2, float v3,
-                                      float v4)
+// int over the segment of [K(Q(s)) - K(R)] / cosh(s) ds
+__device__ __forceinline__ float seg_eval(float sa, float hl, float A, float B2, float c4, float dd, float Rr,
+                                          float vr, float add, int meta)
 {
-    const float S4 = ((u + v) * u + v2) * u + v3;
-    const float br = u * S4 * (1.f + iQ) + v4 * (1.f + __fdividef(2.f * iQ, Rr));
-    return __fdividef(d, 120.f * (Q + Rr)) * br;
-}
-
-// K(Q) - K(R) (K~ or K) at one node; piece 1: Q < 1, piece 2: 1 <= Q < 2
-__device__ __forceinline__ float dk(float Q, float t2, bool piece1, const FaceRef &fr, const EdgeRef &er)
-{
-    if (piece1) {
-        const float d = er.cc + t2;
-        const float iq = __fdividef(1.f, Q + fr.R);
-        const float s5 = (((Q + fr.R) * Q + fr.R2) * Q + fr.R3) * Q + fr.R4;
-        const float phf = (1.f / 6.f) - 0.075f * (Q * Q + fr.R2) + 0.025f * s5 * iq;
-        return fr.tilde ? d * (__fdividef(0.25f * iq, Q * fr.R) - phf) : d * phf;
-    }
-    const float iQ = __fdividef(1.f, Q);
-    const float u = __fdividef(er.c4 - t2, 2.f + Q);
-    if (fr.R >= 1.f) {
-        const float d = er.cc + t2;
-        const float x = dkt2(Q, iQ, u, d, fr.R, fr.v, fr.v2, fr.v3, fr.v4);
-        return fr.tilde ? x : __fdividef(d * iQ, 4.f * fr.R * (Q + fr.R)) - x;
-    }
-    const float d1 = er.c1 + t2;
-    const float x = dkt2(Q, iQ, u, d1, 1.f, 1.f, 1.f, 1.f, 1.f);
-    return (fr.tilde ? x : __fdividef(d1 * iQ, 4.f * (Q + 1.f)) - x) + fr.C1;
-}
-
-// int_{sa}^{sb} [K(Q(s)) - K(R)] / cosh(s) ds on one kernel piece
-__device__ __forceinline__ float seg(float sa, float sb, float A, float B2, bool piece1, const FaceRef &fr,
-                                     const EdgeRef &er)
-{
-    const float len = sb - sa;
-    const int m = len > 2.f ? (int)ceilf(0.5f * len) : 1;
-    const float hl = 0.5f * len / (float)m;
+    const int m = meta & 255;
+    const bool piece1 = (meta & SEG_PIECE1) != 0;
+    const bool tilde = (meta & SEG_TILDE) != 0;
+    const float R2 = Rr * Rr;
+    // piece 1: powers of R; piece 2: powers of v = 2 - Rr
+    const float v = piece1 ? Rr : vr;
+    const float p2 = v * v, p3 = p2 * v, p4 = p2 * p2;
     float tot = 0.f;
     for (int p = 0; p < m; ++p) {
         const float mid = sa + (2.f * p + 1.f) * hl;
@@ -123,51 +98,26 @@ __device__ __forceinline__ float seg(float sa, float sb, float A, float B2, bool
             const float tau = 0.5f * A * (em * (1.f + ei));
             const float t2 = tau * tau;
             const float Q = sqrtf(B2 + t2);
-            acc += gl_w(i >> 1) * __fdividef(dk(Q, t2, piece1, fr, er), ch);
+            const float d = dd + t2;
+            float f;
+            if (piece1) {
+                const float iq = __fdividef(1.f, Q + Rr);
+                const float s5 = (((Q + Rr) * Q + p2) * Q + p3) * Q + p4;
+                const float phf = (1.f / 6.f) - 0.075f * (Q * Q + R2) + 0.025f * s5 * iq;
+                f = tilde ? d * (__fdividef(0.25f * iq, Q * Rr) - phf) : d * phf;
+            } else {
+                const float iQ = __fdividef(1.f, Q);
+                const float u = __fdividef(c4 - t2, 2.f + Q);
+                const float S4 = ((u + v) * u + p2) * u + p3;
+                const float br = u * S4 * (1.f + iQ) + p4 * (1.f + __fdividef(2.f * iQ, Rr));
+                const float x = __fdividef(d, 120.f * (Q + Rr)) * br;
+                f = (tilde ? x : __fdividef(d * iQ, 4.f * Rr * (Q + Rr)) - x) + add;
+            }
+            acc += gl_w(i >> 1) * __fdividef(f, ch);
         }
         tot += acc * hl;
     }
     return tot;
-}
-
-// (D/pi) int over |tau| in [ua, ub] of [K(Q) - K(R)] A/(A^2 + tau^2) dtau (>= 0)
-__device__ __forceinline__ float g_int(float ua, float ub, float A, float D, float B2, const FaceRef &fr,
-                                       const EdgeRef &er)
-{
-    const float t1 = er.c1 < 0.f ? sqrtf(-er.c1) : 0.f;
-    const float t2 = er.c4 > 0.f ? sqrtf(er.c4) : 0.f;
-    const float iA = 1.f / A;
-    float tot = 0.f;
-    {
-        float a = ua, b = fminf(ub, t1);
-        if (b > a) tot += seg(asinhf(a * iA), asinhf(b * iA), A, B2, true, fr, er);
-    }
-    {
-        float a = fmaxf(ua, t1), b = fminf(ub, t2);
-        if (b > a) tot += seg(asinhf(a * iA), asinhf(b * iA), A, B2, false, fr, er);
-    }
-    if (fr.tilde) {   // beyond 2h: K~(Q) = 0, so the integrand is -K~(R) >= 0
-        float a = fmaxf(ua, t2), b = ub;
-        if (b > a) tot -= fr.KR * atan2f((b - a) * A, A * A + a * b);
-    }
-    return tot * D * 0.31830988618379067154f;
-}
-
-// Edge from T0 to T1 along its line (signed, tau measured from the foot F).
-// Returns the signed edge integral; mag receives the sum of the magnitudes
-// of the non-negative pieces it is made of.
-__device__ __forceinline__ float edge_q(float D, float A, float T0, float T1, float B2, const FaceRef &fr,
-                                        const EdgeRef &er, float &mag)
-{
-    if ((T0 >= 0.f && T1 >= 0.f) || (T0 <= 0.f && T1 <= 0.f)) {
-        float u0 = fabsf(T0), u1 = fabsf(T1);
-        float v = g_int(fminf(u0, u1), fmaxf(u0, u1), A, D, B2, fr, er);
-        mag = v;
-        return T1 >= T0 ? v : -v;
-    }
-    float v = g_int(0.f, fabsf(T0), A, D, B2, fr, er) + g_int(0.f, fabsf(T1), A, D, B2, fr, er);
-    mag = v;
-    return T1 > T0 ? v : -v;
 }
 
 }  // namespace emq

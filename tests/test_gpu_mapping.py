@@ -77,10 +77,11 @@ def test_map_exact_fp64_parity(ctx, case):
     assert nf == 0
 
 
-def test_map_exact_deterministic(ctx, case):
-    _, _, (a, ra, ua, _) = run_gpu(ctx, case, 0)
-    _, _, (b, rb, ub, _) = run_gpu(ctx, case, 0)
-    assert torch.equal(a, b) and torch.equal(ra, rb) and torch.equal(ua, ub)
+@pytest.mark.parametrize("precision", [0, 1])
+def test_map_exact_deterministic(ctx, case, precision):
+    _, _, (a, ra, ua, na) = run_gpu(ctx, case, precision, 1e-5)
+    _, _, (b, rb, ub, nb) = run_gpu(ctx, case, precision, 1e-5)
+    assert torch.equal(a, b) and torch.equal(ra, rb) and torch.equal(ua, ub) and na == nb
 
 
 def test_map_exact_mixed(ctx, case):
