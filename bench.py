@@ -144,6 +144,7 @@ def run_ours(args, rank, world):
                    fp64_threshold=args.fp64_threshold)
     stream = torch.cuda.current_stream(device)
     map_ms = []
+    kernel_ms = []   # (main pass, FP64 recompute) of each timed map_exact, from the library's events
 
     pseudo = WORKLOADS[args.workload][1]
 
@@ -160,10 +161,12 @@ def run_ours(args, rank, world):
         if record:
             e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
             e0.record(stream)
-        wts, rho, wsum, nf = api.map_exact(ctx, pr, g["x"], g["y"], g["z"], g["h"], g["m"], vor, P)
+        wts, rho, wsum, nf = api.map_exact(ctx, pr, g["x"], g["y"], g["z"], g["h"], g["m"], vor, P,
+                                           want_count=not record)
         if record:
             e1.record(stream)
             map_ms.append((e0, e1))
+            kernel_ms.append(ctx.map_times())
         f, fp = api.map_back(ctx, pr, wts, fc, ps, tree)
         return dict(npairs=pr.info()[0], npseudo=ps.info()[0] if pseudo else w.n, nfp64=nf, rho=rho, fp=fp, wsum=wsum,
                     w=wts, pr=pr, g=g, vor=vor)
@@ -212,6 +215,7 @@ def run_ours(args, rank, world):
     torch.cuda.synchronize()
     clocks = ClockSampler(dev_index)
     clocks.start()
+    ctx.set_timing(True)
     launches0 = ctx.launches
     step_ms, npairs = [], 0
     for _ in range(args.steps):
@@ -226,15 +230,12 @@ def run_ours(args, rank, world):
     if world > 1:
         torch.distributed.barrier()
     ck = clocks.stop()
+    ctx.set_timing(False)
     launches = ctx.launches - launches0
     t_ms = sum(a.elapsed_time(b) for a, b in step_ms)
     t_map = [a.elapsed_time(b) for a, b in map_ms[-args.steps:]]
-    tmax = t_ms
-    if world > 1:
-        tt = torch.tensor([t_ms], device=device)
-        torch.distributed.all_reduce(tt, op=torch.distributed.ReduceOp.MAX)
-        tmax = float(tt.item())
-    value = npairs * world / (tmax * 1e-3)
+    tmax, units = reduce_over_ranks(t_ms, npairs, world, device)
+    value = units / (tmax * 1e-3)
     res = dict(metric=METRIC, value=value, unit="pairs/s", n_gpus=world, steps=args.steps,
                warmup=args.warmup, ms_per_step=tmax / args.steps, higher_is_better=True,
                scaling="weak", vs_baseline=None,
@@ -246,30 +247,85 @@ def run_ours(args, rank, world):
                        "l2": "flushed between steps (258 MiB write)", "parallelism": f"replicas x{world}"},
                map_exact_ms=statistics.mean(t_map), map_exact_pairs_per_s=out["npairs"] / (statistics.mean(t_map) * 1e-3),
                accuracy=acc, gpu_launches=launches, clocks=ck)
-    res["roofline"] = roofline(out["npairs"], statistics.mean(t_map), args.precision)
+    k_main = statistics.mean(k[0] for k in kernel_ms)
+    k_re = statistics.mean(k[1] for k in kernel_ms)
+    res["map_exact_kernels_ms"] = {"main": k_main, "fp64_recompute": k_re}
+    res["roofline"] = roofline(out["npairs"], k_main, args.precision, args.workload)
     if not args.no_e2e:
         res["e2e"] = run_e2e(args, w, step, device)
     return res
 
 
-def roofline(npairs, ms, precision):
-    """Dominant kernel: the per-pair analytic integral (FP32 bulk pass in mixed
-    mode), bound by the FP32 pipe.  Algorithmic work per pair: FLOPS_PER_PAIR
-    (see the design doc); peak: 152 SMs x 128 FP32 lanes x 2 flop x 2.07 GHz."""
-    flops_per_pair = FLOPS_PER_PAIR_F32 if precision == "mixed" else FLOPS_PER_PAIR_F64
-    peak = 152 * 128 * 2 * 2.07e9 / 1e12 if precision == "mixed" else FP64_PEAK_TFLOPS
-    achieved = npairs * flops_per_pair / (ms * 1e-3) / 1e12
-    return {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
-            "frac": achieved / peak, "traffic": None,
-            "kernel": "k_map_fp32" if precision == "mixed" else "k_map_fp64",
-            "peak_source": "derived: 152 SMs x 128 FP32 lanes x 2 x 2.07 GHz"}
+def reduce_over_ranks(t_ms, units, world, device):
+    """Whole-job figures across ranks: the slowest rank's timed milliseconds
+    and the units (pairs) all ranks processed.  One process per GPU; on one
+    rank this is the identity."""
+    if world == 1:
+        return float(t_ms), float(units)
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([float(t_ms)], dtype=torch.float64, device=device)
+    u = torch.tensor([float(units)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    dist.all_reduce(u, op=dist.ReduceOp.SUM)
+    return float(t.item()), float(u.item())
 
 
-# FP32 operations per pair of the bulk pass and FP64 per pair of the FP64 pass,
-# counted on the 1e6-particle workload (DESIGN.md, measurement section)
-FLOPS_PER_PAIR_F32 = 1.0e4
-FLOPS_PER_PAIR_F64 = 1.0e4
+# Algorithmic work of map_exact per pair, per workload: the cell's faces, the
+# faces within reach (D < 2 and R < 2 in units of h) and their edges, and the
+# 8-node quadrature sub-pieces, averaged over random pairs of each workload
+# with a CPU model of the FP32 pass (6,000 pairs of the 1e6 cloud, 3,683 of
+# the 1e5 sphere).
+WORK = {
+    "pseudo_1e6": dict(faces=15.64, faces_used=11.33, edges_used=60.65, subpieces=58.54),
+    "sphere_1e5": dict(faces=15.23, faces_used=7.93, edges_used=43.36, subpieces=40.33),
+}
+# FP64 flops (FMA = 2) of the FP32 pass's geometry, counted in its source:
+# per face the inside test and the plane distance, per face within reach the
+# reference distance and the face constants, per edge of those faces A, T0,
+# T1 and the three per-edge constants
+FP64_FLOPS_FACE, FP64_FLOPS_USED_FACE, FP64_FLOPS_EDGE = 13, 36, 22
+# FP32 flops per quadrature node (common part 15, piece-2 integrand 21), with
+# expm1, sqrt and about six reciprocals on the SFU besides
+FP32_FLOPS_NODE = 36
+# nominal GB300 rates: FP64 1.25 TFLOP/s (152 SMs x 2 DFMA/clk x 2 x 2.07 GHz);
+# FP32 152 SMs x 128 lanes x 2 x 2.07 GHz
 FP64_PEAK_TFLOPS = 1.25
+FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.07e9 / 1e12
+# DRAM traffic of one k_map_fp32 launch per pair (ncu, dram__bytes_read.sum +
+# dram__bytes_write.sum over the pairs of the launch), per workload
+TRAFFIC_PER_PAIR = {"pseudo_1e6": 138.17, "sphere_1e5": 80.06}
+
+
+def roofline(npairs, ms, precision, workload):
+    """Dominant kernel of map_exact.  Mixed mode: the FP32 pass k_map_fp32,
+    whose binding pipe is FP64 (its geometry; ncu: FP64 pipe ~50% busy, FMA
+    ~10%), so the roofline is the FP64 rate with the FP64 flops counted above;
+    the FP32 quadrature's rate is reported beside it.  FP64 mode: the closed
+    form k_map_fp64, with the same geometry count over all faces and edges
+    (its transcendental calls are not counted)."""
+    wk = WORK[workload]
+    if precision == "mixed":
+        f64 = (FP64_FLOPS_FACE * wk["faces"] + FP64_FLOPS_USED_FACE * wk["faces_used"]
+               + FP64_FLOPS_EDGE * wk["edges_used"])
+        f32 = FP32_FLOPS_NODE * 8 * wk["subpieces"]
+    else:
+        edges_all = wk["edges_used"] * wk["faces"] / wk["faces_used"]
+        f64 = (FP64_FLOPS_FACE + FP64_FLOPS_USED_FACE) * wk["faces"] + FP64_FLOPS_EDGE * edges_all
+        f32 = 0.0
+    t = ms * 1e-3
+    achieved = npairs * f64 / t / 1e12
+    tr = TRAFFIC_PER_PAIR.get(workload) if precision == "mixed" else None
+    out = {"bound": "alu", "achieved": achieved, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
+           "frac": achieved / FP64_PEAK_TFLOPS, "traffic": tr * npairs if tr else None,
+           "kernel": "k_map_fp32" if precision == "mixed" else "k_map_fp64", "pipe": "fp64",
+           "flops_per_pair": f64, "kernel_ms": ms,
+           "peak_source": "nominal GB300 FP64 rate (152 SMs x 2 DFMA/clk x 2 flop x 2.07 GHz)"}
+    if f32:
+        a32 = npairs * f32 / t / 1e12
+        out["fp32_quadrature"] = {"achieved": a32, "peak": FP32_PEAK_TFLOPS, "frac": a32 / FP32_PEAK_TFLOPS,
+                                  "flops_per_pair": f32}
+    return out
 
 
 def run_e2e(args, w, step, device):

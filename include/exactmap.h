@@ -80,6 +80,15 @@ int em_ctx_sync(em_ctx *ctx);
 const char *em_last_error(void);
 /* Number of kernels the library has launched through this context so far. */
 int64_t em_ctx_launch_count(const em_ctx *ctx);
+/* Turn on (on != 0) or off the recording of CUDA events around the kernels
+ * of map_exact (creates the events on first use; costs two event records per
+ * pass).  Library bookkeeping for measurement, not part of the method. */
+int em_ctx_set_timing(em_ctx *ctx, int on);
+/* Device time of the last map_exact enqueued while timing was on: ms_main =
+ * the main pass (FP64 kernel, or the FP32 pass in mixed mode), ms_recompute =
+ * the FP64 recompute of flagged pairs (0 in FP64 mode).  Waits for the
+ * recorded events.  Both are 0 if nothing was recorded. */
+int em_ctx_map_times(em_ctx *ctx, double *ms_main, double *ms_recompute);
 
 /* ---- build_tree ------------------------------------------------------------
  * Morton-ordered octree of n particles (the paper's gravity tree, Section
@@ -181,9 +190,13 @@ int pairs_destroy(em_pairs *pr);
  *   rho_j = sum_i m_i w_ij / V_j   (deterministic, ascending i)
  *   u_i   = sum_j w_ij             (partition-of-unity check, ascending j).
  *   d_w_out[npairs], d_rho_out[ncell] (device); d_wsum_out[np] may be NULL.
- *   p->precision: 0 FP64; 1 FP32 bulk with compensated sums, pairs whose
- *   estimated error exceeds p->fp64_threshold recomputed in FP64.
- *   h_nfp64 (host, may be NULL): number of pairs recomputed in FP64. */
+ *   p->precision: 0 = FP64 closed form for every pair.  1 = mixed: an FP32
+ *   quadrature of each edge integral (FP64 edge geometry, per-pair sums in
+ *   FP64) with a per-pair error bound; pairs whose bound exceeds
+ *   p->fp64_threshold |w| + 1e-14, or whose particle lies in a face plane,
+ *   are recomputed with the FP64 closed form on the device.
+ *   h_nfp64 (host, may be NULL): number of pairs recomputed in FP64; passing
+ *   it makes the call wait for the mixed pass, NULL leaves it asynchronous. */
 int map_exact(em_ctx *ctx, const em_pairs *pr, const double *d_x, const double *d_y, const double *d_z,
               const double *d_h, const double *d_m, const em_voronoi *v, const em_params *p,
               double *d_w_out, double *d_rho_out, double *d_wsum_out, int64_t *h_nfp64);

@@ -73,6 +73,16 @@ class Context:
     def sync(self):
         N.call("em_ctx_sync", self.handle)
 
+    def set_timing(self, on: bool = True):
+        """Record CUDA events around the map_exact kernels (see map_times)."""
+        N.call("em_ctx_set_timing", self.handle, int(bool(on)))
+
+    def map_times(self):
+        """(main pass ms, FP64 recompute ms) of the last map_exact while timing was on."""
+        a, b = C.c_double(), C.c_double()
+        N.call("em_ctx_map_times", self.handle, C.byref(a), C.byref(b))
+        return a.value, b.value
+
     def close(self):
         if getattr(self, "handle", None):
             N.lib().em_ctx_destroy(self.handle)
@@ -258,8 +268,10 @@ def pairs_from_list(ctx: Context, pair_i, pair_j, np_: int, vor: Voronoi) -> Pai
 
 
 def map_exact(ctx: Context, pairs: Pairs, x, y, z, h_, m, vor: Voronoi, params: Params,
-              want_wsum: bool = True, out=None):
-    """Returns (w per pair, rho per cell, sum_j w_ij per particle or None, #pairs in FP64)."""
+              want_wsum: bool = True, out=None, want_count: bool = True):
+    """Returns (w per pair, rho per cell, sum_j w_ij per particle or None, #pairs in FP64).
+    The count makes the call wait for the mixed pass; want_count=False leaves
+    it asynchronous and returns None for the count."""
     npairs, np_, nc = pairs.info()
     if out is None:
         out = (ctx.empty(npairs), ctx.empty(nc), ctx.empty(np_) if want_wsum else None)
@@ -268,8 +280,9 @@ def map_exact(ctx: Context, pairs: Pairs, x, y, z, h_, m, vor: Voronoi, params: 
     p = params.native()
     N.call("map_exact", ctx.handle, pairs.handle, _ptr(x, f64, np_, "x"), _ptr(y, f64, np_, "y"),
            _ptr(z, f64, np_, "z"), _ptr(h_, f64, np_, "h"), _ptr(m, f64, np_, "m"), vor.handle,
-           C.byref(p), _ptr(w, f64, npairs), _ptr(rho, f64, nc), _ptr(wsum), C.byref(nfp64))
-    return w, rho, wsum, nfp64.value
+           C.byref(p), _ptr(w, f64, npairs), _ptr(rho, f64, nc), _ptr(wsum),
+           C.byref(nfp64) if want_count else None)
+    return w, rho, wsum, nfp64.value if want_count else None
 
 
 def map_back(ctx: Context, pairs: Pairs, w, f_cell, pseudo: Pseudo | None = None,

@@ -48,13 +48,50 @@ EM_EXPORT int em_ctx_create(em_ctx **ctx, int device, void *stream)
     c->device = device;
     c->stream = (cudaStream_t)stream;
     c->launches = 0;
+    c->timing = false;
+    c->recorded[0] = c->recorded[1] = false;
+    for (auto &e : c->ev) e = nullptr;
     *ctx = c;
     return EM_OK;
 }
 
 EM_EXPORT int em_ctx_destroy(em_ctx *ctx)
 {
+    if (ctx) {
+        for (auto &e : ctx->ev)
+            if (e) cudaEventDestroy(e);
+    }
     delete ctx;
+    return EM_OK;
+}
+
+EM_EXPORT int em_ctx_set_timing(em_ctx *ctx, int on)
+{
+    EM_CHECK_ARG(ctx);
+    if (on && !ctx->ev[0]) {
+        EM_CUDA(cudaSetDevice(ctx->device));
+        for (auto &e : ctx->ev) EM_CUDA(cudaEventCreate(&e));
+    }
+    ctx->timing = on != 0;
+    ctx->recorded[0] = ctx->recorded[1] = false;
+    return EM_OK;
+}
+
+EM_EXPORT int em_ctx_map_times(em_ctx *ctx, double *ms_main, double *ms_recompute)
+{
+    EM_CHECK_ARG(ctx && ms_main && ms_recompute);
+    *ms_main = *ms_recompute = 0.0;
+    float t = 0.f;
+    if (ctx->recorded[0]) {
+        EM_CUDA(cudaEventSynchronize(ctx->ev[1]));
+        EM_CUDA(cudaEventElapsedTime(&t, ctx->ev[0], ctx->ev[1]));
+        *ms_main = t;
+    }
+    if (ctx->recorded[1]) {
+        EM_CUDA(cudaEventSynchronize(ctx->ev[3]));
+        EM_CUDA(cudaEventElapsedTime(&t, ctx->ev[2], ctx->ev[3]));
+        *ms_recompute = t;
+    }
     return EM_OK;
 }
 

@@ -17,6 +17,11 @@ struct em_ctx {
     int device;
     cudaStream_t stream;
     int64_t launches;
+    // optional timing of the map_exact kernels (em_ctx_set_timing):
+    // ev[0..1] bracket the main pass, ev[2..3] the FP64 recompute of flagged pairs
+    bool timing;
+    cudaEvent_t ev[4];
+    bool recorded[2];
 };
 
 void em_set_error(const char *fmt, ...);
@@ -123,15 +128,16 @@ struct em_pseudo {
     explicit em_pseudo(cudaStream_t s) : mem(s) {}
 };
 
-// One face-edge of a cell, in the frame of the cell's generator g:
-// m = in-plane outward edge normal, cm = m.(V_k - g); e = unit edge
-// direction, ce = e.(V_k - g); L = edge length.
+// One face of a cell, in the frame of the cell's generator g.
 struct __align__(32) PlaneD {
     double x, y, z, w;   // unit outward normal (x, y, z), offset w = n.(V_0 - g)
 };
 struct __align__(16) PlaneF {
     float x, y, z, w;
 };
+// One face-edge of a cell, in the frame of the cell's generator g:
+// m = in-plane outward edge normal, cm = m.(V_k - g); e = unit edge
+// direction, ce = e.(V_k - g); L = edge length.
 struct __align__(16) EdgeD {
     double mx, my, mz, cm, ex, ey, ez, ce, L, pad;
 };

@@ -1,5 +1,6 @@
 // Exact mapping (map_exact), cell densities, inverse mapping (map_back), and
 // the import paths for cells and pair lists.
+#include <algorithm>
 #include <cmath>
 
 #include "common.cuh"
@@ -324,6 +325,29 @@ __global__ void __launch_bounds__(128) k_map_fp64(int64_t npairs, const int32_t 
     double err;
     w[k] = pair_weight<double, true>(x[i] - gen[3 * j], y[i] - gen[3 * j + 1], z[i] - gen[3 * j + 2], h[i], radius[j],
                                cfo[j], cfo[j + 1], fvo, plane, edge, err);
+}
+
+// FP64 recompute of the pairs the FP32 pass flagged; the count is read on
+// the device, so the launch needs no host synchronisation (grid-stride loop).
+__global__ void __launch_bounds__(128) k_map_fp64_flagged(const int *__restrict__ nflag, const int32_t *__restrict__ pi,
+                                                          const int32_t *__restrict__ pj, const double *__restrict__ x,
+                                                          const double *__restrict__ y, const double *__restrict__ z,
+                                                          const double *__restrict__ h, const double *__restrict__ gen,
+                                                          const double *__restrict__ radius,
+                                                          const int64_t *__restrict__ cfo,
+                                                          const int64_t *__restrict__ fvo,
+                                                          const PlaneD *__restrict__ plane,
+                                                          const EdgeD *__restrict__ edge,
+                                                          const int32_t *__restrict__ list, double *__restrict__ w)
+{
+    const int64_t n = *nflag;
+    for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < n; t += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t k = list[t];
+        const int i = pi[k], j = pj[k];
+        double err;
+        w[k] = pair_weight<double, true>(x[i] - gen[3 * j], y[i] - gen[3 * j + 1], z[i] - gen[3 * j + 2], h[i],
+                                         radius[j], cfo[j], cfo[j + 1], fvo, plane, edge, err);
+    }
 }
 
 // FP32 bulk pass (quadrature form, see quad32.cuh).
@@ -665,13 +689,19 @@ EM_EXPORT int map_exact(em_ctx *ctx, const em_pairs *pr, const double *d_x, cons
     int block = p->block_pairs > 0 ? p->block_pairs : 128;
     EM_CHECK_ARG(block % 32 == 0 && block <= 128);
     if (h_nfp64) *h_nfp64 = 0;
+    if (ctx->timing) ctx->recorded[0] = ctx->recorded[1] = false;
     if (n) {
+        if (ctx->timing) EM_CUDA(cudaEventRecord(ctx->ev[0], ctx->stream));
         if (p->precision == 0) {
             k_map_fp64<<<em_grid(n, block), block, 0, ctx->stream>>>(n, pr->pair_i, pr->pair_j, d_x, d_y, d_z, d_h,
                                                                      v->gen, v->radius, v->cell_face_off,
                                                                      v->face_vert_off, v->plane, v->edge, nullptr,
                                                                      d_w_out);
             EM_LAUNCHED(ctx);
+            if (ctx->timing) {
+                EM_CUDA(cudaEventRecord(ctx->ev[1], ctx->stream));
+                ctx->recorded[0] = true;
+            }
         } else {
             DevArena tmp(ctx->stream, true);
             int32_t *flagged;
@@ -683,16 +713,27 @@ EM_EXPORT int map_exact(em_ctx *ctx, const em_pairs *pr, const double *d_x, cons
                 n, pr->pair_i, pr->pair_j, d_x, d_y, d_z, d_h, v->gen, v->radius, v->cell_face_off,
                 v->face_vert_off, v->plane, v->edge, v->edge_f, (float)p->fp64_threshold, d_w_out, flagged, nflag);
             EM_LAUNCHED(ctx);
-            int hflag = 0;
-            EM_CUDA(cudaMemcpyAsync(&hflag, nflag, sizeof(int), cudaMemcpyDeviceToHost, ctx->stream));
-            EM_CUDA(cudaStreamSynchronize(ctx->stream));
-            if (hflag) {
-                k_map_fp64<<<em_grid(hflag, block), block, 0, ctx->stream>>>(
-                    hflag, pr->pair_i, pr->pair_j, d_x, d_y, d_z, d_h, v->gen, v->radius, v->cell_face_off,
-                    v->face_vert_off, v->plane, v->edge, flagged, d_w_out);
-                EM_LAUNCHED(ctx);
+            if (ctx->timing) {
+                EM_CUDA(cudaEventRecord(ctx->ev[1], ctx->stream));
+                EM_CUDA(cudaEventRecord(ctx->ev[2], ctx->stream));
             }
-            if (h_nfp64) *h_nfp64 = hflag;
+            // FP64 recompute of the flagged pairs; the count stays on the device
+            const int grid = (int)std::min<int64_t>((n + block - 1) / block, 152 * 16);
+            k_map_fp64_flagged<<<grid, block, 0, ctx->stream>>>(nflag, pr->pair_i, pr->pair_j, d_x, d_y, d_z, d_h,
+                                                                 v->gen, v->radius, v->cell_face_off,
+                                                                 v->face_vert_off, v->plane, v->edge, flagged,
+                                                                 d_w_out);
+            EM_LAUNCHED(ctx);
+            if (ctx->timing) {
+                EM_CUDA(cudaEventRecord(ctx->ev[3], ctx->stream));
+                ctx->recorded[0] = ctx->recorded[1] = true;
+            }
+            if (h_nfp64) {
+                int hflag = 0;
+                EM_CUDA(cudaMemcpyAsync(&hflag, nflag, sizeof(int), cudaMemcpyDeviceToHost, ctx->stream));
+                EM_CUDA(cudaStreamSynchronize(ctx->stream));
+                *h_nfp64 = hflag;
+            }
         }
     }
     if (d_rho_out && v->ncell) {

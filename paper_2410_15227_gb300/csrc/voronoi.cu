@@ -1,20 +1,22 @@
 // build_voronoi: Voronoi cells of the generation sites, clipped to the box.
 //
-// Each cell is built by one thread in the generator's frame (g at the
-// origin).  The convex cell is held in dual form: its planes (n.x <= d) and
-// its vertices, each a triangle of three plane indices ordered
-// counter-clockwise seen from outside, with the vertex position.  Clipping by
-// a bisector removes the vertices beyond it and replaces each edge that
-// crossed the plane by a new vertex (the kept neighbour across an edge (a, b)
-// is the vertex holding (b, a)).
+// Each cell is built by one warp, with the cell in shared memory, in the
+// generator's frame (g at the origin).  The convex cell is held in dual form:
+// its planes (n.x <= d) and its vertices, each a triangle of three plane
+// indices ordered counter-clockwise seen from outside, with the vertex
+// position.  Clipping by a bisector removes the vertices beyond it and
+// replaces each edge that crossed the plane by a new vertex (the kept
+// neighbour across an edge (a, b) is the vertex holding (b, a)); the lanes
+// share the vertex work (voronoi_warp.cuh).
 //
-// Candidates come first from the K nearest generators (a bounded list kept
-// sorted while walking the generators' box hierarchy).  The cell is exact
-// once 2 R_max < d_K, R_max being its farthest vertex: no generator farther
-// than 2 R_max can cut it.  Otherwise every generator within 2 R_max that was
-// not in the list is clipped in as well, shrinking R_max as it goes.
-// Pass 1 records the bisectors that actually cut; pass 2 replays exactly
-// those clips (bit-identical state) and writes the faces.
+// Candidates: the generators within a search radius of the site, found by a
+// warp walk of the generators' box hierarchy and clipped nearest first.  The
+// cell is exact once 2 R_max is below the search radius, R_max being its
+// farthest vertex: no generator farther than 2 R_max can cut it.  Otherwise
+// the shell up to 2 R_max is clipped in as well.  Pass 1 (count) builds the
+// cell, records the bisectors that actually cut it and its size; pass 2
+// (emit) replays exactly those clips (bit-identical state) and writes the
+// faces at the scanned offsets.
 #include <cmath>
 
 #include "common.cuh"
