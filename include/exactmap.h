@@ -201,6 +201,28 @@ int map_exact(em_ctx *ctx, const em_pairs *pr, const double *d_x, const double *
               const double *d_h, const double *d_m, const em_voronoi *v, const em_params *p,
               double *d_w_out, double *d_rho_out, double *d_wsum_out, int64_t *h_nfp64);
 
+/* ---- map_exact_noalloc -------------------------------------------------------
+ * The same computation and results as map_exact (bit-identical w, rho, u and
+ * FP64 count), for callers that must not allocate device memory during the
+ * call.  The paper has no counterpart: this is a deployment variant of the
+ * library, not a step of the method.
+ *   - Allocates nothing: the mixed pass's list of flagged pairs and its
+ *     counter are a fixed array of EM_NOALLOC_MAX_PAIRS entries in the
+ *     library's own device memory (4 MiB per device); the counter is zeroed
+ *     on the context's stream at the start of every call.
+ *   - pr->npairs > EM_NOALLOC_MAX_PAIRS: returns EM_ECAPACITY with a message,
+ *     nothing enqueued.
+ *   - The first call on a device looks up the array's address (with that
+ *     device made current, then restored); make it before any stream capture
+ *     that is to contain the call.
+ *   - The array is shared: calls that overlap in time on one device (two
+ *     streams, or two host threads) race on it.  Serialise them.
+ *   - Arguments, layout, ownership and h_nfp64 as for map_exact. */
+#define EM_NOALLOC_MAX_PAIRS (1 << 20)
+int map_exact_noalloc(em_ctx *ctx, const em_pairs *pr, const double *d_x, const double *d_y, const double *d_z,
+                      const double *d_h, const double *d_m, const em_voronoi *v, const em_params *p,
+                      double *d_w_out, double *d_rho_out, double *d_wsum_out, int64_t *h_nfp64);
+
 /* ---- map_back -------------------------------------------------------------------
  * Inverse mapping of a per-cell field onto the (pseudo-)particles
  * (Section 2.3): f_i = sum_j w_ij f_j / sum_j w_ij (NaN when particle i has

@@ -61,6 +61,7 @@ SIGNATURES = {
     "pairs_get": (I32, [P, P, P, P, P, P]),
     "pairs_destroy": (I32, [P]),
     "map_exact": (I32, [P, P, P, P, P, P, P, P, PPAR, P, P, P, PI64]),
+    "map_exact_noalloc": (I32, [P, P, P, P, P, P, P, P, PPAR, P, P, P, PI64]),
     "map_back": (I32, [P, P, P, P, P, P, P, P]),
 }
 

@@ -285,6 +285,26 @@ def map_exact(ctx: Context, pairs: Pairs, x, y, z, h_, m, vor: Voronoi, params: 
     return w, rho, wsum, nfp64.value if want_count else None
 
 
+def map_exact_noalloc(ctx: Context, pairs: Pairs, x, y, z, h_, m, vor: Voronoi, params: Params,
+                      out, want_count: bool = True):
+    """map_exact into caller-supplied outputs out = (w, rho, wsum or None),
+    without any device allocation by the library (at most
+    NOALLOC_MAX_PAIRS pairs; concurrent calls on one device race).
+    Returns (w, rho, wsum, #pairs in FP64 or None)."""
+    npairs, np_, nc = pairs.info()
+    w, rho, wsum = out
+    nfp64 = C.c_int64()
+    p = params.native()
+    N.call("map_exact_noalloc", ctx.handle, pairs.handle, _ptr(x, f64, np_, "x"), _ptr(y, f64, np_, "y"),
+           _ptr(z, f64, np_, "z"), _ptr(h_, f64, np_, "h"), _ptr(m, f64, np_, "m"), vor.handle,
+           C.byref(p), _ptr(w, f64, npairs), _ptr(rho, f64, nc), _ptr(wsum, f64, np_),
+           C.byref(nfp64) if want_count else None)
+    return w, rho, wsum, nfp64.value if want_count else None
+
+
+NOALLOC_MAX_PAIRS = 1 << 20
+
+
 def map_back(ctx: Context, pairs: Pairs, w, f_cell, pseudo: Pseudo | None = None,
              tree: Tree | None = None):
     """Returns (f per (pseudo-)particle, f per SPH particle or None)."""

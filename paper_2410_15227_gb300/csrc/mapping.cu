@@ -2,6 +2,7 @@
 // the import paths for cells and pair lists.
 #include <algorithm>
 #include <cmath>
+#include <mutex>
 
 #include "common.cuh"
 #include "exact.cuh"
@@ -728,6 +729,113 @@ EM_EXPORT int map_exact(em_ctx *ctx, const em_pairs *pr, const double *d_x, cons
                 EM_CUDA(cudaEventRecord(ctx->ev[3], ctx->stream));
                 ctx->recorded[0] = ctx->recorded[1] = true;
             }
+            if (h_nfp64) {
+                int hflag = 0;
+                EM_CUDA(cudaMemcpyAsync(&hflag, nflag, sizeof(int), cudaMemcpyDeviceToHost, ctx->stream));
+                EM_CUDA(cudaStreamSynchronize(ctx->stream));
+                *h_nfp64 = hflag;
+            }
+        }
+    }
+    if (d_rho_out && v->ncell) {
+        k_cell_density<<<em_grid(v->ncell * 32, 256), 256, 0, ctx->stream>>>(v->ncell, pr->cell_pair_off, pr->pair_i,
+                                                                               d_w_out, d_m, v->volume, d_rho_out);
+        EM_LAUNCHED(ctx);
+    }
+    if (d_wsum_out && pr->np) {
+        k_particle_wsum<<<em_grid(pr->np, 256), 256, 0, ctx->stream>>>(pr->np, pr->part_pair_off, pr->part_pair_idx,
+                                                                        d_w_out, d_wsum_out);
+        EM_LAUNCHED(ctx);
+    }
+    return EM_OK;
+}
+
+// ---------------------------------------------------------------------------
+// map_exact without allocation: the mixed pass's flagged-pair list and its
+// counter live in a fixed device array instead of stream-ordered scratch.
+// ---------------------------------------------------------------------------
+
+namespace {
+
+// Zeroed at the start of every call (the counter); the list needs no reset,
+// the FP32 pass writes entries [0, count) before the FP64 pass reads them.
+static __device__ __align__(256) int32_t g_noalloc_flagged[EM_NOALLOC_MAX_PAIRS];
+static __device__ __align__(256) int g_noalloc_count[1];
+
+constexpr int NOALLOC_MAX_DEVICES = 64;
+std::mutex g_noalloc_mutex;
+int32_t *g_noalloc_flagged_addr[NOALLOC_MAX_DEVICES];
+int *g_noalloc_count_addr[NOALLOC_MAX_DEVICES];
+
+// Device addresses of the two arrays on ctx's device, looked up once per
+// device with that device current.
+int noalloc_buffers(em_ctx *ctx, int32_t **flagged, int **count)
+{
+    EM_CHECK_ARG(ctx->device >= 0 && ctx->device < NOALLOC_MAX_DEVICES);
+    std::lock_guard<std::mutex> lock(g_noalloc_mutex);
+    if (!g_noalloc_flagged_addr[ctx->device]) {
+        int cur = -1;
+        EM_CUDA(cudaGetDevice(&cur));
+        if (cur != ctx->device) EM_CUDA(cudaSetDevice(ctx->device));
+        void *a = nullptr, *b = nullptr;
+        cudaError_t e1 = cudaGetSymbolAddress(&a, g_noalloc_flagged);
+        cudaError_t e2 = e1 == cudaSuccess ? cudaGetSymbolAddress(&b, g_noalloc_count) : e1;
+        if (cur != ctx->device && cur >= 0) cudaSetDevice(cur);
+        if (e2 != cudaSuccess) {
+            em_set_error("map_exact_noalloc: cudaGetSymbolAddress failed on device %d: %s", ctx->device,
+                         cudaGetErrorString(e2));
+            return EM_ECUDA;
+        }
+        g_noalloc_count_addr[ctx->device] = (int *)b;
+        g_noalloc_flagged_addr[ctx->device] = (int32_t *)a;
+    }
+    *flagged = g_noalloc_flagged_addr[ctx->device];
+    *count = g_noalloc_count_addr[ctx->device];
+    return EM_OK;
+}
+
+}  // namespace
+
+EM_EXPORT int map_exact_noalloc(em_ctx *ctx, const em_pairs *pr, const double *d_x, const double *d_y,
+                                const double *d_z, const double *d_h, const double *d_m, const em_voronoi *v,
+                                const em_params *p, double *d_w_out, double *d_rho_out, double *d_wsum_out,
+                                int64_t *h_nfp64)
+{
+    EM_CHECK_ARG(ctx && pr && v && p && pr->ncell == v->ncell);
+    EM_CHECK_ARG(pr->npairs == 0 || (d_x && d_y && d_z && d_h && d_w_out));
+    EM_CHECK_ARG(d_rho_out == nullptr || d_m != nullptr);
+    EM_CHECK_ARG(p->precision == 0 || p->precision == 1);
+    const int64_t n = pr->npairs;
+    if (n > EM_NOALLOC_MAX_PAIRS) {
+        em_set_error("map_exact_noalloc: %lld pairs exceed the fixed capacity of %d pairs", (long long)n,
+                     EM_NOALLOC_MAX_PAIRS);
+        return EM_ECAPACITY;
+    }
+    const int block = p->block_pairs > 0 ? p->block_pairs : 128;
+    EM_CHECK_ARG(block % 32 == 0 && block <= 128);
+    if (h_nfp64) *h_nfp64 = 0;
+    if (n) {
+        if (p->precision == 0) {
+            k_map_fp64<<<em_grid(n, block), block, 0, ctx->stream>>>(n, pr->pair_i, pr->pair_j, d_x, d_y, d_z, d_h,
+                                                                     v->gen, v->radius, v->cell_face_off,
+                                                                     v->face_vert_off, v->plane, v->edge, nullptr,
+                                                                     d_w_out);
+            EM_LAUNCHED(ctx);
+        } else {
+            int32_t *flagged;
+            int *nflag;
+            EM_TRY(noalloc_buffers(ctx, &flagged, &nflag));
+            EM_CUDA(cudaMemsetAsync(nflag, 0, sizeof(int), ctx->stream));
+            k_map_fp32<<<em_grid((n + 31) / 32, MQ_WARPS), 32 * MQ_WARPS, 0, ctx->stream>>>(
+                n, pr->pair_i, pr->pair_j, d_x, d_y, d_z, d_h, v->gen, v->radius, v->cell_face_off,
+                v->face_vert_off, v->plane, v->edge, v->edge_f, (float)p->fp64_threshold, d_w_out, flagged, nflag);
+            EM_LAUNCHED(ctx);
+            const int grid = (int)std::min<int64_t>((n + block - 1) / block, 152 * 16);
+            k_map_fp64_flagged<<<grid, block, 0, ctx->stream>>>(nflag, pr->pair_i, pr->pair_j, d_x, d_y, d_z, d_h,
+                                                                 v->gen, v->radius, v->cell_face_off,
+                                                                 v->face_vert_off, v->plane, v->edge, flagged,
+                                                                 d_w_out);
+            EM_LAUNCHED(ctx);
             if (h_nfp64) {
                 int hflag = 0;
                 EM_CUDA(cudaMemcpyAsync(&hflag, nflag, sizeof(int), cudaMemcpyDeviceToHost, ctx->stream));
