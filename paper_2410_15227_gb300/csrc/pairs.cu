@@ -3,9 +3,14 @@
 //
 // The particles are Morton-sorted and bounded by a 32-ary box hierarchy of
 // their support spheres.  One warp per cell walks it with the cell's bounding
-// ball (generator g_j, radius R_j); each lane then applies the exact test to
-// one candidate.  Hits are compacted with a warp ballot, first counted, then
-// written at the cell's scanned offset.
+// ball (generator g_j, radius R_j); each lane then tests one candidate.  The
+// test first classifies in FP32 (GB300 runs FP64 at 1/64 of the FP32 rate):
+// a candidate whose FP32 distance clears 2h by the band
+// 1e-5 (R_j + |r| + 2h) -- far above the rounding of the FP32 dot products,
+// which is a few ulp of that same scale -- is decided there; only candidates
+// inside the band take the exact FP64 test, which also sets the near flag.
+// The pair set is therefore the FP64 predicate's.  Hits are compacted with a
+// warp ballot, first counted, then written at the cell's scanned offset.
 #include "common.cuh"
 #include "tree_util.cuh"
 
@@ -55,8 +60,47 @@ __device__ __forceinline__ double cell_dist2(double rx, double ry, double rz, in
     return best;
 }
 
-// One warp per cell: candidate particles from the sphere hierarchy, exact
-// test, ballot compaction.  Pass 1 (keys == NULL) writes counts; pass 2
+// cell_dist2 in FP32 from the cell's FP32 plane and edge records: the same
+// steps, so that its error is a few ulp of (R_j + |r|) in the distance.
+__device__ __forceinline__ float cell_dist2_f32(float rx, float ry, float rz, int64_t f0, int64_t f1,
+                                                const int64_t *__restrict__ fvo, const PlaneF *__restrict__ plane,
+                                                const EdgeF *__restrict__ edge, float lim)
+{
+    bool outside = false;
+    for (int64_t f = f0; f < f1; ++f) {
+        PlaneF pl = plane[f];
+        float s = pl.w - (pl.x * rx + pl.y * ry + pl.z * rz);
+        if (s < 0.f) {
+            outside = true;
+            if (-s >= lim) return lim * lim;
+        }
+    }
+    if (!outside) return 0.f;
+    float best = INFINITY;
+    for (int64_t f = f0; f < f1; ++f) {
+        PlaneF pl = plane[f];
+        float s = pl.w - (pl.x * rx + pl.y * ry + pl.z * rz);
+        if (s >= 0.f) continue;
+        float s2 = s * s;
+        if (s2 >= best) continue;
+        bool in_poly = true;
+        float e2 = INFINITY;
+        for (int64_t e = fvo[f]; e < fvo[f + 1]; ++e) {
+            EdgeF E = edge[e];
+            float a = E.cm - (E.mx * rx + E.my * ry + E.mz * rz);
+            in_poly = in_poly && (a >= 0.f);
+            float t0 = E.ce - (E.ex * rx + E.ey * ry + E.ez * rz);
+            float t1 = t0 + E.L;
+            float tc = t0 > 0.f ? t0 : (t1 < 0.f ? t1 : 0.f);
+            e2 = fminf(e2, a * a + tc * tc);
+        }
+        best = fminf(best, in_poly ? s2 : s2 + e2);
+    }
+    return best;
+}
+
+// One warp per cell: candidate particles from the sphere hierarchy, FP32
+// classification, exact FP64 test inside the band, ballot compaction.  Pass 1 (keys == NULL) writes counts; pass 2
 // writes (j << 32 | i) keys and near flags at the cell's offset.
 __global__ void __launch_bounds__(128) k_cell_pairs(int64_t ncell, em::ChunkTree T, const double *__restrict__ xs,
                                                      const double *__restrict__ ys, const double *__restrict__ zs,
@@ -64,7 +108,9 @@ __global__ void __launch_bounds__(128) k_cell_pairs(int64_t ncell, em::ChunkTree
                                                      const double *__restrict__ gen, const double *__restrict__ radius,
                                                      const int64_t *__restrict__ cfo, const int64_t *__restrict__ fvo,
                                                      const PlaneD *__restrict__ plane, const EdgeD *__restrict__ edge,
-                                                     float margin, int64_t *__restrict__ count,
+                                                     const PlaneF *__restrict__ plane_f,
+                                                     const EdgeF *__restrict__ edge_f, float margin,
+                                                     int64_t *__restrict__ count,
                                                      const int64_t *__restrict__ offset, uint64_t *__restrict__ keys,
                                                      int32_t *__restrict__ nearf)
 {
@@ -75,18 +121,28 @@ __global__ void __launch_bounds__(128) k_cell_pairs(int64_t ncell, em::ChunkTree
     const double Rj = radius[j];
     const int64_t f0 = cfo[j], f1 = cfo[j + 1];
     const float R = (float)Rj + margin;
+    const float Rf = (float)Rj;
     int64_t n = 0;
     const int64_t base = keys ? offset[j] : 0;
     em::warp_traverse(T, (float)gx, (float)gy, (float)gz, R * R, INT64_MAX, [&](int64_t k, bool valid) {
         bool hit = false, nearb = false;
         if (valid) {
-            double rx = xs[k] - gx, ry = ys[k] - gy, rz = zs[k] - gz;
-            double h2 = 2.0 * hs[k];
-            double rr = sqrt(rx * rx + ry * ry + rz * rz);
-            if (rr < Rj + h2 * (1.0 + 1e-12)) {
-                double d2 = cell_dist2(rx, ry, rz, f0, f1, fvo, plane, edge, 2.0 * h2);
-                hit = d2 < h2 * h2;
-                if (hit) nearb = fabs(sqrt(d2) - h2) < 0.5e-9 * h2;
+            const double rx = xs[k] - gx, ry = ys[k] - gy, rz = zs[k] - gz;
+            const double h2 = 2.0 * hs[k];
+            const float rxf = (float)rx, ryf = (float)ry, rzf = (float)rz, h2f = (float)h2;
+            const float rr = sqrtf(rxf * rxf + ryf * ryf + rzf * rzf);
+            const float band = 1e-5f * (Rf + rr + h2f);
+            // the cell lies inside the ball of radius R_j around g: dist >= |r| - R_j
+            if (rr < Rf + h2f + band) {
+                const float lo = h2f - band, hi = h2f + band;
+                const float d2f = cell_dist2_f32(rxf, ryf, rzf, f0, f1, fvo, plane_f, edge_f, hi + band);
+                if (lo > 0.f && d2f < lo * lo) {
+                    hit = true;
+                } else if (!(d2f > hi * hi)) {   // inside the band: exact FP64 test
+                    const double d2 = cell_dist2(rx, ry, rz, f0, f1, fvo, plane, edge, 2.0 * h2);
+                    hit = d2 < h2 * h2;
+                    if (hit) nearb = fabs(sqrt(d2) - h2) < 0.5e-9 * h2;
+                }
             }
         }
         uint32_t b = __ballot_sync(0xffffffffu, hit);
@@ -192,8 +248,9 @@ static int find_pairs_impl(em_ctx *ctx, int64_t np, const double *x, const doubl
     EM_TRY(tmp.alloc(&offset, nc + 1));
     EM_CUDA(cudaMemsetAsync(count + nc, 0, sizeof(int64_t), st));
     k_cell_pairs<<<em_grid(nc * 32, 128), 128, 0, st>>>(nc, T, xs, ys, zs, hs, perm, v->gen, v->radius,
-                                                         v->cell_face_off, v->face_vert_off, v->plane, v->edge, margin,
-                                                         count, nullptr, nullptr, nullptr);
+                                                         v->cell_face_off, v->face_vert_off, v->plane, v->edge,
+                                                         v->plane_f, v->edge_f, margin, count, nullptr, nullptr,
+                                                         nullptr);
     EM_LAUNCHED(ctx);
     EM_TRY(em_exclusive_scan_i64(ctx, count, offset, nc + 1));
     int64_t total = 0;
@@ -211,7 +268,8 @@ static int find_pairs_impl(em_ctx *ctx, int64_t np, const double *x, const doubl
     if (total) {
         k_cell_pairs<<<em_grid(nc * 32, 128), 128, 0, st>>>(nc, T, xs, ys, zs, hs, perm, v->gen, v->radius,
                                                              v->cell_face_off, v->face_vert_off, v->plane, v->edge,
-                                                             margin, count, offset, keys, nearf);
+                                                             v->plane_f, v->edge_f, margin, count, offset, keys,
+                                                             nearf);
         EM_LAUNCHED(ctx);
         EM_TRY(em_sort_pairs_u64(ctx, keys, nearf, total, 32 + em_nbits((uint64_t)nc)));
     }
