@@ -122,11 +122,23 @@ __global__ void __launch_bounds__(128) k_cell_pairs(int64_t ncell, em::ChunkTree
     const int64_t f0 = cfo[j], f1 = cfo[j + 1];
     const float R = (float)Rj + margin;
     const float Rf = (float)Rj;
+    const float gxf = (float)gx, gyf = (float)gy, gzf = (float)gz;
+    const float gscale = fabsf(gxf) + fabsf(gyf) + fabsf(gzf);
     int64_t n = 0;
     const int64_t base = keys ? offset[j] : 0;
     em::warp_traverse(T, (float)gx, (float)gy, (float)gz, R * R, INT64_MAX, [&](int64_t k, bool valid) {
         bool hit = false, nearb = false;
-        if (valid) {
+        // candidates beyond R_j + 2h by the band (which here also covers the
+        // FP32 rounding of the coordinates themselves) are dropped before any FP64
+        bool cand = valid;
+        if (cand) {
+            const float4 pk = T.pts[k];
+            const float ex = pk.x - gxf, ey = pk.y - gyf, ez = pk.z - gzf;
+            const float d = sqrtf(ex * ex + ey * ey + ez * ez);
+            const float h2f = 2.f * (float)hs[k];
+            cand = d < Rf + h2f + 1e-5f * (gscale + Rf + d + h2f);
+        }
+        if (cand) {
             const double rx = xs[k] - gx, ry = ys[k] - gy, rz = zs[k] - gz;
             const double h2 = 2.0 * hs[k];
             const float rxf = (float)rx, ryf = (float)ry, rzf = (float)rz, h2f = (float)h2;

@@ -145,8 +145,18 @@ __device__ Density warp_density(const em::ChunkTree &T, const double *__restrict
     const double ih = 1.0 / h;
     const double norm = ih * ih * ih * 0.31830988618379067154;   // 1/(pi h^3)
     float R = (float)(2.0 * h) + margin;
+    // FP32 prefilter: candidates of the walk (whole 32-point chunks) that are
+    // clearly beyond 2h skip the FP64 work.  The band, 1e-5 of the
+    // coordinates' scale plus 2h, is far above the FP32 rounding of the
+    // positions, so no neighbour is dropped.
+    const float xaf = (float)xa, yaf = (float)ya, zaf = (float)za, h2f = (float)(2.0 * h);
+    const float lim = h2f + 1e-5f * (fabsf(xaf) + fabsf(yaf) + fabsf(zaf) + h2f);
+    const float lim2 = lim * lim;
     em::warp_traverse(T, (float)xa, (float)ya, (float)za, R * R, INT64_MAX, [&](int64_t k, bool valid) {
         if (!valid) return;
+        const float4 pk = T.pts[k];
+        const float ex = pk.x - xaf, ey = pk.y - yaf, ez = pk.z - zaf;
+        if (ex * ex + ey * ey + ez * ez >= lim2) return;
         double dx = qx[k] - xa, dy = qy[k] - ya, dz = qz[k] - za;
         double q = sqrt(dx * dx + dy * dy + dz * dz) * ih;
         if (q < 2.0) {
@@ -161,6 +171,48 @@ __device__ Density warp_density(const em::ChunkTree &T, const double *__restrict
         ds += __shfl_xor_sync(0xffffffffu, ds, o);
     }
     return Density{s, ds};
+}
+
+// Sign of f(h) = h_fact n(h)^(-1/3) - h (Eq. 8) for the bisection, which uses
+// nothing else.  Every term of n is non-negative, so once the running sum
+// exceeds (h_fact / h)^3 (1 + 1e-9) the sign is negative whatever the rest of
+// the sum; the walk stops there.  This matters for the wide first brackets
+// (h up to 1e2 h_0), whose 2h sphere holds a large share of the population.
+// Otherwise the full sum decides, as in warp_density.  Returns the sign of f
+// (+1, 0 or -1).
+__device__ int warp_f_sign(const em::ChunkTree &T, const double *__restrict__ qx,
+                                const double *__restrict__ qy, const double *__restrict__ qz, double xa, double ya,
+                                double za, double h, double h_fact, float margin)
+{
+    double s = 0.0;
+    const double ih = 1.0 / h;
+    const double norm = ih * ih * ih * 0.31830988618379067154;   // 1/(pi h^3)
+    const double t = h_fact * ih;
+    const double thr = t * t * t * (1.0 + 1e-9);
+    float R = (float)(2.0 * h) + margin;
+    const float xaf = (float)xa, yaf = (float)ya, zaf = (float)za, h2f = (float)(2.0 * h);
+    const float lim = h2f + 1e-5f * (fabsf(xaf) + fabsf(yaf) + fabsf(zaf) + h2f);
+    const float lim2 = lim * lim;
+    bool full = em::warp_traverse_until(T, xaf, yaf, zaf, R * R, [&](int64_t k, bool valid) {
+        if (valid) {
+            const float4 pk = T.pts[k];
+            const float ex = pk.x - xaf, ey = pk.y - yaf, ez = pk.z - zaf;
+            if (ex * ex + ey * ey + ez * ez < lim2) {
+                double dx = qx[k] - xa, dy = qy[k] - ya, dz = qz[k] - za;
+                double q = sqrt(dx * dx + dy * dy + dz * dz) * ih;
+                if (q < 2.0) s += em::m4_w(q) * norm;
+            }
+        }
+        double tot = s;
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) tot += __shfl_xor_sync(0xffffffffu, tot, o);
+        return !(tot > thr);
+    });
+    if (!full) return -1;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+    const double f = h_fact * pow(s, -1.0 / 3.0) - h;
+    return f > 0.0 ? 1 : (f < 0.0 ? -1 : 0);
 }
 
 // One warp per pseudo-particle: Newton (Eq. 10) from h_0 (Eq. 11) until
@@ -192,25 +244,19 @@ __global__ void k_h_solve(int64_t npseudo, em::ChunkTree T, const double *__rest
     }
     int st = 0;
     if (!ok) {
+        // bisection on signs only (warp_f_sign)
         double lo = 1e-2 * h0, hi = 1e2 * h0;
-        Density dl = warp_density(T, qx, qy, qz, xa, ya, za, lo, margin);
-        Density dh = warp_density(T, qx, qy, qz, xa, ya, za, hi, margin);
-        double flo = h_fact * pow(dl.n, -1.0 / 3.0) - lo;
-        double fhi = h_fact * pow(dh.n, -1.0 / 3.0) - hi;
-        if (flo * fhi > 0.0) {
+        const int slo = warp_f_sign(T, qx, qy, qz, xa, ya, za, lo, h_fact, margin);
+        const int shi = warp_f_sign(T, qx, qy, qz, xa, ya, za, hi, h_fact, margin);
+        const bool plo = slo > 0;
+        if (slo * shi > 0) {
             h = h0;
             st = 2;
         } else {
             for (int k = 0; k < 200 && (hi - lo) > tol * h0; ++k) {
                 double mid = 0.5 * (lo + hi);
-                Density dm = warp_density(T, qx, qy, qz, xa, ya, za, mid, margin);
-                double fm = h_fact * pow(dm.n, -1.0 / 3.0) - mid;
-                if ((fm > 0.0) == (flo > 0.0)) {
-                    lo = mid;
-                    flo = fm;
-                } else {
-                    hi = mid;
-                }
+                if ((warp_f_sign(T, qx, qy, qz, xa, ya, za, mid, h_fact, margin) > 0) == plo) lo = mid;
+                else hi = mid;
             }
             h = 0.5 * (lo + hi);
             st = 1;

@@ -344,13 +344,14 @@ namespace {
 
 __global__ void k_chunk_leaf(int64_t nbox, int64_t n, const double *__restrict__ xs, const double *__restrict__ ys,
                              const double *__restrict__ zs, const double *__restrict__ r, double rscale,
-                             float4 *__restrict__ lo, float4 *__restrict__ hi)
+                             float4 *__restrict__ lo, float4 *__restrict__ hi, float4 *__restrict__ pts)
 {
     int64_t b = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     if (b >= nbox) return;
     float lx = INFINITY, ly = INFINITY, lz = INFINITY, hx = -INFINITY, hy = -INFINITY, hz = -INFINITY;
     int64_t e = (b + 1) * 32 < n ? (b + 1) * 32 : n;
     for (int64_t k = b * 32; k < e; ++k) {
+        pts[k] = make_float4((float)xs[k], (float)ys[k], (float)zs[k], 0.f);
         double rr = r ? r[k] * rscale : 0.0;
         lx = fminf(lx, __double2float_rd(xs[k] - rr));
         ly = fminf(ly, __double2float_rd(ys[k] - rr));
@@ -396,10 +397,12 @@ int em_chunk_tree_build(em_ctx *ctx, DevArena &mem, int64_t n, const double *xs,
         if (l) T.count[l] = 0;
     }
     T.nlev = 0;
+    T.pts = nullptr;
     if (n == 0) {
         *out = T;
         return EM_OK;
     }
+    EM_TRY(mem.alloc(&T.pts, n));
     int l = 1;
     for (;; ++l) {
         if (l > em::kMaxLevels) {
@@ -411,7 +414,7 @@ int em_chunk_tree_build(em_ctx *ctx, DevArena &mem, int64_t n, const double *xs,
         EM_TRY(mem.alloc(&T.hi[l], T.count[l]));
         if (l == 1)
             k_chunk_leaf<<<em_grid(T.count[1], 128), 128, 0, ctx->stream>>>(T.count[1], n, xs, ys, zs, r, rscale,
-                                                                             T.lo[1], T.hi[1]);
+                                                                             T.lo[1], T.hi[1], T.pts);
         else
             k_chunk_up<<<em_grid(T.count[l], 128), 128, 0, ctx->stream>>>(T.count[l], T.count[l - 1], T.lo[l - 1],
                                                                            T.hi[l - 1], T.lo[l], T.hi[l]);

@@ -69,6 +69,7 @@ struct ChunkTree {
     int64_t count[kMaxLevels + 1];    // nodes per level (count[0] = items)
     float4 *lo[kMaxLevels + 1];       // per level l >= 1: box min (xyz)
     float4 *hi[kMaxLevels + 1];       // box max
+    float4 *pts = nullptr;            // level 0: item positions rounded to FP32 (w = 0)
 };
 
 __host__ __device__ __forceinline__ float box_dist2(const float4 lo, const float4 hi, float px, float py, float pz)
@@ -115,6 +116,48 @@ __device__ __forceinline__ bool warp_traverse(const ChunkTree &T, float px, floa
         if (lvl == 1) {
             int64_t k = node * 32 + lane;
             visit(k, k < T.count[0]);
+        } else {
+            int64_t child = node * 32 + lane;
+            bool hit = child < T.count[lvl - 1] &&
+                       box_dist2(T.lo[lvl - 1][child], T.hi[lvl - 1][child], px, py, pz) <= R2m;
+            mask[lvl - 1] = __ballot_sync(0xffffffffu, hit);
+            base[lvl - 1] = node;
+            --lvl;
+        }
+    }
+    return true;
+}
+
+// warp_traverse whose visit returns true to go on and false to end the walk
+// (a warp-uniform value).  Returns false if the walk was ended by visit.
+template <class Visit>
+__device__ __forceinline__ bool warp_traverse_until(const ChunkTree &T, float px, float py, float pz, float R2,
+                                                    Visit &&visit)
+{
+    const int lane = threadIdx.x & 31;
+    uint32_t mask[kMaxLevels + 1];
+    int64_t base[kMaxLevels + 1];
+    const int top = T.nlev;
+    if (top <= 0) return true;
+    const float R2m = R2 * 1.00001f + 1e-30f;   // conservative margin for the float boxes
+    {
+        bool hit = lane < T.count[top] && box_dist2(T.lo[top][lane], T.hi[top][lane], px, py, pz) <= R2m;
+        mask[top] = __ballot_sync(0xffffffffu, hit);
+        base[top] = 0;
+    }
+    int lvl = top;
+    while (true) {
+        if (mask[lvl] == 0) {
+            if (lvl == top) break;
+            ++lvl;
+            continue;
+        }
+        int c = __ffs(mask[lvl]) - 1;
+        mask[lvl] &= mask[lvl] - 1;
+        int64_t node = base[lvl] * 32 + c;
+        if (lvl == 1) {
+            int64_t k = node * 32 + lane;
+            if (!visit(k, k < T.count[0])) return false;
         } else {
             int64_t child = node * 32 + lane;
             bool hit = child < T.count[lvl - 1] &&
