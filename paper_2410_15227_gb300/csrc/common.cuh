@@ -163,6 +163,7 @@ struct em_voronoi {
     EdgeD *edge = nullptr;              // [nfv]
     PlaneF *plane_f = nullptr;
     EdgeF *edge_f = nullptr;
+    EdgeF *edge_fl = nullptr;           // [nfv] E - (double)(float)E: low parts of the edge records
     explicit em_voronoi(cudaStream_t s) : mem(s) {}
 };
 

@@ -18,7 +18,7 @@ __global__ void k_prepare_cells(int64_t ncell, const double *__restrict__ gen, c
                                 const int64_t *__restrict__ fvo, const double *__restrict__ verts,
                                 const double *__restrict__ normals, double *__restrict__ radius,
                                 PlaneD *__restrict__ plane, EdgeD *__restrict__ edge, PlaneF *__restrict__ plane_f,
-                                EdgeF *__restrict__ edge_f)
+                                EdgeF *__restrict__ edge_f, EdgeF *__restrict__ edge_fl)
 {
     int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     if (j >= ncell) return;
@@ -67,6 +67,19 @@ __global__ void k_prepare_cells(int64_t ncell, const double *__restrict__ gen, c
             F.L = (float)E.L;
             F.pad0 = F.pad1 = F.pad2 = 0.f;
             edge_f[k] = F;
+            // low parts: E = hi + lo to about 2^-48 relative (float-float)
+            EdgeF G;
+            G.mx = (float)(E.mx - (double)F.mx);
+            G.my = (float)(E.my - (double)F.my);
+            G.mz = (float)(E.mz - (double)F.mz);
+            G.cm = (float)(E.cm - (double)F.cm);
+            G.ex = (float)(E.ex - (double)F.ex);
+            G.ey = (float)(E.ey - (double)F.ey);
+            G.ez = (float)(E.ez - (double)F.ez);
+            G.ce = (float)(E.ce - (double)F.ce);
+            G.L = (float)(E.L - (double)F.L);
+            G.pad0 = G.pad1 = G.pad2 = 0.f;
+            edge_fl[k] = G;
         }
     }
     radius[j] = sqrt(r2max);
@@ -79,10 +92,11 @@ int em_prepare_cells(em_ctx *ctx, em_voronoi *v)
     EM_TRY(v->mem.alloc(&v->edge, v->nfv));
     EM_TRY(v->mem.alloc(&v->plane_f, v->nface));
     EM_TRY(v->mem.alloc(&v->edge_f, v->nfv));
+    EM_TRY(v->mem.alloc(&v->edge_fl, v->nfv));
     if (v->ncell) {
         k_prepare_cells<<<em_grid(v->ncell, 128), 128, 0, ctx->stream>>>(
             v->ncell, v->gen, v->cell_face_off, v->face_vert_off, v->verts, v->normals, v->radius, v->plane,
-            v->edge, v->plane_f, v->edge_f);
+            v->edge, v->plane_f, v->edge_f, v->edge_fl);
         EM_LAUNCHED(ctx);
     }
     return EM_OK;
@@ -370,8 +384,16 @@ __global__ void __launch_bounds__(128) k_map_fp64_flagged(const int *__restrict_
 // it exceeds tol |w| + 1e-14; so does a face plane through P.
 namespace {
 
-constexpr int MQ_SLOTS = 12;   // segments a lane holds between evaluations
-constexpr int MQ_WARPS = 2;    // warps per block
+// launch shape of the FP32 pass (build-time tuning knobs)
+#ifndef EM_MQ_SLOTS
+#define EM_MQ_SLOTS 6
+#endif
+#ifndef EM_MQ_WARPS
+#define EM_MQ_WARPS 2
+#endif
+constexpr int MQ_SLOTS = EM_MQ_SLOTS;   // segments a lane holds between evaluations (>= 5)
+constexpr int MQ_WARPS = EM_MQ_WARPS;   // warps per block
+static_assert(MQ_SLOTS >= 5, "an edge queues up to four segments");
 constexpr unsigned FULL_MASK = 0xffffffffu;
 
 struct SegQueue {
@@ -419,7 +441,8 @@ __device__ __forceinline__ void mq_flush(SegQueue &q, int lane, int cnt, double 
 
 // Face constants of the lane's current face.
 struct FaceState {
-    double D64, rr2, dm1, d4;   // D, rho^2, D^2 - 1, 4 - D^2 (units of h)
+    double D64, rr2;            // D, rho^2 (units of h)
+    emq::ff dm1, d4;            // D^2 - 1, 4 - D^2 (float-float)
     float Df, R, v, KR, C1;     // v = 2 - R
     float sign;   // orientation of the face as seen from P (sign of the signed distance)
 };
@@ -480,7 +503,7 @@ __device__ __forceinline__ void mq_push_g(SegQueue &q, int lane, int &cnt, float
     const float t2 = c4 > 0.f ? sqrtf(c4) : 0.f;
     const float iA = 1.f / A;
     const int tflag = tilde ? emq::SEG_TILDE : 0;
-#pragma unroll
+#pragma unroll 1
     for (int piece = 1; piece <= 2; ++piece) {
         const float a = piece == 1 ? ua : fmaxf(ua, t1);
         const float b = piece == 1 ? fminf(ub, t1) : fminf(ub, t2);
@@ -522,8 +545,8 @@ __global__ void __launch_bounds__(32 * MQ_WARPS) k_map_fp32(int64_t npairs, cons
                                                         const double *__restrict__ radius,
                                                         const int64_t *__restrict__ cfo, const int64_t *__restrict__ fvo,
                                                         const PlaneD *__restrict__ plane,
-                                                        const EdgeD *__restrict__ edge,
-                                                        const EdgeF *__restrict__ edge_f, float tol,
+                                                        const EdgeF *__restrict__ edge_f,
+                                                        const EdgeF *__restrict__ edge_fl, float tol,
                                                         double *__restrict__ w, int32_t *__restrict__ flagged,
                                                         int *__restrict__ nflag)
 {
@@ -556,6 +579,9 @@ __global__ void __launch_bounds__(32 * MQ_WARPS) k_map_fp32(int64_t npairs, cons
     const double ih = 1.0 / hh;
     const float rxf = (float)rx, ryf = (float)ry, rzf = (float)rz, ihf = (float)ih;
     const bool tilde = !full;
+    // float-float copies of r = p - g and 1/h for the per-edge geometry
+    const emq::ff rxx = emq::ff_from_double(rx), ryy = emq::ff_from_double(ry), rzz = emq::ff_from_double(rz);
+    const emq::ff ihh = emq::ff_from_double(ih);
 
     double acc = 0.0, mag = 0.0;
     bool force = false;   // the FP32 form does not apply: recompute in FP64
@@ -594,8 +620,8 @@ __global__ void __launch_bounds__(32 * MQ_WARPS) k_map_fp32(int64_t npairs, cons
                 if (!(tilde && R2 >= 4.0)) {   // else the polygon lies entirely beyond 2h
                     fs.D64 = D64;
                     fs.rr2 = rr2;
-                    fs.dm1 = D64 * D64 - 1.0;
-                    fs.d4 = 4.0 - D64 * D64;
+                    fs.dm1 = emq::ff_from_double(D64 * D64 - 1.0);
+                    fs.d4 = emq::ff_from_double(4.0 - D64 * D64);
                     fs.Df = (float)D64;
                     face_consts(R2, tilde, fs);
                     fs.sign = sd > 0.0 ? 1.f : -1.f;
@@ -606,25 +632,33 @@ __global__ void __launch_bounds__(32 * MQ_WARPS) k_map_fp32(int64_t npairs, cons
         }
         for (int ei = 0; __any_sync(FULL_MASK, ei < ne); ++ei) {
             if (ei < ne) {
-                EdgeD E = edge[e0 + ei];
-                const double a = (E.cm - (E.mx * rx + E.my * ry + E.mz * rz)) * ih;
-                if (a != 0.0) {
-                    const double t0 = (E.ce - (E.ex * rx + E.ey * ry + E.ez * rz)) * ih;
-                    const double t1 = t0 + E.L * ih;
-                    const float A = (float)fabs(a), T0 = (float)t0, T1 = (float)t1;
+                // edge geometry in float-float (see quad32.cuh): A, T0, T1 and
+                // B^2 - 1, 4 - B^2, A^2 - rho^2 each rounded once to FP32
+                const EdgeF H = edge_f[e0 + ei], Lo = edge_fl[e0 + ei];
+                const emq::ff ah = emq::ff_offset_dot(H.cm, Lo.cm, H.mx, Lo.mx, H.my, Lo.my, H.mz, Lo.mz, rxx, ryy, rzz);
+                const emq::ff a = emq::ff_mul(ah, ihh);
+                if (a.hi != 0.f) {
+                    const emq::ff th = emq::ff_offset_dot(H.ce, Lo.ce, H.ex, Lo.ex, H.ey, Lo.ey, H.ez, Lo.ez, rxx, ryy, rzz);
+                    const emq::ff t0 = emq::ff_mul(th, ihh);
+                    const emq::ff t1 = emq::ff_add(t0, emq::ff_mul(emq::ff{H.L, Lo.L}, ihh));
+                    const emq::ff a2 = emq::ff_mul(a, a);
+                    const float A = fabsf(a.hi + a.lo), T0 = t0.hi + t0.lo, T1 = t1.hi + t1.lo;
                     const float B2f = fs.Df * fs.Df + A * A;
-                    const float c1 = (float)(fs.dm1 + a * a), c4 = (float)(fs.d4 - a * a),
-                                cc = (float)(a * a - fs.rr2);
+                    const emq::ff c1x = emq::ff_add(fs.dm1, a2), c4x = emq::ff_add(fs.d4, emq::ff_neg(a2));
+                    const emq::ff ccx = emq::ff_add(a2, emq::ff_neg(emq::ff_from_double(fs.rr2)));
+                    const float c1 = c1x.hi + c1x.lo, c4 = c4x.hi + c4x.lo, cc = ccx.hi + ccx.lo;
                     // signed factor: D/pi, face orientation, side of the edge line, direction along it
-                    const float base = fs.sign * (a > 0.0 ? 1.f : -1.f) * fs.Df * 0.31830988618379067154f;
-                    if ((T0 >= 0.f && T1 >= 0.f) || (T0 <= 0.f && T1 <= 0.f)) {
-                        const float u0 = fabsf(T0), u1 = fabsf(T1);
-                        mq_push_g(q, lane, cnt, fminf(u0, u1), fmaxf(u0, u1), A, B2f, c1, c4, cc,
-                                  T1 >= T0 ? base : -base, fs, tilde, acc, mag);
-                    } else {
-                        const float sc = T1 > T0 ? base : -base;
-                        mq_push_g(q, lane, cnt, 0.f, fabsf(T0), A, B2f, c1, c4, cc, sc, fs, tilde, acc, mag);
-                        mq_push_g(q, lane, cnt, 0.f, fabsf(T1), A, B2f, c1, c4, cc, sc, fs, tilde, acc, mag);
+                    const float base = fs.sign * (a.hi > 0.f ? 1.f : -1.f) * fs.Df * 0.31830988618379067154f;
+                    // the edge's |tau| ranges: one if T0 and T1 lie on one side of
+                    // the foot F, else [0, |T0|] and [0, |T1|]
+                    const float u0 = fabsf(T0), u1 = fabsf(T1);
+                    const bool one_side = (T0 >= 0.f && T1 >= 0.f) || (T0 <= 0.f && T1 <= 0.f);
+                    const float sc = (one_side ? T1 >= T0 : T1 > T0) ? base : -base;
+#pragma unroll 1
+                    for (int part = 0; part < (one_side ? 1 : 2); ++part) {
+                        const float ua = one_side ? fminf(u0, u1) : 0.f;
+                        const float ub = one_side ? fmaxf(u0, u1) : (part ? u1 : u0);
+                        mq_push_g(q, lane, cnt, ua, ub, A, B2f, c1, c4, cc, sc, fs, tilde, acc, mag);
                     }
                 }
             }
@@ -636,19 +670,27 @@ __global__ void __launch_bounds__(32 * MQ_WARPS) k_map_fp32(int64_t npairs, cons
         }
     }
     if (__any_sync(FULL_MASK, cnt > 0)) mq_flush(q, lane, cnt, acc, mag);
-    if (!valid) return;
-    // the integrals were summed with their signs: w = sum (full kernel) or
-    // [P inside] - sum (complement kernel)
-    const double wk = full ? acc : ((inside ? 1.0 : 0.0) - acc);
-    if (inside && !full) mag += 1.0;
-    w[k] = wk;
-    // error bound of the FP32 pass: 12 ulp of every non-negative piece it
-    // summed (pieces are relative-accurate to a few ulp; the factor carries a
-    // 1.5x margin over the largest error/bound ratio seen against FP64)
-    const double est = 12.0 * 5.9604644775390625e-8 * mag;
-    if (force || !(est <= (double)tol * fabs(wk) + 1e-14)) {
-        int slot = atomicAdd(nflag, 1);
-        flagged[slot] = (int32_t)k;
+    bool flag = false;
+    if (valid) {
+        // the integrals were summed with their signs: w = sum (full kernel) or
+        // [P inside] - sum (complement kernel)
+        const double wk = full ? acc : ((inside ? 1.0 : 0.0) - acc);
+        if (inside && !full) mag += 1.0;
+        w[k] = wk;
+        // error bound of the FP32 pass: 12 ulp of every non-negative piece it
+        // summed (pieces are relative-accurate to a few ulp; the factor carries a
+        // 1.5x margin over the largest error/bound ratio seen against FP64)
+        const double est = 12.0 * 5.9604644775390625e-8 * mag;
+        flag = force || !(est <= (double)tol * fabs(wk) + 1e-14);
+    }
+    // one append per warp: the flagged pairs of a warp (mostly of one cell)
+    // stay together in the list, which keeps the FP64 pass's warps coherent
+    const unsigned fm = __ballot_sync(FULL_MASK, flag);
+    if (fm) {
+        int base = 0;
+        if (lane == 0) base = atomicAdd(nflag, __popc(fm));
+        base = __shfl_sync(FULL_MASK, base, 0);
+        if (flag) flagged[base + __popc(fm & ((1u << lane) - 1u))] = (int32_t)k;
     }
 }
 
@@ -712,7 +754,7 @@ EM_EXPORT int map_exact(em_ctx *ctx, const em_pairs *pr, const double *d_x, cons
             EM_CUDA(cudaMemsetAsync(nflag, 0, sizeof(int), ctx->stream));
             k_map_fp32<<<em_grid((n + 31) / 32, MQ_WARPS), 32 * MQ_WARPS, 0, ctx->stream>>>(
                 n, pr->pair_i, pr->pair_j, d_x, d_y, d_z, d_h, v->gen, v->radius, v->cell_face_off,
-                v->face_vert_off, v->plane, v->edge, v->edge_f, (float)p->fp64_threshold, d_w_out, flagged, nflag);
+                v->face_vert_off, v->plane, v->edge_f, v->edge_fl, (float)p->fp64_threshold, d_w_out, flagged, nflag);
             EM_LAUNCHED(ctx);
             if (ctx->timing) {
                 EM_CUDA(cudaEventRecord(ctx->ev[1], ctx->stream));
@@ -828,7 +870,7 @@ EM_EXPORT int map_exact_noalloc(em_ctx *ctx, const em_pairs *pr, const double *d
             EM_CUDA(cudaMemsetAsync(nflag, 0, sizeof(int), ctx->stream));
             k_map_fp32<<<em_grid((n + 31) / 32, MQ_WARPS), 32 * MQ_WARPS, 0, ctx->stream>>>(
                 n, pr->pair_i, pr->pair_j, d_x, d_y, d_z, d_h, v->gen, v->radius, v->cell_face_off,
-                v->face_vert_off, v->plane, v->edge, v->edge_f, (float)p->fp64_threshold, d_w_out, flagged, nflag);
+                v->face_vert_off, v->plane, v->edge_f, v->edge_fl, (float)p->fp64_threshold, d_w_out, flagged, nflag);
             EM_LAUNCHED(ctx);
             const int grid = (int)std::min<int64_t>((n + block - 1) / block, 152 * 16);
             k_map_fp64_flagged<<<grid, block, 0, ctx->stream>>>(nflag, pr->pair_i, pr->pair_j, d_x, d_y, d_z, d_h,

@@ -49,7 +49,13 @@
 
 #include <cuda_runtime.h>
 
+#ifndef EM_NODE_UNROLL
+#define EM_NODE_UNROLL 2   // unroll of the 8-node loop (build-time tuning knob)
+#endif
+
 namespace emq {
+
+constexpr int kNodeUnroll = EM_NODE_UNROLL;
 
 __device__ __forceinline__ float gl_x(int i)
 {
@@ -88,7 +94,7 @@ __device__ __forceinline__ float seg_eval(float sa, float hl, float A, float B2,
     for (int p = 0; p < m; ++p) {
         const float mid = sa + (2.f * p + 1.f) * hl;
         float acc = 0.f;
-#pragma unroll
+#pragma unroll kNodeUnroll
         for (int i = 0; i < 8; ++i) {
             const float s = mid + ((i & 1) ? -hl : hl) * gl_x(i >> 1);
             const float em = expm1f(s);
@@ -118,6 +124,59 @@ __device__ __forceinline__ float seg_eval(float sa, float hl, float A, float B2,
         tot += acc * hl;
     }
     return tot;
+}
+
+// ---------------------------------------------------------------------------
+// Float-float arithmetic (a value held as hi + lo, two FP32 numbers), for the
+// per-edge geometry of the FP32 pass: with the error-free transformations of
+// Knuth (two-sum) and of the FMA product (two-prod), a dot product of
+// float-float operands is accurate to about 2^-48 of its terms, far below
+// the single FP32 rounding the quadrature's inputs need, at a fraction of the
+// cost of FP64 on a part whose FP64 rate is 1/64 of its FP32 rate.
+// ---------------------------------------------------------------------------
+struct ff {
+    float hi, lo;
+};
+
+__device__ __forceinline__ ff ff_two_sum(float a, float b)
+{
+    const float s = a + b;
+    const float v = s - a;
+    return ff{s, (a - (s - v)) + (b - v)};
+}
+__device__ __forceinline__ ff ff_two_prod(float a, float b)
+{
+    const float p = a * b;
+    return ff{p, fmaf(a, b, -p)};
+}
+__device__ __forceinline__ ff ff_add(ff x, ff y)
+{
+    const ff s = ff_two_sum(x.hi, y.hi);
+    return ff_two_sum(s.hi, s.lo + (x.lo + y.lo));
+}
+__device__ __forceinline__ ff ff_neg(ff x) { return ff{-x.hi, -x.lo}; }
+__device__ __forceinline__ ff ff_mul(ff x, ff y)
+{
+    const ff p = ff_two_prod(x.hi, y.hi);
+    return ff_two_sum(p.hi, p.lo + fmaf(x.hi, y.lo, x.lo * y.hi));
+}
+__device__ __forceinline__ ff ff_from_double(double v)
+{
+    const float h = (float)v;
+    return ff{h, (float)(v - (double)h)};
+}
+// c - (mx rx + my ry + mz rz), every operand float-float
+__device__ __forceinline__ ff ff_offset_dot(float ch, float cl, float mxh, float mxl, float myh, float myl, float mzh,
+                                            float mzl, ff rx, ff ry, ff rz)
+{
+    const ff p0 = ff_two_prod(mxh, rx.hi), p1 = ff_two_prod(myh, ry.hi), p2 = ff_two_prod(mzh, rz.hi);
+    float lo = (p0.lo + p1.lo) + p2.lo;
+    lo += fmaf(mxh, rx.lo, mxl * rx.hi) + fmaf(myh, ry.lo, myl * ry.hi) + fmaf(mzh, rz.lo, mzl * rz.hi);
+    const ff s1 = ff_two_sum(p0.hi, p1.hi);
+    const ff s2 = ff_two_sum(s1.hi, p2.hi);
+    lo += s1.lo + s2.lo;
+    const ff d = ff_two_sum(ch, -s2.hi);
+    return ff_two_sum(d.hi, d.lo + (cl - lo));
 }
 
 }  // namespace emq
