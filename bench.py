@@ -280,11 +280,12 @@ WORK = {
     "pseudo_1e6": dict(faces=15.64, faces_used=11.33, edges_used=60.65, subpieces=58.54),
     "sphere_1e5": dict(faces=15.23, faces_used=7.93, edges_used=43.36, subpieces=40.33),
 }
-# FP64 flops (FMA = 2) of the FP32 pass's geometry, counted in its source:
-# per face the inside test and the plane distance, per face within reach the
-# reference distance and the face constants, per edge of those faces A, T0,
-# T1 and the three per-edge constants
-FP64_FLOPS_FACE, FP64_FLOPS_USED_FACE, FP64_FLOPS_EDGE = 13, 36, 22
+# FP64 flops (FMA = 2) of the FP32 pass, counted in its source: per face the
+# inside test and the plane distance (13), per face within reach the
+# reference distance, D^2 - 1, 4 - D^2 and the face constants (45); the edge
+# geometry is float-float FP32 (about 130 FP32 flops per edge of those faces)
+FP64_FLOPS_FACE, FP64_FLOPS_USED_FACE, FP64_FLOPS_EDGE = 13, 45, 0
+FP32_FLOPS_EDGE = 130
 # FP32 flops per quadrature node (common part 15, piece-2 integrand 21), with
 # expm1, sqrt and about six reciprocals on the SFU besides
 FP32_FLOPS_NODE = 36
@@ -294,24 +295,27 @@ FP64_PEAK_TFLOPS = 1.25
 FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.07e9 / 1e12
 # DRAM traffic of one k_map_fp32 launch per pair (ncu, dram__bytes_read.sum +
 # dram__bytes_write.sum over the pairs of the launch), per workload
-TRAFFIC_PER_PAIR = {"pseudo_1e6": 138.17, "sphere_1e5": 80.06}
+TRAFFIC_PER_PAIR = {"sphere_1e5": 64.3}
 
 
 def roofline(npairs, ms, precision, workload):
     """Dominant kernel of map_exact.  Mixed mode: the FP32 pass k_map_fp32,
-    whose binding pipe is FP64 (its geometry; ncu: FP64 pipe ~50% busy, FMA
-    ~10%), so the roofline is the FP64 rate with the FP64 flops counted above;
-    the FP32 quadrature's rate is reported beside it.  FP64 mode: the closed
+    whose busiest pipe is FP64 (per-face geometry and face constants; ncu:
+    FP64 pipe ~70% busy, FMA ~33%, issue ~67%), so the roofline is the FP64
+    rate with the FP64 flops counted above; the FP32 work's rate is reported
+    beside it.  FP64 mode: the closed
     form k_map_fp64, with the same geometry count over all faces and edges
     (its transcendental calls are not counted)."""
     wk = WORK[workload]
     if precision == "mixed":
         f64 = (FP64_FLOPS_FACE * wk["faces"] + FP64_FLOPS_USED_FACE * wk["faces_used"]
                + FP64_FLOPS_EDGE * wk["edges_used"])
-        f32 = FP32_FLOPS_NODE * 8 * wk["subpieces"]
+        f32 = FP32_FLOPS_NODE * 8 * wk["subpieces"] + FP32_FLOPS_EDGE * wk["edges_used"]
     else:
+        # the closed form: per face the plane distance, per edge of every face
+        # the FP64 geometry (22 flops; transcendental calls not counted)
         edges_all = wk["edges_used"] * wk["faces"] / wk["faces_used"]
-        f64 = (FP64_FLOPS_FACE + FP64_FLOPS_USED_FACE) * wk["faces"] + FP64_FLOPS_EDGE * edges_all
+        f64 = 13 * wk["faces"] + 22 * edges_all
         f32 = 0.0
     t = ms * 1e-3
     achieved = npairs * f64 / t / 1e12
