@@ -23,6 +23,7 @@ constexpr int WCAND = 256;   // candidate list (power of two for the bitonic sor
 struct WCell {
     double pl[WMAXP][4];
     double v[2][WMAXV][3];
+    float vf[WMAXV][4];   // the current vertices rounded to FP32, w = |x| + |y| + |z|
     double f[WMAXV];
     double cd2[WCAND];
     int cid[WCAND];
@@ -37,6 +38,20 @@ __device__ __forceinline__ unsigned lanemask_lt() { return (1u << (threadIdx.x &
 __device__ __forceinline__ bool has_edge(const uint8_t *t, uint8_t a, uint8_t b)
 {
     return (t[0] == a && t[1] == b) || (t[1] == a && t[2] == b) || (t[2] == a && t[0] == b);
+}
+
+// Refresh the FP32 copy of the current vertices (all lanes).
+__device__ __forceinline__ void wsync_vf(WCell &c)
+{
+    const int cur = c.cur;
+    for (int t = threadIdx.x & 31; t < c.nt; t += 32) {
+        const float x = (float)c.v[cur][t][0], y = (float)c.v[cur][t][1], z = (float)c.v[cur][t][2];
+        c.vf[t][0] = x;
+        c.vf[t][1] = y;
+        c.vf[t][2] = z;
+        c.vf[t][3] = fabsf(x) + fabsf(y) + fabsf(z);
+    }
+    __syncwarp();
 }
 
 __device__ void wcell_box(WCell &c, const double *box, double gx, double gy, double gz)
@@ -71,6 +86,7 @@ __device__ void wcell_box(WCell &c, const double *box, double gx, double gy, dou
         }
     }
     __syncwarp();
+    wsync_vf(c);
 }
 
 // Drop planes no vertex refers to (one lane; rare).
@@ -106,6 +122,18 @@ __device__ int wclip(WCell &c, double nx, double ny, double nz, double d, int id
 {
     const int lane = threadIdx.x & 31;
     const int cur = c.cur, nxt = cur ^ 1, nt = c.nt;
+    {
+        // FP32 side test: a bisector that every vertex clears by the band (far
+        // above the FP32 rounding of n, v, d and the products) cuts nothing
+        const float nxf = (float)nx, nyf = (float)ny, nzf = (float)nz, df = (float)d;
+        const float nmax = fmaxf(fmaxf(fabsf(nxf), fabsf(nyf)), fabsf(nzf));
+        bool maybe = false;
+        for (int t = lane; t < nt; t += 32) {
+            const float ff = nxf * c.vf[t][0] + nyf * c.vf[t][1] + nzf * c.vf[t][2] - df;
+            maybe = maybe || ff > -1e-5f * (nmax * c.vf[t][3] + fabsf(df));
+        }
+        if (!__any_sync(0xffffffffu, maybe)) return 0;
+    }
     bool any = false;
     for (int t = lane; t < nt; t += 32) {
         double f = nx * c.v[cur][t][0] + ny * c.v[cur][t][1] + nz * c.v[cur][t][2] - d;
@@ -191,6 +219,7 @@ __device__ int wclip(WCell &c, double nx, double ny, double nz, double d, int id
         c.cur = nxt;
     }
     __syncwarp();
+    wsync_vf(c);
     return 1;
 }
 
@@ -221,10 +250,23 @@ __device__ int gather(WCell &c, const em::ChunkTree &T, const double *__restrict
     const int lane = threadIdx.x & 31;
     int n = 0;
     float R = (float)sqrt(hi2) + margin;
+    // FP32 window test on the rounded positions: points clearly outside the
+    // window (by a band above the rounding of the coordinates) skip the FP64
+    const float gxf = (float)gx, gyf = (float)gy, gzf = (float)gz;
+    const float gabs = fabsf(gxf) + fabsf(gyf) + fabsf(gzf);
+    const float rhi = sqrtf((float)hi2) * (1.f + 1e-5f) + 1e-5f * gabs;
+    const float rlo = lo2 > 0.0 ? sqrtf((float)lo2) * (1.f - 1e-5f) - 1e-5f * gabs : -1.f;
     em::warp_traverse(T, (float)gx, (float)gy, (float)gz, R * R, INT64_MAX, [&](int64_t k, bool valid) {
         bool hit = false;
         double d2 = 0.0;
-        if (valid && k != s) {
+        bool cand = valid && k != s;
+        if (cand) {
+            const float4 pk = T.pts[k];
+            const float ex = pk.x - gxf, ey = pk.y - gyf, ez = pk.z - gzf;
+            const float rf = sqrtf(ex * ex + ey * ey + ez * ez);
+            cand = rf <= rhi && rf >= rlo;
+        }
+        if (cand) {
             double dx = xs[k] - gx, dy = ys[k] - gy, dz = zs[k] - gz;
             d2 = dx * dx + dy * dy + dz * dz;
             hit = d2 >= lo2 && d2 < hi2;
@@ -245,18 +287,21 @@ __device__ int gather(WCell &c, const em::ChunkTree &T, const double *__restrict
     return n > WCAND ? -1 : n;
 }
 
-// Bitonic sort of the first n candidates by (d^2, index), padded to WCAND.
+// Bitonic sort of the first n candidates by (d^2, index), padded with
+// (inf, max) up to the next power of two (at most WCAND).
 __device__ void sort_cand(WCell &c, int n)
 {
     const int lane = threadIdx.x & 31;
-    for (int i = n + lane; i < WCAND; i += 32) {
+    int len = 2;
+    while (len < n) len <<= 1;
+    for (int i = n + lane; i < len; i += 32) {
         c.cd2[i] = INFINITY;
         c.cid[i] = 0x7fffffff;
     }
     __syncwarp();
-    for (int size = 2; size <= WCAND; size <<= 1) {
+    for (int size = 2; size <= len; size <<= 1) {
         for (int stride = size >> 1; stride > 0; stride >>= 1) {
-            for (int i = lane; i < WCAND / 2; i += 32) {
+            for (int i = lane; i < len / 2; i += 32) {
                 int lo = 2 * i - (i & (stride - 1));
                 int hi = lo + stride;
                 bool up = ((lo & size) == 0);
@@ -286,21 +331,31 @@ __device__ int gather_cutting(WCell &c, const em::ChunkTree &T, const double *__
 {
     const int lane = threadIdx.x & 31;
     const int cur = c.cur, nt = c.nt;
+    // The pruning tests run in FP32 with margins above the rounding of the
+    // coordinates (S below is a bound on their magnitudes): a box or point is
+    // dropped only where the exact test would drop it too.
+    const float gxf = (float)gx, gyf = (float)gy, gzf = (float)gz;
+    const float gabs = fabsf(gxf) + fabsf(gyf) + fabsf(gzf);
+    const float rhi = sqrtf((float)hi2) * (1.f + 1e-5f) + 1e-5f * gabs;
+    const float rlo = skip2 > 0.0 ? sqrtf((float)skip2) * (1.f - 1e-5f) - 1e-5f * gabs : -1.f;
     auto box_can_cut = [&](const float4 lo, const float4 hi) -> bool {
-        const double lx = (double)lo.x - gx, ly = (double)lo.y - gy, lz = (double)lo.z - gz;
-        const double hx = (double)hi.x - gx, hy = (double)hi.y - gy, hz = (double)hi.z - gz;
-        {   // the whole box at or beyond the window's outer radius
-            double dx = fmax(fmax(lx, -hx), 0.0), dy = fmax(fmax(ly, -hy), 0.0), dz = fmax(fmax(lz, -hz), 0.0);
-            if (dx * dx + dy * dy + dz * dz >= hi2 * (1.0 + 1e-9)) return false;
+        const float babs = fabsf(lo.x) + fabsf(lo.y) + fabsf(lo.z) + fabsf(hi.x) + fabsf(hi.y) + fabsf(hi.z);
+        const float lx = lo.x - gxf, ly = lo.y - gyf, lz = lo.z - gzf;
+        const float hx = hi.x - gxf, hy = hi.y - gyf, hz = hi.z - gzf;
+        {   // the whole box beyond the window's outer radius
+            float dx = fmaxf(fmaxf(lx, -hx), 0.f), dy = fmaxf(fmaxf(ly, -hy), 0.f), dz = fmaxf(fmaxf(lz, -hz), 0.f);
+            if (sqrtf(dx * dx + dy * dy + dz * dz) > rhi + 1e-5f * babs) return false;
         }
+        // some vertex nearer to the box than to the site
         for (int t = 0; t < nt; ++t) {
-            const double *v = c.v[cur][t];
-            double dx = fmax(fmax(lx - v[0], v[0] - hx), 0.0);
-            double dy = fmax(fmax(ly - v[1], v[1] - hy), 0.0);
-            double dz = fmax(fmax(lz - v[2], v[2] - hz), 0.0);
-            double db = dx * dx + dy * dy + dz * dz;
-            double dg = v[0] * v[0] + v[1] * v[1] + v[2] * v[2];
-            if (db < dg) return true;
+            const float vx = c.vf[t][0], vy = c.vf[t][1], vz = c.vf[t][2];
+            float dx = fmaxf(fmaxf(lx - vx, vx - hx), 0.f);
+            float dy = fmaxf(fmaxf(ly - vy, vy - hy), 0.f);
+            float dz = fmaxf(fmaxf(lz - vz, vz - hz), 0.f);
+            const float db = dx * dx + dy * dy + dz * dz;
+            const float dg = vx * vx + vy * vy + vz * vz;
+            const float S = gabs + babs + c.vf[t][3];
+            if (db < dg + 1e-5f * S * S) return true;
         }
         return false;
     };
@@ -327,7 +382,24 @@ __device__ int gather_cutting(WCell &c, const em::ChunkTree &T, const double *__
             int64_t k = node * 32 + lane;
             bool hit = false;
             double d2 = 0.0;
-            if (k < T.count[0] && k != s) {
+            bool cand = k < T.count[0] && k != s;
+            if (cand) {
+                // FP32: inside the window and some vertex possibly beyond the bisector
+                const float4 pk = T.pts[k];
+                const float ex = pk.x - gxf, ey = pk.y - gyf, ez = pk.z - gzf;
+                const float rf = sqrtf(ex * ex + ey * ey + ez * ez);
+                cand = rf <= rhi && rf >= rlo;
+                if (cand) {
+                    const float df = 0.5f * rf * rf, rabs = fabsf(ex) + fabsf(ey) + fabsf(ez);
+                    bool maybe = false;
+                    for (int t = 0; t < nt && !maybe; ++t) {
+                        const float ff = ex * c.vf[t][0] + ey * c.vf[t][1] + ez * c.vf[t][2] - df;
+                        maybe = ff > -1e-5f * (gabs + rabs + c.vf[t][3]) * (c.vf[t][3] + rabs);
+                    }
+                    cand = maybe;
+                }
+            }
+            if (cand) {
                 double rx = xs[k] - gx, ry = ys[k] - gy, rz = zs[k] - gz;
                 d2 = rx * rx + ry * ry + rz * rz;
                 if (d2 >= skip2 && d2 < hi2) {
