@@ -250,33 +250,36 @@ __device__ int gather(WCell &c, const em::ChunkTree &T, const double *__restrict
     const int lane = threadIdx.x & 31;
     int n = 0;
     float R = (float)sqrt(hi2) + margin;
-    // FP32 window test on the rounded positions: points clearly outside the
-    // window (by a band above the rounding of the coordinates) skip the FP64
+    // The window test runs in FP32 on the rounded positions and keeps every
+    // point whose FP32 distance lies within the window widened by a band above
+    // the rounding of the coordinates: a superset of the exact window, which
+    // is all the callers need (every generator in the window gets clipped).
+    // The sort key is the FP32 squared distance; only near-coincident points
+    // are checked in FP64.
     const float gxf = (float)gx, gyf = (float)gy, gzf = (float)gz;
     const float gabs = fabsf(gxf) + fabsf(gyf) + fabsf(gzf);
     const float rhi = sqrtf((float)hi2) * (1.f + 1e-5f) + 1e-5f * gabs;
     const float rlo = lo2 > 0.0 ? sqrtf((float)lo2) * (1.f - 1e-5f) - 1e-5f * gabs : -1.f;
-    em::warp_traverse(T, (float)gx, (float)gy, (float)gz, R * R, INT64_MAX, [&](int64_t k, bool valid) {
+    const float rtiny = 1e-5f * (gabs + rhi);
+    em::warp_traverse(T, gxf, gyf, gzf, R * R, INT64_MAX, [&](int64_t k, bool valid) {
         bool hit = false;
-        double d2 = 0.0;
-        bool cand = valid && k != s;
-        if (cand) {
+        float d2f = 0.f;
+        if (valid && k != s) {
             const float4 pk = T.pts[k];
             const float ex = pk.x - gxf, ey = pk.y - gyf, ez = pk.z - gzf;
-            const float rf = sqrtf(ex * ex + ey * ey + ez * ez);
-            cand = rf <= rhi && rf >= rlo;
-        }
-        if (cand) {
-            double dx = xs[k] - gx, dy = ys[k] - gy, dz = zs[k] - gz;
-            d2 = dx * dx + dy * dy + dz * dz;
-            hit = d2 >= lo2 && d2 < hi2;
-            if (d2 == 0.0) status |= emv::VS_COINCIDENT;
+            d2f = ex * ex + ey * ey + ez * ez;
+            const float rf = sqrtf(d2f);
+            hit = rf <= rhi && rf >= rlo;
+            if (rf < rtiny) {   // possibly the same point
+                const double dx = xs[k] - gx, dy = ys[k] - gy, dz = zs[k] - gz;
+                if (dx * dx + dy * dy + dz * dz == 0.0) status |= emv::VS_COINCIDENT;
+            }
         }
         unsigned m = __ballot_sync(0xffffffffu, hit);
         if (hit) {
             int pos = n + __popc(m & lanemask_lt());
             if (pos < WCAND) {
-                c.cd2[pos] = d2;
+                c.cd2[pos] = (double)d2f;
                 c.cid[pos] = (int)k;
             }
         }
@@ -496,7 +499,9 @@ __device__ int wbuild_cell(WCell &c, const em::ChunkTree &T, const double *__res
             const double bx = box[1] - box[0], by = box[3] - box[2], bz = box[5] - box[4];
             kth = 0.01 * (bx * bx + by * by + bz * bz);
         }
-        R2 = kth * cbrt(1.5 * K / 8.0) * cbrt(1.5 * K / 8.0);
+        // the chunk's own 8th nearest overestimates the local spacing (its
+        // members lie mostly to one side), hence the factor 1/4
+        R2 = 0.25 * kth * cbrt(1.5 * K / 8.0) * cbrt(1.5 * K / 8.0);
     }
     // stage 1: shrink or grow R until the candidates fit and number at least K
     double lo_ok = 0.0, hi_bad = INFINITY;
@@ -511,7 +516,7 @@ __device__ int wbuild_cell(WCell &c, const em::ChunkTree &T, const double *__res
         }
         if (nc < K && nc < n - 1 && hi_bad == INFINITY && it < 40) {
             lo_ok = R2;
-            R2 *= 3.0;
+            R2 *= 2.0;
             continue;
         }
         break;
