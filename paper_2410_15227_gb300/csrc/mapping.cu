@@ -344,6 +344,10 @@ __global__ void __launch_bounds__(128) k_map_fp64(int64_t npairs, const int32_t 
 
 // FP64 recompute of the pairs the FP32 pass flagged; the count is read on
 // the device, so the launch needs no host synchronisation (grid-stride loop).
+// A list entry k >= 0 is recomputed with the FP64 complement form (faces
+// beyond 2h skipped; its rounding, about 1e-13, is far inside the mixed
+// mode's tolerance); an entry ~k (< 0) marks a particle in a face plane,
+// recomputed with the full form, for which such a face carries nothing.
 __global__ void __launch_bounds__(128) k_map_fp64_flagged(const int *__restrict__ nflag, const int32_t *__restrict__ pi,
                                                           const int32_t *__restrict__ pj, const double *__restrict__ x,
                                                           const double *__restrict__ y, const double *__restrict__ z,
@@ -357,11 +361,15 @@ __global__ void __launch_bounds__(128) k_map_fp64_flagged(const int *__restrict_
 {
     const int64_t n = *nflag;
     for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < n; t += (int64_t)gridDim.x * blockDim.x) {
-        const int64_t k = list[t];
+        const int32_t code = list[t];
+        const int64_t k = code >= 0 ? code : ~code;
         const int i = pi[k], j = pj[k];
         double err;
-        w[k] = pair_weight<double, true>(x[i] - gen[3 * j], y[i] - gen[3 * j + 1], z[i] - gen[3 * j + 2], h[i],
-                                         radius[j], cfo[j], cfo[j + 1], fvo, plane, edge, err);
+        const double rx = x[i] - gen[3 * j], ry = y[i] - gen[3 * j + 1], rz = z[i] - gen[3 * j + 2];
+        w[k] = code >= 0 ? pair_weight<double, false>(rx, ry, rz, h[i], radius[j], cfo[j], cfo[j + 1], fvo, plane,
+                                                      edge, err)
+                         : pair_weight<double, true>(rx, ry, rz, h[i], radius[j], cfo[j], cfo[j + 1], fvo, plane,
+                                                     edge, err);
     }
 }
 
@@ -690,7 +698,7 @@ __global__ void __launch_bounds__(32 * MQ_WARPS) k_map_fp32(int64_t npairs, cons
         int base = 0;
         if (lane == 0) base = atomicAdd(nflag, __popc(fm));
         base = __shfl_sync(FULL_MASK, base, 0);
-        if (flag) flagged[base + __popc(fm & ((1u << lane) - 1u))] = (int32_t)k;
+        if (flag) flagged[base + __popc(fm & ((1u << lane) - 1u))] = force ? ~(int32_t)k : (int32_t)k;
     }
 }
 
