@@ -295,7 +295,7 @@ FP64_PEAK_TFLOPS = 1.25
 FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.07e9 / 1e12
 # DRAM traffic of one k_map_fp32 launch per pair (ncu, dram__bytes_read.sum +
 # dram__bytes_write.sum over the pairs of the launch), per workload
-TRAFFIC_PER_PAIR = {"sphere_1e5": 64.3}
+TRAFFIC_PER_PAIR = {"pseudo_1e6": 109.2, "sphere_1e5": 64.3}
 
 
 def roofline(npairs, ms, precision, workload):
