@@ -14,17 +14,30 @@ using namespace em;
 // Derived cell geometry in each generator's frame
 // ---------------------------------------------------------------------------
 
-__global__ void k_prepare_cells(int64_t ncell, const double *__restrict__ gen, const int64_t *__restrict__ cfo,
-                                const int64_t *__restrict__ fvo, const double *__restrict__ verts,
-                                const double *__restrict__ normals, double *__restrict__ radius,
-                                PlaneD *__restrict__ plane, EdgeD *__restrict__ edge, PlaneF *__restrict__ plane_f,
-                                EdgeF *__restrict__ edge_f, EdgeF *__restrict__ edge_fl)
+// One thread per face (adjacent threads write adjacent records); the face's
+// cell by binary search in the cell offsets.  The cell radius is the largest
+// |V - g| over its vertices: every face raises its cell's r^2 with an atomic
+// max on the bit pattern (non-negative doubles order like their bits), so the
+// result does not depend on the order of the faces.
+__global__ void k_prepare_cells(int64_t nface, int64_t ncell, const double *__restrict__ gen,
+                                const int64_t *__restrict__ cfo, const int64_t *__restrict__ fvo,
+                                const double *__restrict__ verts, const double *__restrict__ normals,
+                                unsigned long long *__restrict__ r2bits, PlaneD *__restrict__ plane,
+                                EdgeD *__restrict__ edge, PlaneF *__restrict__ plane_f, EdgeF *__restrict__ edge_f,
+                                EdgeF *__restrict__ edge_fl)
 {
-    int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-    if (j >= ncell) return;
+    const int64_t f = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (f >= nface) return;
+    int64_t lo = 0, hi = ncell;   // cfo[lo] <= f < cfo[hi]
+    while (hi - lo > 1) {
+        const int64_t mid = (lo + hi) >> 1;
+        if (cfo[mid] <= f) lo = mid;
+        else hi = mid;
+    }
+    const int64_t j = lo;
     double gx = gen[3 * j], gy = gen[3 * j + 1], gz = gen[3 * j + 2];
     double r2max = 0.0;
-    for (int64_t f = cfo[j]; f < cfo[j + 1]; ++f) {
+    {
         double nx = normals[3 * f], ny = normals[3 * f + 1], nz = normals[3 * f + 2];
         int64_t v0 = fvo[f], v1 = fvo[f + 1];
         double c = nx * (verts[3 * v0] - gx) + ny * (verts[3 * v0 + 1] - gy) + nz * (verts[3 * v0 + 2] - gz);
@@ -82,7 +95,14 @@ __global__ void k_prepare_cells(int64_t ncell, const double *__restrict__ gen, c
             edge_fl[k] = G;
         }
     }
-    radius[j] = sqrt(r2max);
+    atomicMax(r2bits + j, (unsigned long long)__double_as_longlong(r2max));
+}
+
+__global__ void k_radius_finish(int64_t ncell, double *__restrict__ radius)
+{
+    const int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (j >= ncell) return;
+    radius[j] = sqrt(radius[j]);   // the bits hold r^2 as a double
 }
 
 int em_prepare_cells(em_ctx *ctx, em_voronoi *v)
@@ -94,9 +114,14 @@ int em_prepare_cells(em_ctx *ctx, em_voronoi *v)
     EM_TRY(v->mem.alloc(&v->edge_f, v->nfv));
     EM_TRY(v->mem.alloc(&v->edge_fl, v->nfv));
     if (v->ncell) {
-        k_prepare_cells<<<em_grid(v->ncell, 128), 128, 0, ctx->stream>>>(
-            v->ncell, v->gen, v->cell_face_off, v->face_vert_off, v->verts, v->normals, v->radius, v->plane,
-            v->edge, v->plane_f, v->edge_f, v->edge_fl);
+        EM_CUDA(cudaMemsetAsync(v->radius, 0, v->ncell * sizeof(double), ctx->stream));
+        if (v->nface) {
+            k_prepare_cells<<<em_grid(v->nface, 128), 128, 0, ctx->stream>>>(
+                v->nface, v->ncell, v->gen, v->cell_face_off, v->face_vert_off, v->verts, v->normals,
+                (unsigned long long *)v->radius, v->plane, v->edge, v->plane_f, v->edge_f, v->edge_fl);
+            EM_LAUNCHED(ctx);
+        }
+        k_radius_finish<<<em_grid(v->ncell, 256), 256, 0, ctx->stream>>>(v->ncell, v->radius);
         EM_LAUNCHED(ctx);
     }
     return EM_OK;

@@ -13,10 +13,10 @@
 // warp walk of the generators' box hierarchy and clipped nearest first.  The
 // cell is exact once 2 R_max is below the search radius, R_max being its
 // farthest vertex: no generator farther than 2 R_max can cut it.  Otherwise
-// the shell up to 2 R_max is clipped in as well.  Pass 1 (count) builds the
-// cell, records the bisectors that actually cut it and its size; pass 2
-// (emit) replays exactly those clips (bit-identical state) and writes the
-// faces at the scanned offsets.
+// the shell up to 2 R_max is clipped in as well.  The build pass writes each
+// finished cell's faces into a scratch slot of fixed capacity (64 faces, 384
+// face-vertices: every vertex belongs to three faces) and its counts; after
+// the scan of the counts, a copy pass moves the slots to the cells' offsets.
 #include <cmath>
 
 #include "common.cuh"
@@ -34,13 +34,90 @@ using emw::WCell;
 
 constexpr int VW = 2;   // warps (cells) per block
 
-__global__ void __launch_bounds__(32 * VW) k_voronoi_count(int64_t ngen, em::ChunkTree T, const double *__restrict__ xs,
+// Capacity of a cell's scratch slot: faces (planes) and face-vertices (every
+// vertex belongs to three faces).
+constexpr int SLOT_F = emw::WMAXP;
+constexpr int SLOT_FV = 3 * emw::WMAXV;
+
+// Write the faces of the finished cell c: per face its unit normal, the
+// neighbour id and the offset of its vertex loop, the loop's vertices (CCW
+// seen from outside, absolute coordinates) from fvbase on; returns the counts
+// and the volume (divergence theorem).  Faces beyond fcap or vertices beyond
+// fvcap set bad.
+__device__ void emit_faces(const WCell &c, double gx, double gy, double gz, int fcap, int fvcap,
+                           int32_t *__restrict__ fvo, double *__restrict__ verts, double *__restrict__ normals,
+                           int64_t *__restrict__ nbr, int &nf, int &nfv, double &vol, bool &bad)
+{
+    const int lane = threadIdx.x & 31;
+    int fbase = 0, fvbase = 0;
+    double v = 0.0;
+    uint8_t loop[WMAXV_LOOP];
+    bool err = false;
+    for (int r = 0; r < c.np; r += 32) {
+        int q = r + lane;
+        int n = q < c.np ? emw::wface_loop(c, q, loop, WMAXV_LOOP) : 0;
+        if (n < 0) err = true;
+        bool face = n >= 3;
+        unsigned m = __ballot_sync(0xffffffffu, face);
+        int fi = fbase + __popc(m & emw::lanemask_lt());
+        int len = face ? n : 0, incl = len;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            int t = __shfl_up_sync(0xffffffffu, incl, o);
+            if (lane >= o) incl += t;
+        }
+        int fvi = fvbase + incl - len;
+        if (face) {
+            if (fi >= fcap || fvi + n > fvcap) {
+                err = true;
+            } else {
+                const int cur = c.cur;
+                double nx = c.pl[q][0], ny = c.pl[q][1], nz = c.pl[q][2];
+                double ln = sqrt(nx * nx + ny * ny + nz * nz);
+                nx /= ln;
+                ny /= ln;
+                nz /= ln;
+                normals[3 * fi] = nx;
+                normals[3 * fi + 1] = ny;
+                normals[3 * fi + 2] = nz;
+                nbr[fi] = c.pid[q];
+                fvo[fi] = fvi;
+                double ax = 0.0, ay = 0.0, az = 0.0;   // twice the vector area
+                for (int i = 0; i < n; ++i) {
+                    const double *pa = c.v[cur][loop[i]], *pb = c.v[cur][loop[(i + 1) % n]];
+                    ax += pa[1] * pb[2] - pa[2] * pb[1];
+                    ay += pa[2] * pb[0] - pa[0] * pb[2];
+                    az += pa[0] * pb[1] - pa[1] * pb[0];
+                    verts[3 * (fvi + i)] = pa[0] + gx;
+                    verts[3 * (fvi + i) + 1] = pa[1] + gy;
+                    verts[3 * (fvi + i) + 2] = pa[2] + gz;
+                }
+                double area = 0.5 * (ax * nx + ay * ny + az * nz);
+                v += area * (c.pl[q][3] / ln) / 3.0;
+            }
+        }
+        fbase += __popc(m);
+        fvbase += __shfl_sync(0xffffffffu, incl, 31);
+    }
+    bad = __any_sync(0xffffffffu, err);
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    nf = fbase;
+    nfv = fvbase;
+    vol = v;
+}
+
+// One warp per cell (sorted index s): build the cell, write its faces into
+// the cell's scratch slot, its counts, generator and volume.
+__global__ void __launch_bounds__(32 * VW) k_voronoi_build(int64_t ngen, em::ChunkTree T, const double *__restrict__ xs,
                                                            const double *__restrict__ ys, const double *__restrict__ zs,
                                                            const int32_t *__restrict__ perm, double xlo, double xhi,
                                                            double ylo, double yhi, double zlo, double zhi, int K,
                                                            float margin, int64_t *__restrict__ nface,
-                                                           int64_t *__restrict__ nfv, int32_t *__restrict__ clips,
-                                                           int32_t *__restrict__ nclips, int *__restrict__ status_or)
+                                                           int64_t *__restrict__ nfv, int32_t *__restrict__ s_fvo,
+                                                           double *__restrict__ s_verts, double *__restrict__ s_normals,
+                                                           int64_t *__restrict__ s_nbr, double *__restrict__ volume,
+                                                           double *__restrict__ gen, int *__restrict__ status_or)
 {
     __shared__ WCell cells[VW];
     const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -54,30 +131,22 @@ __global__ void __launch_bounds__(32 * VW) k_voronoi_count(int64_t ngen, em::Chu
     }
     const double box[6] = {xlo, xhi, ylo, yhi, zlo, zhi};
     int nclip = 0;
-    int st = emw::wbuild_cell(c, T, xs, ys, zs, perm, s, box, K, margin, clips + s * MAXCLIP, nclip);
-    int64_t nf = 0, nv = 0;
+    int st = emw::wbuild_cell(c, T, xs, ys, zs, perm, s, box, K, margin, nullptr, nclip);
+    int nf = 0, nv = 0;
+    double vol = 0.0;
     if (!st) {
-        uint8_t loop[WMAXV_LOOP];
         bool bad = false;
-        for (int q = lane; q < c.np; q += 32) {
-            int n = emw::wface_loop(c, q, loop, WMAXV_LOOP);
-            if (n < 0) bad = true;
-            if (n >= 3) {
-                ++nf;
-                nv += n;
-            }
-        }
-        if (__any_sync(0xffffffffu, bad)) st |= VS_TOPOLOGY;
-#pragma unroll
-        for (int o = 16; o > 0; o >>= 1) {
-            nf += __shfl_xor_sync(0xffffffffu, nf, o);
-            nv += __shfl_xor_sync(0xffffffffu, nv, o);
-        }
+        emit_faces(c, xs[s], ys[s], zs[s], SLOT_F, SLOT_FV, s_fvo + s * SLOT_F, s_verts + s * (3 * SLOT_FV),
+                   s_normals + s * (3 * SLOT_F), s_nbr + s * SLOT_F, nf, nv, vol, bad);
+        if (bad) st |= VS_TOPOLOGY;
     }
     if (lane == 0) {
-        nclips[s] = nclip;
         nface[j] = nf;
         nfv[j] = nv;
+        volume[j] = vol;
+        gen[3 * j] = xs[s];
+        gen[3 * j + 1] = ys[s];
+        gen[3 * j + 2] = zs[s];
         if (st) {
             atomicOr(status_or, st);
             atomicMin(status_or + 1, (int)s);   // first failing cell (sorted index)
@@ -85,107 +154,26 @@ __global__ void __launch_bounds__(32 * VW) k_voronoi_count(int64_t ngen, em::Chu
     }
 }
 
-__global__ void __launch_bounds__(32 * VW) k_voronoi_emit(int64_t ngen, const double *__restrict__ xs,
-                                                          const double *__restrict__ ys, const double *__restrict__ zs,
-                                                          const int32_t *__restrict__ perm, double xlo, double xhi,
-                                                          double ylo, double yhi, double zlo, double zhi,
-                                                          const int32_t *__restrict__ clips,
-                                                          const int32_t *__restrict__ nclips,
-                                                          const int64_t *__restrict__ cell_face_off,
-                                                          const int64_t *__restrict__ cell_fv_off,
-                                                          int64_t *__restrict__ face_vert_off, double *__restrict__ verts,
-                                                          double *__restrict__ normals, int64_t *__restrict__ nbr,
-                                                          double *__restrict__ volume, double *__restrict__ gen,
-                                                          int *__restrict__ status_or)
+// One warp per cell: copy its scratch slot to the cell's scanned offsets.
+__global__ void k_voronoi_compact(int64_t ngen, const int32_t *__restrict__ perm,
+                                  const int64_t *__restrict__ cell_face_off, const int64_t *__restrict__ cell_fv_off,
+                                  const int32_t *__restrict__ s_fvo, const double *__restrict__ s_verts,
+                                  const double *__restrict__ s_normals, const int64_t *__restrict__ s_nbr,
+                                  int64_t *__restrict__ face_vert_off, double *__restrict__ verts,
+                                  double *__restrict__ normals, int64_t *__restrict__ nbr)
 {
-    __shared__ WCell cells[VW];
-    const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int64_t s = blockIdx.x * (int64_t)VW + w;
+    const int64_t s = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
+    const int lane = threadIdx.x & 31;
     if (s >= ngen) return;
-    WCell &c = cells[w];
-    const double box[6] = {xlo, xhi, ylo, yhi, zlo, zhi};
-    const double gx = xs[s], gy = ys[s], gz = zs[s];
-    const int ncl = nclips[s];
     const int64_t j = perm[s];
-    if (ncl < 0 || ncl > MAXCLIP || j < 0 || j >= ngen) {
-        if (lane == 0) atomicOr(status_or, VS_BOUNDS);
-        return;
+    const int64_t f0 = cell_face_off[j], fv0 = cell_fv_off[j];
+    const int nf = (int)(cell_face_off[j + 1] - f0), nv = (int)(cell_fv_off[j + 1] - fv0);
+    for (int f = lane; f < nf; f += 32) {
+        face_vert_off[f0 + f] = fv0 + s_fvo[s * SLOT_F + f];
+        nbr[f0 + f] = s_nbr[s * SLOT_F + f];
     }
-    emw::wcell_box(c, box, gx, gy, gz);
-    const int32_t *cl = clips + s * MAXCLIP;
-    for (int q = 0; q < ncl; ++q) {
-        int k = cl[q];
-        if (k < 0 || k >= ngen) {
-            if (lane == 0) atomicOr(status_or, VS_BOUNDS);
-            return;
-        }
-        double dx = xs[k] - gx, dy = ys[k] - gy, dz = zs[k] - gz;
-        if (emw::wclip(c, dx, dy, dz, 0.5 * (dx * dx + dy * dy + dz * dz), perm[k]) < 0) {
-            if (lane == 0) atomicOr(status_or, VS_BOUNDS);
-            return;
-        }
-    }
-    if (lane == 0) {
-        gen[3 * j] = gx;
-        gen[3 * j + 1] = gy;
-        gen[3 * j + 2] = gz;
-    }
-    const int64_t f0 = cell_face_off[j], f_end = cell_face_off[j + 1];
-    const int64_t fv0 = cell_fv_off[j], fv_end = cell_fv_off[j + 1];
-    int64_t fbase = f0, fvbase = fv0;
-    double vol = 0.0;
-    uint8_t loop[WMAXV_LOOP];
-    bool bad = false;
-    for (int r = 0; r < c.np; r += 32) {
-        int q = r + lane;
-        int n = q < c.np ? emw::wface_loop(c, q, loop, WMAXV_LOOP) : 0;
-        bool face = n >= 3;
-        unsigned m = __ballot_sync(0xffffffffu, face);
-        int64_t fi = fbase + __popc(m & emw::lanemask_lt());
-        // exclusive scan of loop lengths over the lanes
-        int len = face ? n : 0, incl = len;
-#pragma unroll
-        for (int o = 1; o < 32; o <<= 1) {
-            int t = __shfl_up_sync(0xffffffffu, incl, o);
-            if (lane >= o) incl += t;
-        }
-        int64_t fvi = fvbase + incl - len;
-        if (face) {
-            if (fi >= f_end || fvi + n > fv_end) {
-                bad = true;
-            } else {
-                const int cur = c.cur;
-                double nx = c.pl[q][0], ny = c.pl[q][1], nz = c.pl[q][2];
-                double ln = sqrt(nx * nx + ny * ny + nz * nz);
-                nx /= ln;
-                ny /= ln;
-                nz /= ln;
-                normals[3 * fi] = nx;
-                normals[3 * fi + 1] = ny;
-                normals[3 * fi + 2] = nz;
-                nbr[fi] = c.pid[q];
-                face_vert_off[fi] = fvi;
-                double ax = 0.0, ay = 0.0, az = 0.0;   // twice the vector area
-                for (int i = 0; i < n; ++i) {
-                    const double *a = c.v[cur][loop[i]], *b = c.v[cur][loop[(i + 1) % n]];
-                    ax += a[1] * b[2] - a[2] * b[1];
-                    ay += a[2] * b[0] - a[0] * b[2];
-                    az += a[0] * b[1] - a[1] * b[0];
-                    verts[3 * (fvi + i)] = a[0] + gx;
-                    verts[3 * (fvi + i) + 1] = a[1] + gy;
-                    verts[3 * (fvi + i) + 2] = a[2] + gz;
-                }
-                double area = 0.5 * (ax * nx + ay * ny + az * nz);
-                vol += area * (c.pl[q][3] / ln) / 3.0;
-            }
-        }
-        fbase += __popc(m);
-        fvbase += __shfl_sync(0xffffffffu, incl, 31);
-    }
-    if (__any_sync(0xffffffffu, bad) && lane == 0) atomicOr(status_or, VS_BOUNDS);
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) vol += __shfl_xor_sync(0xffffffffu, vol, o);
-    if (lane == 0) volume[j] = vol;
+    for (int t = lane; t < 3 * nf; t += 32) normals[3 * f0 + t] = s_normals[s * (3 * SLOT_F) + t];
+    for (int t = lane; t < 3 * nv; t += 32) verts[3 * fv0 + t] = s_verts[s * (3 * SLOT_FV) + t];
 }
 
 __global__ void k_finish_offsets(int64_t *face_vert_off, int64_t nface, int64_t nfv)
@@ -215,15 +203,22 @@ static int voronoi_impl(em_ctx *ctx, int64_t ngen, const double *gx, const doubl
     int K = p->knn_k > 0 ? p->knn_k : 48;
     if (K > MAXK) K = MAXK;
     int64_t *nface, *nfv, *cfo, *cfvo;
-    int32_t *clips, *nclips;
     int *status;
+    // per-cell scratch slots for the faces, written by the build pass
+    int32_t *s_fvo;
+    double *s_verts, *s_normals;
+    int64_t *s_nbr;
     EM_TRY(tmp.alloc(&nface, ngen + 1));
     EM_TRY(tmp.alloc(&nfv, ngen + 1));
     EM_TRY(tmp.alloc(&cfvo, ngen + 1));
-    EM_TRY(tmp.alloc(&clips, ngen * MAXCLIP));
-    EM_TRY(tmp.alloc(&nclips, ngen));
+    EM_TRY(tmp.alloc(&s_fvo, ngen * SLOT_F));
+    EM_TRY(tmp.alloc(&s_nbr, ngen * SLOT_F));
+    EM_TRY(tmp.alloc(&s_normals, ngen * 3 * SLOT_F));
+    EM_TRY(tmp.alloc(&s_verts, ngen * 3 * SLOT_FV));
     EM_TRY(tmp.alloc(&status, 2));
     EM_TRY(v->mem.alloc(&cfo, ngen + 1));
+    EM_TRY(v->mem.alloc(&v->gen, 3 * ngen));
+    EM_TRY(v->mem.alloc(&v->volume, ngen));
     EM_CUDA(cudaMemsetAsync(status, 0, sizeof(int), st));
     EM_CUDA(cudaMemsetAsync(status + 1, 0x7f, sizeof(int), st));
     EM_CUDA(cudaMemsetAsync(nface + ngen, 0, sizeof(int64_t), st));
@@ -232,8 +227,9 @@ static int voronoi_impl(em_ctx *ctx, int64_t ngen, const double *gx, const doubl
     double ext = 0.0;
     for (int k = 0; k < 6; ++k) ext = fmax(ext, fabs(b[k]));
     const float margin = (float)(4e-7 * (ext + 1.0));
-    k_voronoi_count<<<em_grid(ngen, VW), 32 * VW, 0, st>>>(ngen, T, xs, ys, zs, perm, b[0], b[1], b[2], b[3], b[4], b[5],
-                                                            K, margin, nface, nfv, clips, nclips, status);
+    k_voronoi_build<<<em_grid(ngen, VW), 32 * VW, 0, st>>>(ngen, T, xs, ys, zs, perm, b[0], b[1], b[2], b[3], b[4], b[5],
+                                                            K, margin, nface, nfv, s_fvo, s_verts, s_normals, s_nbr,
+                                                            v->volume, v->gen, status);
     EM_LAUNCHED(ctx);
     EM_TRY(em_exclusive_scan_i64(ctx, nface, cfo, ngen + 1));
     EM_TRY(em_exclusive_scan_i64(ctx, nfv, cfvo, ngen + 1));
@@ -267,22 +263,13 @@ static int voronoi_impl(em_ctx *ctx, int64_t ngen, const double *gx, const doubl
     v->nface = tot[0];
     v->nfv = tot[1];
     v->cell_face_off = cfo;
-    EM_TRY(v->mem.alloc(&v->gen, 3 * ngen));
     EM_TRY(v->mem.alloc(&v->face_vert_off, v->nface + 1));
     EM_TRY(v->mem.alloc(&v->verts, 3 * v->nfv));
     EM_TRY(v->mem.alloc(&v->normals, 3 * v->nface));
     EM_TRY(v->mem.alloc(&v->nbr, v->nface));
-    EM_TRY(v->mem.alloc(&v->volume, ngen));
-    k_voronoi_emit<<<em_grid(ngen, VW), 32 * VW, 0, st>>>(ngen, xs, ys, zs, perm, b[0], b[1], b[2], b[3], b[4], b[5], clips,
-                                                      nclips, cfo, cfvo, v->face_vert_off, v->verts, v->normals,
-                                                      v->nbr, v->volume, v->gen, status);
+    k_voronoi_compact<<<em_grid(ngen * 32, 256), 256, 0, st>>>(ngen, perm, cfo, cfvo, s_fvo, s_verts, s_normals, s_nbr,
+                                                               v->face_vert_off, v->verts, v->normals, v->nbr);
     EM_LAUNCHED(ctx);
-    EM_CUDA(cudaMemcpyAsync(&hstatus, status, sizeof(int), cudaMemcpyDeviceToHost, st));
-    EM_CUDA(cudaStreamSynchronize(st));
-    if (hstatus) {
-        em_set_error("build_voronoi: face output disagreed with the counting pass (status %d)", hstatus);
-        return EM_ECAPACITY;
-    }
     k_finish_offsets<<<1, 1, 0, st>>>(v->face_vert_off, v->nface, v->nfv);
     EM_LAUNCHED(ctx);
     return em_prepare_cells(ctx, v);

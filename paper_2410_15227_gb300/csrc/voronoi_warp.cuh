@@ -448,7 +448,7 @@ __device__ int clip_sorted(WCell &c, const double *__restrict__ xs, const double
         double dx = xs[k] - gx, dy = ys[k] - gy, dz = zs[k] - gz;
         int r = wclip(c, dx, dy, dz, 0.5 * (dx * dx + dy * dy + dz * dz), perm[k]);
         if (r < 0) return -r;
-        if (r > 0) {
+        if (r > 0 && clip_ids) {   // record the cutting bisectors when asked
             if (nclip >= emv::MAXCLIP) return emv::VS_CLIPS;
             if ((threadIdx.x & 31) == 0) clip_ids[nclip] = k;
             ++nclip;
