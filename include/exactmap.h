@@ -203,13 +203,17 @@ int map_exact(em_ctx *ctx, const em_pairs *pr, const double *d_x, const double *
 
 /* ---- map_exact_noalloc -------------------------------------------------------
  * The same computation and results as map_exact (bit-identical w, rho, u and
- * FP64 count), for callers that must not allocate device memory during the
- * call.  The paper has no counterpart: this is a deployment variant of the
- * library, not a step of the method.
+ * FP64 count), for callers that cannot allocate device memory during the
+ * call: a simulation code that hands all free device memory to its own pool
+ * at start-up (a cudaMalloc inside the library then fails), or one that
+ * calls the mapping every time step and cannot afford the device-wide
+ * synchronisation an allocation may cause.  The paper has no counterpart:
+ * this is a deployment variant of the library, not a step of the method.
  *   - Allocates nothing: the mixed pass's list of flagged pairs and its
  *     counter are a fixed array of EM_NOALLOC_MAX_PAIRS entries in the
- *     library's own device memory (4 MiB per device); the counter is zeroed
- *     on the context's stream at the start of every call.
+ *     library's own device memory (4 MiB, held on every GPU that loads the
+ *     library until the process exits); the counter is zeroed on the
+ *     context's stream at the start of every call.
  *   - pr->npairs > EM_NOALLOC_MAX_PAIRS: returns EM_ECAPACITY with a message,
  *     nothing enqueued.
  *   - The first call on a device looks up the array's address (with that

@@ -288,8 +288,10 @@ def map_exact(ctx: Context, pairs: Pairs, x, y, z, h_, m, vor: Voronoi, params: 
 def map_exact_noalloc(ctx: Context, pairs: Pairs, x, y, z, h_, m, vor: Voronoi, params: Params,
                       out, want_count: bool = True):
     """map_exact into caller-supplied outputs out = (w, rho, wsum or None),
-    without any device allocation by the library (at most
-    NOALLOC_MAX_PAIRS pairs; concurrent calls on one device race).
+    without any device allocation by the library, for callers whose device
+    memory is all owned by their own pool or that cannot take an allocation's
+    synchronisation each step (at most NOALLOC_MAX_PAIRS pairs; calls that
+    overlap on one device race on the library's fixed scratch array).
     Returns (w, rho, wsum, #pairs in FP64 or None)."""
     npairs, np_, nc = pairs.info()
     w, rho, wsum = out

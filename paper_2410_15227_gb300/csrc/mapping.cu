@@ -826,8 +826,11 @@ EM_EXPORT int map_exact(em_ctx *ctx, const em_pairs *pr, const double *d_x, cons
 }
 
 // ---------------------------------------------------------------------------
-// map_exact without allocation: the mixed pass's flagged-pair list and its
-// counter live in a fixed device array instead of stream-ordered scratch.
+// map_exact without allocation, for callers that cannot allocate device
+// memory during the call (their own pool holds all free memory, or they cannot
+// take an allocation's synchronisation every step): the mixed pass's
+// flagged-pair list and its counter live in a fixed device array instead of
+// stream-ordered scratch.
 // ---------------------------------------------------------------------------
 
 namespace {

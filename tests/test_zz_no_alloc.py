@@ -1,5 +1,7 @@
-"""map_exact_noalloc (the allocation-free variant of map_exact) against
-map_exact on the same inputs: identical weights, densities, sums and FP64
+"""map_exact_noalloc, the variant of map_exact for callers that cannot
+allocate device memory during the call (a simulation code that owns all free
+device memory through its own pool, or one that cannot take an allocation's
+synchronisation every time step), against map_exact on the same inputs: identical weights, densities, sums and FP64
 counts, on two calls in a row (the fixed counter must be reset by each call),
 in both precision modes; and the capacity check.  Collected last so that it
 also runs after every other GPU test in the same process."""
