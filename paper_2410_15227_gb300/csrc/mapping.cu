@@ -14,17 +14,14 @@ using namespace em;
 // Derived cell geometry in each generator's frame
 // ---------------------------------------------------------------------------
 
-// One thread per face (adjacent threads write adjacent records); the face's
-// cell by binary search in the cell offsets.  The cell radius is the largest
-// |V - g| over its vertices: every face raises its cell's r^2 with an atomic
-// max on the bit pattern (non-negative doubles order like their bits), so the
-// result does not depend on the order of the faces.
-__global__ void k_prepare_cells(int64_t nface, int64_t ncell, const double *__restrict__ gen,
+// Per face (one thread each): the face's cell by binary search in the cell
+// offsets, the plane records, and the face and cell ids of its vertices for
+// the edge pass.
+__global__ void k_prepare_faces(int64_t nface, int64_t ncell, const double *__restrict__ gen,
                                 const int64_t *__restrict__ cfo, const int64_t *__restrict__ fvo,
                                 const double *__restrict__ verts, const double *__restrict__ normals,
-                                unsigned long long *__restrict__ r2bits, PlaneD *__restrict__ plane,
-                                EdgeD *__restrict__ edge, PlaneF *__restrict__ plane_f, EdgeF *__restrict__ edge_f,
-                                EdgeF *__restrict__ edge_fl)
+                                PlaneD *__restrict__ plane, PlaneF *__restrict__ plane_f,
+                                int32_t *__restrict__ face_of_fv, int32_t *__restrict__ cell_of_face)
 {
     const int64_t f = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     if (f >= nface) return;
@@ -35,67 +32,84 @@ __global__ void k_prepare_cells(int64_t nface, int64_t ncell, const double *__re
         else hi = mid;
     }
     const int64_t j = lo;
-    double gx = gen[3 * j], gy = gen[3 * j + 1], gz = gen[3 * j + 2];
-    double r2max = 0.0;
-    {
-        double nx = normals[3 * f], ny = normals[3 * f + 1], nz = normals[3 * f + 2];
-        int64_t v0 = fvo[f], v1 = fvo[f + 1];
-        double c = nx * (verts[3 * v0] - gx) + ny * (verts[3 * v0 + 1] - gy) + nz * (verts[3 * v0 + 2] - gz);
-        plane[f] = PlaneD{nx, ny, nz, c};
-        plane_f[f] = PlaneF{(float)nx, (float)ny, (float)nz, (float)c};
-        for (int64_t k = v0; k < v1; ++k) {
-            int64_t k1 = (k + 1 < v1) ? k + 1 : v0;
-            double ax = verts[3 * k] - gx, ay = verts[3 * k + 1] - gy, az = verts[3 * k + 2] - gz;
-            double bx = verts[3 * k1] - gx, by = verts[3 * k1 + 1] - gy, bz = verts[3 * k1 + 2] - gz;
-            double q = ax * ax + ay * ay + az * az;
-            r2max = q > r2max ? q : r2max;
-            double ex = bx - ax, ey = by - ay, ez = bz - az;
-            double L = sqrt(ex * ex + ey * ey + ez * ez);
-            EdgeD E;
-            if (L > 0.0) {
-                ex /= L;
-                ey /= L;
-                ez /= L;
-            }
-            E.ex = ex;
-            E.ey = ey;
-            E.ez = ez;
-            E.L = L;
-            E.mx = ey * nz - ez * ny;   // e x n: in-plane outward normal
-            E.my = ez * nx - ex * nz;
-            E.mz = ex * ny - ey * nx;
-            E.cm = E.mx * ax + E.my * ay + E.mz * az;
-            E.ce = ex * ax + ey * ay + ez * az;
-            E.pad = 0.0;
-            edge[k] = E;
-            EdgeF F;
-            F.mx = (float)E.mx;
-            F.my = (float)E.my;
-            F.mz = (float)E.mz;
-            F.cm = (float)E.cm;
-            F.ex = (float)E.ex;
-            F.ey = (float)E.ey;
-            F.ez = (float)E.ez;
-            F.ce = (float)E.ce;
-            F.L = (float)E.L;
-            F.pad0 = F.pad1 = F.pad2 = 0.f;
-            edge_f[k] = F;
-            // low parts: E = hi + lo to about 2^-48 relative (float-float)
-            EdgeF G;
-            G.mx = (float)(E.mx - (double)F.mx);
-            G.my = (float)(E.my - (double)F.my);
-            G.mz = (float)(E.mz - (double)F.mz);
-            G.cm = (float)(E.cm - (double)F.cm);
-            G.ex = (float)(E.ex - (double)F.ex);
-            G.ey = (float)(E.ey - (double)F.ey);
-            G.ez = (float)(E.ez - (double)F.ez);
-            G.ce = (float)(E.ce - (double)F.ce);
-            G.L = (float)(E.L - (double)F.L);
-            G.pad0 = G.pad1 = G.pad2 = 0.f;
-            edge_fl[k] = G;
-        }
+    const double gx = gen[3 * j], gy = gen[3 * j + 1], gz = gen[3 * j + 2];
+    const double nx = normals[3 * f], ny = normals[3 * f + 1], nz = normals[3 * f + 2];
+    const int64_t v0 = fvo[f], v1 = fvo[f + 1];
+    const double c = nx * (verts[3 * v0] - gx) + ny * (verts[3 * v0 + 1] - gy) + nz * (verts[3 * v0 + 2] - gz);
+    plane[f] = PlaneD{nx, ny, nz, c};
+    plane_f[f] = PlaneF{(float)nx, (float)ny, (float)nz, (float)c};
+    cell_of_face[f] = (int32_t)j;
+    for (int64_t k = v0; k < v1; ++k) face_of_fv[k] = (int32_t)f;
+}
+
+// Per face-vertex k (one thread each, so that the records are written by
+// adjacent threads): the edge from vertex k to the next vertex of its face, in
+// the generator's frame, as FP64 and FP32 hi/lo records.  The cell radius is
+// the largest |V - g| over its vertices: every vertex raises its cell's r^2
+// with an atomic max on the bit pattern (non-negative doubles order like their
+// bits), so the result does not depend on the order.
+__global__ void k_prepare_edges(int64_t nfv, const double *__restrict__ gen, const int64_t *__restrict__ fvo,
+                                const double *__restrict__ verts, const double *__restrict__ normals,
+                                const int32_t *__restrict__ face_of_fv, const int32_t *__restrict__ cell_of_face,
+                                unsigned long long *__restrict__ r2bits, EdgeD *__restrict__ edge,
+                                EdgeF *__restrict__ edge_f, EdgeF *__restrict__ edge_fl)
+{
+    const int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (k >= nfv) return;
+    const int64_t f = face_of_fv[k];
+    const int64_t j = cell_of_face[f];
+    const double gx = gen[3 * j], gy = gen[3 * j + 1], gz = gen[3 * j + 2];
+    const double nx = normals[3 * f], ny = normals[3 * f + 1], nz = normals[3 * f + 2];
+    const int64_t v0 = fvo[f], v1 = fvo[f + 1];
+    int64_t k1 = (k + 1 < v1) ? k + 1 : v0;
+    double ax = verts[3 * k] - gx, ay = verts[3 * k + 1] - gy, az = verts[3 * k + 2] - gz;
+    double bx = verts[3 * k1] - gx, by = verts[3 * k1 + 1] - gy, bz = verts[3 * k1 + 2] - gz;
+    double q = ax * ax + ay * ay + az * az;
+    double ex = bx - ax, ey = by - ay, ez = bz - az;
+    double L = sqrt(ex * ex + ey * ey + ez * ez);
+    EdgeD E;
+    if (L > 0.0) {
+        ex /= L;
+        ey /= L;
+        ez /= L;
     }
-    atomicMax(r2bits + j, (unsigned long long)__double_as_longlong(r2max));
+    E.ex = ex;
+    E.ey = ey;
+    E.ez = ez;
+    E.L = L;
+    E.mx = ey * nz - ez * ny;   // e x n: in-plane outward normal
+    E.my = ez * nx - ex * nz;
+    E.mz = ex * ny - ey * nx;
+    E.cm = E.mx * ax + E.my * ay + E.mz * az;
+    E.ce = ex * ax + ey * ay + ez * az;
+    E.pad = 0.0;
+    edge[k] = E;
+    EdgeF F;
+    F.mx = (float)E.mx;
+    F.my = (float)E.my;
+    F.mz = (float)E.mz;
+    F.cm = (float)E.cm;
+    F.ex = (float)E.ex;
+    F.ey = (float)E.ey;
+    F.ez = (float)E.ez;
+    F.ce = (float)E.ce;
+    F.L = (float)E.L;
+    F.pad0 = F.pad1 = F.pad2 = 0.f;
+    edge_f[k] = F;
+    // low parts: E = hi + lo to about 2^-48 relative (float-float)
+    EdgeF G;
+    G.mx = (float)(E.mx - (double)F.mx);
+    G.my = (float)(E.my - (double)F.my);
+    G.mz = (float)(E.mz - (double)F.mz);
+    G.cm = (float)(E.cm - (double)F.cm);
+    G.ex = (float)(E.ex - (double)F.ex);
+    G.ey = (float)(E.ey - (double)F.ey);
+    G.ez = (float)(E.ez - (double)F.ez);
+    G.ce = (float)(E.ce - (double)F.ce);
+    G.L = (float)(E.L - (double)F.L);
+    G.pad0 = G.pad1 = G.pad2 = 0.f;
+    edge_fl[k] = G;
+    atomicMax(r2bits + j, (unsigned long long)__double_as_longlong(q));
 }
 
 __global__ void k_radius_finish(int64_t ncell, double *__restrict__ radius)
@@ -116,9 +130,17 @@ int em_prepare_cells(em_ctx *ctx, em_voronoi *v)
     if (v->ncell) {
         EM_CUDA(cudaMemsetAsync(v->radius, 0, v->ncell * sizeof(double), ctx->stream));
         if (v->nface) {
-            k_prepare_cells<<<em_grid(v->nface, 128), 128, 0, ctx->stream>>>(
-                v->nface, v->ncell, v->gen, v->cell_face_off, v->face_vert_off, v->verts, v->normals,
-                (unsigned long long *)v->radius, v->plane, v->edge, v->plane_f, v->edge_f, v->edge_fl);
+            DevArena tmp(ctx->stream, true);
+            int32_t *face_of_fv, *cell_of_face;
+            EM_TRY(tmp.alloc(&face_of_fv, v->nfv));
+            EM_TRY(tmp.alloc(&cell_of_face, v->nface));
+            k_prepare_faces<<<em_grid(v->nface, 128), 128, 0, ctx->stream>>>(
+                v->nface, v->ncell, v->gen, v->cell_face_off, v->face_vert_off, v->verts, v->normals, v->plane,
+                v->plane_f, face_of_fv, cell_of_face);
+            EM_LAUNCHED(ctx);
+            k_prepare_edges<<<em_grid(v->nfv, 256), 256, 0, ctx->stream>>>(
+                v->nfv, v->gen, v->face_vert_off, v->verts, v->normals, face_of_fv, cell_of_face,
+                (unsigned long long *)v->radius, v->edge, v->edge_f, v->edge_fl);
             EM_LAUNCHED(ctx);
         }
         k_radius_finish<<<em_grid(v->ncell, 256), 256, 0, ctx->stream>>>(v->ncell, v->radius);
@@ -424,6 +446,9 @@ namespace {
 #ifndef EM_MQ_WARPS
 #define EM_MQ_WARPS 2
 #endif
+#ifndef EM_MQ_MINB
+#define EM_MQ_MINB 0   // minimum resident blocks per SM asked of the compiler (0: none)
+#endif
 constexpr int MQ_SLOTS = EM_MQ_SLOTS;   // segments a lane holds between evaluations (>= 5)
 constexpr int MQ_WARPS = EM_MQ_WARPS;   // warps per block
 static_assert(MQ_SLOTS >= 5, "an edge queues up to four segments");
@@ -571,7 +596,12 @@ __device__ __forceinline__ void mq_push_g(SegQueue &q, int lane, int &cnt, float
 
 }  // namespace
 
-__global__ void __launch_bounds__(32 * MQ_WARPS) k_map_fp32(int64_t npairs, const int32_t *__restrict__ pi,
+#if EM_MQ_MINB > 0
+#define MQ_LAUNCH_BOUNDS __launch_bounds__(32 * EM_MQ_WARPS, EM_MQ_MINB)
+#else
+#define MQ_LAUNCH_BOUNDS __launch_bounds__(32 * EM_MQ_WARPS)
+#endif
+__global__ void MQ_LAUNCH_BOUNDS k_map_fp32(int64_t npairs, const int32_t *__restrict__ pi,
                                                         const int32_t *__restrict__ pj, const double *__restrict__ x,
                                                         const double *__restrict__ y, const double *__restrict__ z,
                                                         const double *__restrict__ h, const double *__restrict__ gen,

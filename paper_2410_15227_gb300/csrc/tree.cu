@@ -129,18 +129,43 @@ __global__ void k_node_sums(int64_t lo, int64_t hi, const int32_t *__restrict__ 
     cz[a] = __ddiv_rn(sz, sm);
 }
 
-// s_node = max over constituents of |x - COM|; one warp per node.
-__global__ void k_node_size(int64_t nnode, const int32_t *__restrict__ first, const int32_t *__restrict__ count,
+// s_node = max over constituents of |x - COM|.  Nodes are cut into chunks of
+// SIZE_CHUNK constituents, one warp per chunk, so that the root's million
+// particles do not fall to one warp; each chunk raises its node's r^2 with an
+// atomic max on the bit pattern (non-negative doubles order like their bits).
+// Every term is rounded as before and max does not depend on the order, so
+// the result is the same bit for bit.
+constexpr int SIZE_CHUNK = 1024;
+
+__global__ void k_size_chunks(int64_t nnode, const int32_t *__restrict__ count, int64_t *__restrict__ nchunk)
+{
+    const int64_t a = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (a < nnode) nchunk[a] = (count[a] + SIZE_CHUNK - 1) / SIZE_CHUNK;
+}
+
+__global__ void k_node_size(int64_t nnode, int64_t ntask, const int64_t *__restrict__ task_off,
+                            const int32_t *__restrict__ first, const int32_t *__restrict__ count,
                             const double *__restrict__ xs, const double *__restrict__ ys,
                             const double *__restrict__ zs, const double *__restrict__ cx,
-                            const double *__restrict__ cy, const double *__restrict__ cz, double *__restrict__ size)
+                            const double *__restrict__ cy, const double *__restrict__ cz,
+                            unsigned long long *__restrict__ r2bits)
 {
-    int64_t a = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
-    int lane = threadIdx.x & 31;
-    if (a >= nnode) return;
-    double ax = cx[a], ay = cy[a], az = cz[a];
+    const int64_t t = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
+    const int lane = threadIdx.x & 31;
+    if (t >= ntask) return;
+    int64_t lo = 0, hi = nnode;   // task_off[lo] <= t < task_off[hi]
+    while (hi - lo > 1) {
+        const int64_t mid = (lo + hi) >> 1;
+        if (task_off[mid] <= t) lo = mid;
+        else hi = mid;
+    }
+    const int64_t a = lo;
+    const int64_t c = t - task_off[a];
+    const double ax = cx[a], ay = cy[a], az = cz[a];
+    const int32_t k0 = first[a] + (int32_t)(c * SIZE_CHUNK);
+    const int32_t k1 = min(first[a] + count[a], k0 + SIZE_CHUNK);
     double r2 = 0.0;
-    for (int32_t k = first[a] + lane; k < first[a] + count[a]; k += 32) {
+    for (int32_t k = k0 + lane; k < k1; k += 32) {
         double dx = __dsub_rn(xs[k], ax), dy = __dsub_rn(ys[k], ay), dz = __dsub_rn(zs[k], az);
         double q = __dadd_rn(__dadd_rn(__dmul_rn(dx, dx), __dmul_rn(dy, dy)), __dmul_rn(dz, dz));
         r2 = q > r2 ? q : r2;
@@ -150,7 +175,13 @@ __global__ void k_node_size(int64_t nnode, const int32_t *__restrict__ first, co
         double q = __shfl_xor_sync(0xffffffffu, r2, o);
         r2 = q > r2 ? q : r2;
     }
-    if (lane == 0) size[a] = __dsqrt_rn(r2);
+    if (lane == 0) atomicMax(r2bits + a, (unsigned long long)__double_as_longlong(r2));
+}
+
+__global__ void k_size_finish(int64_t nnode, double *__restrict__ size)
+{
+    const int64_t a = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (a < nnode) size[a] = __dsqrt_rn(size[a]);   // the bits hold r^2 as a double
 }
 
 struct TopoArrays {
@@ -308,9 +339,26 @@ static int build_tree_impl(em_ctx *ctx, em_tree *t, const double *d_x, const dou
                                                             t->cx, t->cy, t->cz);
         EM_LAUNCHED(ctx);
     }
-    k_node_size<<<em_grid(nn * 32, 256), 256, 0, st>>>(nn, t->first, t->count, t->xs, t->ys, t->zs, t->cx, t->cy,
-                                                         t->cz, t->size);
-    EM_LAUNCHED(ctx);
+    {
+        DevArena tmp(st, true);
+        int64_t *nchunk, *task_off;
+        EM_TRY(tmp.alloc(&nchunk, nn + 1));
+        EM_TRY(tmp.alloc(&task_off, nn + 1));
+        EM_CUDA(cudaMemsetAsync(nchunk + nn, 0, sizeof(int64_t), st));
+        k_size_chunks<<<em_grid(nn, 256), 256, 0, st>>>(nn, t->count, nchunk);
+        EM_LAUNCHED(ctx);
+        EM_TRY(em_exclusive_scan_i64(ctx, nchunk, task_off, nn + 1));
+        int64_t ntask = 0;
+        EM_CUDA(cudaMemcpyAsync(&ntask, task_off + nn, sizeof(int64_t), cudaMemcpyDeviceToHost, st));
+        EM_CUDA(cudaStreamSynchronize(st));
+        EM_CUDA(cudaMemsetAsync(t->size, 0, nn * sizeof(double), st));
+        k_node_size<<<em_grid(ntask * 32, 256), 256, 0, st>>>(nn, ntask, task_off, t->first, t->count, t->xs, t->ys,
+                                                                t->zs, t->cx, t->cy, t->cz,
+                                                                (unsigned long long *)t->size);
+        EM_LAUNCHED(ctx);
+        k_size_finish<<<em_grid(nn, 256), 256, 0, st>>>(nn, t->size);
+        EM_LAUNCHED(ctx);
+    }
     return EM_OK;
 }
 
