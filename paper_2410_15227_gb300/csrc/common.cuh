@@ -162,6 +162,7 @@ struct em_voronoi {
     PlaneD *plane = nullptr;            // [nface] (n, c = n.(V_0 - g))
     EdgeD *edge = nullptr;              // [nfv]
     PlaneF *plane_f = nullptr;
+    PlaneF *plane_fl = nullptr;         // [nface] P - (double)(float)P: low parts of the plane records
     EdgeF *edge_f = nullptr;
     EdgeF *edge_fl = nullptr;           // [nfv] E - (double)(float)E: low parts of the edge records
     explicit em_voronoi(cudaStream_t s) : mem(s) {}

@@ -21,7 +21,8 @@ __global__ void k_prepare_faces(int64_t nface, int64_t ncell, const double *__re
                                 const int64_t *__restrict__ cfo, const int64_t *__restrict__ fvo,
                                 const double *__restrict__ verts, const double *__restrict__ normals,
                                 PlaneD *__restrict__ plane, PlaneF *__restrict__ plane_f,
-                                int32_t *__restrict__ face_of_fv, int32_t *__restrict__ cell_of_face)
+                                PlaneF *__restrict__ plane_fl, int32_t *__restrict__ face_of_fv,
+                                int32_t *__restrict__ cell_of_face)
 {
     const int64_t f = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     if (f >= nface) return;
@@ -37,7 +38,11 @@ __global__ void k_prepare_faces(int64_t nface, int64_t ncell, const double *__re
     const int64_t v0 = fvo[f], v1 = fvo[f + 1];
     const double c = nx * (verts[3 * v0] - gx) + ny * (verts[3 * v0 + 1] - gy) + nz * (verts[3 * v0 + 2] - gz);
     plane[f] = PlaneD{nx, ny, nz, c};
-    plane_f[f] = PlaneF{(float)nx, (float)ny, (float)nz, (float)c};
+    const PlaneF F{(float)nx, (float)ny, (float)nz, (float)c};
+    plane_f[f] = F;
+    // low parts: the plane = hi + lo to about 2^-48 relative (float-float)
+    plane_fl[f] = PlaneF{(float)(nx - (double)F.x), (float)(ny - (double)F.y), (float)(nz - (double)F.z),
+                         (float)(c - (double)F.w)};
     cell_of_face[f] = (int32_t)j;
     for (int64_t k = v0; k < v1; ++k) face_of_fv[k] = (int32_t)f;
 }
@@ -125,6 +130,7 @@ int em_prepare_cells(em_ctx *ctx, em_voronoi *v)
     EM_TRY(v->mem.alloc(&v->plane, v->nface));
     EM_TRY(v->mem.alloc(&v->edge, v->nfv));
     EM_TRY(v->mem.alloc(&v->plane_f, v->nface));
+    EM_TRY(v->mem.alloc(&v->plane_fl, v->nface));
     EM_TRY(v->mem.alloc(&v->edge_f, v->nfv));
     EM_TRY(v->mem.alloc(&v->edge_fl, v->nfv));
     if (v->ncell) {
@@ -136,7 +142,7 @@ int em_prepare_cells(em_ctx *ctx, em_voronoi *v)
             EM_TRY(tmp.alloc(&cell_of_face, v->nface));
             k_prepare_faces<<<em_grid(v->nface, 128), 128, 0, ctx->stream>>>(
                 v->nface, v->ncell, v->gen, v->cell_face_off, v->face_vert_off, v->verts, v->normals, v->plane,
-                v->plane_f, face_of_fv, cell_of_face);
+                v->plane_f, v->plane_fl, face_of_fv, cell_of_face);
             EM_LAUNCHED(ctx);
             k_prepare_edges<<<em_grid(v->nfv, 256), 256, 0, ctx->stream>>>(
                 v->nfv, v->gen, v->face_vert_off, v->verts, v->normals, face_of_fv, cell_of_face,
@@ -423,16 +429,20 @@ __global__ void __launch_bounds__(128) k_map_fp64_flagged(const int *__restrict_
 // FP32 bulk pass (quadrature form, see quad32.cuh).
 //
 // A warp maps 32 consecutive pairs (mostly of one cell, since pairs are
-// sorted by cell), one pair per lane for the geometry: per face the FP64
-// plane distance D and an FP32 pass for the reference R = distance from p to
-// the face polygon (any value used consistently for the face is exact when P
-// is outside the polygon; inside, R = D), then R, 2 - R, K(R) and K(1) - K(R)
-// from FP64; per edge D, A, T0, T1, B^2, B^2 - 1, 4 - B^2 and A^2 - rho^2 in
-// FP64 (one rounding each).  Each edge yields up to four quadrature segments,
-// which the lane appends to its column of a per-warp queue in shared memory;
-// whenever a lane's column may overflow, the warp evaluates all queued
-// segments together, one segment per lane, so that the node loop runs with
-// the warp converged whatever the pairs' geometry.  Each lane then adds its
+// sorted by cell), one pair per lane for the geometry: per face the plane
+// distance D in float-float and an FP32 pass for the reference R = distance
+// from p to the face polygon (any value used consistently for the face is
+// exact when P is outside the polygon; inside, R = D), then R, 2 - R, K(R)
+// and K(1) - K(R) from FP64; per edge A, T0, T1, B^2 - 1, 4 - B^2 and
+// A^2 - rho^2 in float-float, each rounded once to FP32.  The FP64 pipe runs
+// at 1/64 of the FP32 rate, so nothing per edge or per quadrature segment
+// touches it: the pieces are summed in float-float.
+//
+// Each edge yields up to four quadrature segments, which the lane appends to
+// its column of a per-warp queue in shared memory; whenever a lane's column
+// may overflow, the warp evaluates all queued segments together, one segment
+// per lane, so that the node loop runs with the warp converged whatever the
+// pairs' geometry.  Each lane then adds its
 // own segments' results in the order it queued them, which keeps the result
 // bit-reproducible.  The estimated error 8 eps times the sum of the
 // magnitudes of the non-negative pieces flags the pair for the FP64 pass when
@@ -463,8 +473,11 @@ struct SegQueue {
 };
 
 // Evaluate every queued segment of the warp, then add each lane's own results
-// to its pair in queue order.  Called with the warp converged.
-__device__ __forceinline__ void mq_flush(SegQueue &q, int lane, int cnt, double &acc, double &mag)
+// to its pair in queue order.  Called with the warp converged.  The sum is
+// kept in float-float (the product scale * result exactly, the additions to
+// about 2^-44 of the magnitudes), the magnitudes in FP32: they only scale
+// the error bound.
+__device__ __forceinline__ void mq_flush(SegQueue &q, int lane, int cnt, emq::ff &acc, float &mag)
 {
     int x = cnt;
 #pragma unroll
@@ -490,17 +503,17 @@ __device__ __forceinline__ void mq_flush(SegQueue &q, int lane, int cnt, double 
     }
     __syncwarp();
     for (int sl = 0; sl < cnt; ++sl) {
-        const double v = (double)q.scale[sl][lane] * (double)q.res[sl][lane];
-        acc += v;
-        mag += fabs(v);
+        const emq::ff v = emq::ff_two_prod(q.scale[sl][lane], q.res[sl][lane]);
+        acc = emq::ff_add(acc, v);
+        mag += fabsf(v.hi);
     }
     __syncwarp();
 }
 
 // Face constants of the lane's current face.
 struct FaceState {
-    double D64, rr2;            // D, rho^2 (units of h)
-    emq::ff dm1, d4;            // D^2 - 1, 4 - D^2 (float-float)
+    emq::ff dm1, d4;            // D^2 - 1, 4 - D^2 (float-float, units of h)
+    float rr2;                  // rho^2 (units of h; FP32 by construction)
     float Df, R, v, KR, C1;     // v = 2 - R
     float sign;   // orientation of the face as seen from P (sign of the signed distance)
 };
@@ -555,7 +568,7 @@ __device__ __forceinline__ void face_consts(double R2, bool tilde, FaceState &fs
 // of an edge) with the signed factor sc; the part beyond 2h is added directly.
 __device__ __forceinline__ void mq_push_g(SegQueue &q, int lane, int &cnt, float ua, float ub, float A, float B2,
                                           float c1, float c4, float cc, float sc, const FaceState &fs, bool tilde,
-                                          double &acc, double &mag)
+                                          emq::ff &acc, float &mag)
 {
     const float t1 = c1 < 0.f ? sqrtf(-c1) : 0.f;
     const float t2 = c4 > 0.f ? sqrtf(c4) : 0.f;
@@ -587,9 +600,9 @@ __device__ __forceinline__ void mq_push_g(SegQueue &q, int lane, int &cnt, float
     if (tilde) {   // beyond 2h: K~(Q) = 0, the integrand is -K~(R) >= 0
         const float a = fmaxf(ua, t2), b = ub;
         if (b > a) {
-            const double v = (double)sc * (double)(-fs.KR * atan2f((b - a) * A, A * A + a * b));
-            acc += v;
-            mag += fabs(v);
+            const emq::ff v = emq::ff_two_prod(sc, -fs.KR * atan2f((b - a) * A, A * A + a * b));
+            acc = emq::ff_add(acc, v);
+            mag += fabsf(v.hi);
         }
     }
 }
@@ -607,7 +620,8 @@ __global__ void MQ_LAUNCH_BOUNDS k_map_fp32(int64_t npairs, const int32_t *__res
                                                         const double *__restrict__ h, const double *__restrict__ gen,
                                                         const double *__restrict__ radius,
                                                         const int64_t *__restrict__ cfo, const int64_t *__restrict__ fvo,
-                                                        const PlaneD *__restrict__ plane,
+                                                        const PlaneF *__restrict__ plane_f,
+                                                        const PlaneF *__restrict__ plane_fl,
                                                         const EdgeF *__restrict__ edge_f,
                                                         const EdgeF *__restrict__ edge_fl, float tol,
                                                         double *__restrict__ w, int32_t *__restrict__ flagged,
@@ -621,9 +635,8 @@ __global__ void MQ_LAUNCH_BOUNDS k_map_fp32(int64_t npairs, const int32_t *__res
     const int64_t k = k0 + lane;
     const bool valid = k < npairs;
 
-    double rx = 0.0, ry = 0.0, rz = 0.0, hh = 1.0;
+    double rx = 0.0, ry = 0.0, rz = 0.0, hh = 1.0, rad = 0.0;
     int64_t f = 0, f1 = 0;
-    bool inside = false, full = false;
     if (valid) {
         const int i = pi[k], j = pj[k];
         rx = x[i] - gen[3 * j];
@@ -632,39 +645,47 @@ __global__ void MQ_LAUNCH_BOUNDS k_map_fp32(int64_t npairs, const int32_t *__res
         hh = h[i];
         f = cfo[j];
         f1 = cfo[j + 1];
-        inside = true;
-        for (int64_t g = f; g < f1; ++g) {
-            PlaneD pl = plane[g];
-            inside = inside && !(pl.w - (pl.x * rx + pl.y * ry + pl.z * rz) < 0.0);
-        }
-        full = inside && (sqrt(rx * rx + ry * ry + rz * rz) + radius[j] < 2.0 * hh);
+        rad = radius[j];
     }
     const double ih = 1.0 / hh;
     const float rxf = (float)rx, ryf = (float)ry, rzf = (float)rz, ihf = (float)ih;
-    const bool tilde = !full;
-    // float-float copies of r = p - g and 1/h for the per-edge geometry
+    // float-float copies of r = p - g and 1/h for the plane and edge geometry
     const emq::ff rxx = emq::ff_from_double(rx), ryy = emq::ff_from_double(ry), rzz = emq::ff_from_double(rz);
     const emq::ff ihh = emq::ff_from_double(ih);
+    // signed distance c - n.r of P from face g's plane (positive inside), in
+    // float-float; the inside test and the faces' orientations below both
+    // take their signs from this one value
+    auto plane_dist = [&](int64_t g) {
+        const PlaneF H = plane_f[g], Lo = plane_fl[g];
+        return emq::ff_offset_dot(H.w, Lo.w, H.x, Lo.x, H.y, Lo.y, H.z, Lo.z, rxx, ryy, rzz);
+    };
+    bool inside = valid, full = false;
+    if (valid) {
+        for (int64_t g = f; g < f1; ++g) inside = inside && !(plane_dist(g).hi < 0.f);
+        full = inside && (sqrt(rx * rx + ry * ry + rz * rz) + rad < 2.0 * hh);
+    }
+    const bool tilde = !full;
 
-    double acc = 0.0, mag = 0.0;
+    emq::ff acc{0.f, 0.f};
+    float mag = 0.f;
     bool force = false;   // the FP32 form does not apply: recompute in FP64
     int cnt = 0;
     const int nface = valid ? (int)(f1 - f) : 0;
     // faces and edges in lockstep across the warp: consecutive pairs mostly
-    // share their cell, so the FP64 geometry runs with the lanes converged
+    // share their cell, so the per-face geometry runs with the lanes converged
     for (int fi = 0; __any_sync(FULL_MASK, fi < nface); ++fi) {
         int64_t e0 = 0;
         int ne = 0;
         FaceState fs{};
         if (fi < nface) {
             const int64_t g = f + fi;
-            PlaneD pl = plane[g];
-            const double sd = pl.w - (pl.x * rx + pl.y * ry + pl.z * rz);
-            const double D64 = fabs(sd) * ih;
+            const emq::ff sd = plane_dist(g);
+            const emq::ff D = emq::ff_mul(sd.hi < 0.f ? emq::ff_neg(sd) : sd, ihh);
             // P in (or within underflow of) the face plane: in the complement
             // form such a face would carry half of the kernel
-            if (tilde && D64 < 1e-30) force = true;
-            if (!(sd == 0.0 || (tilde && D64 >= 2.0))) {
+            if (tilde && D.hi < 1e-30f) force = true;
+            const bool beyond = D.hi > 2.f || (D.hi == 2.f && D.lo >= 0.f);
+            if (!(sd.hi == 0.f || (tilde && beyond))) {
                 // reference distance to the polygon (FP32)
                 const int64_t g0 = fvo[g], g1 = fvo[g + 1];
                 bool inpoly = true;
@@ -678,16 +699,16 @@ __global__ void MQ_LAUNCH_BOUNDS k_map_fp32(int64_t npairs, const int32_t *__res
                     float tc = t0 > 0.f ? t0 : (t1 < 0.f ? t1 : 0.f);
                     rho2 = fminf(rho2, a * a + tc * tc);
                 }
-                const double rr2 = inpoly ? 0.0 : (double)rho2;
-                const double R2 = D64 * D64 + rr2;
+                const float rr2 = inpoly ? 0.f : rho2;
+                const emq::ff D2 = emq::ff_mul(D, D);
+                const double R2 = ((double)D2.hi + (double)D2.lo) + (double)rr2;
                 if (!(tilde && R2 >= 4.0)) {   // else the polygon lies entirely beyond 2h
-                    fs.D64 = D64;
                     fs.rr2 = rr2;
-                    fs.dm1 = emq::ff_from_double(D64 * D64 - 1.0);
-                    fs.d4 = emq::ff_from_double(4.0 - D64 * D64);
-                    fs.Df = (float)D64;
+                    fs.dm1 = emq::ff_add(D2, emq::ff{-1.f, 0.f});
+                    fs.d4 = emq::ff_add(emq::ff{4.f, 0.f}, emq::ff_neg(D2));
+                    fs.Df = D.hi + D.lo;
                     face_consts(R2, tilde, fs);
-                    fs.sign = sd > 0.0 ? 1.f : -1.f;
+                    fs.sign = sd.hi > 0.f ? 1.f : -1.f;
                     e0 = g0;
                     ne = (int)(g1 - g0);
                 }
@@ -708,7 +729,7 @@ __global__ void MQ_LAUNCH_BOUNDS k_map_fp32(int64_t npairs, const int32_t *__res
                     const float A = fabsf(a.hi + a.lo), T0 = t0.hi + t0.lo, T1 = t1.hi + t1.lo;
                     const float B2f = fs.Df * fs.Df + A * A;
                     const emq::ff c1x = emq::ff_add(fs.dm1, a2), c4x = emq::ff_add(fs.d4, emq::ff_neg(a2));
-                    const emq::ff ccx = emq::ff_add(a2, emq::ff_neg(emq::ff_from_double(fs.rr2)));
+                    const emq::ff ccx = emq::ff_add(a2, emq::ff{-fs.rr2, 0.f});
                     const float c1 = c1x.hi + c1x.lo, c4 = c4x.hi + c4x.lo, cc = ccx.hi + ccx.lo;
                     // signed factor: D/pi, face orientation, side of the edge line, direction along it
                     const float base = fs.sign * (a.hi > 0.f ? 1.f : -1.f) * fs.Df * 0.31830988618379067154f;
@@ -737,14 +758,15 @@ __global__ void MQ_LAUNCH_BOUNDS k_map_fp32(int64_t npairs, const int32_t *__res
     if (valid) {
         // the integrals were summed with their signs: w = sum (full kernel) or
         // [P inside] - sum (complement kernel)
-        const double wk = full ? acc : ((inside ? 1.0 : 0.0) - acc);
-        if (inside && !full) mag += 1.0;
+        const double sum = (double)acc.hi + (double)acc.lo;
+        const double wk = full ? sum : ((inside ? 1.0 : 0.0) - sum);
+        const double magd = (double)mag + ((inside && !full) ? 1.0 : 0.0);
         w[k] = wk;
         // error bound of the FP32 pass: 8 ulp of every non-negative piece it
         // summed (pieces are relative-accurate to a few ulp; against FP64 the
         // largest error/bound ratio seen was 0.81, and no pair of the test
         // workloads exceeds the tolerance until the factor drops below 2)
-        const double est = 8.0 * 5.9604644775390625e-8 * mag;
+        const double est = 8.0 * 5.9604644775390625e-8 * magd;
         flag = force || !(est <= (double)tol * fabs(wk) + 1e-14);
     }
     // one append per warp: the flagged pairs of a warp (mostly of one cell)
@@ -818,7 +840,7 @@ EM_EXPORT int map_exact(em_ctx *ctx, const em_pairs *pr, const double *d_x, cons
             EM_CUDA(cudaMemsetAsync(nflag, 0, sizeof(int), ctx->stream));
             k_map_fp32<<<em_grid((n + 31) / 32, MQ_WARPS), 32 * MQ_WARPS, 0, ctx->stream>>>(
                 n, pr->pair_i, pr->pair_j, d_x, d_y, d_z, d_h, v->gen, v->radius, v->cell_face_off,
-                v->face_vert_off, v->plane, v->edge_f, v->edge_fl, (float)p->fp64_threshold, d_w_out, flagged, nflag);
+                v->face_vert_off, v->plane_f, v->plane_fl, v->edge_f, v->edge_fl, (float)p->fp64_threshold, d_w_out, flagged, nflag);
             EM_LAUNCHED(ctx);
             if (ctx->timing) {
                 EM_CUDA(cudaEventRecord(ctx->ev[1], ctx->stream));
@@ -937,7 +959,7 @@ EM_EXPORT int map_exact_noalloc(em_ctx *ctx, const em_pairs *pr, const double *d
             EM_CUDA(cudaMemsetAsync(nflag, 0, sizeof(int), ctx->stream));
             k_map_fp32<<<em_grid((n + 31) / 32, MQ_WARPS), 32 * MQ_WARPS, 0, ctx->stream>>>(
                 n, pr->pair_i, pr->pair_j, d_x, d_y, d_z, d_h, v->gen, v->radius, v->cell_face_off,
-                v->face_vert_off, v->plane, v->edge_f, v->edge_fl, (float)p->fp64_threshold, d_w_out, flagged, nflag);
+                v->face_vert_off, v->plane_f, v->plane_fl, v->edge_f, v->edge_fl, (float)p->fp64_threshold, d_w_out, flagged, nflag);
             EM_LAUNCHED(ctx);
             const int grid = (int)std::min<int64_t>((n + block - 1) / block, 152 * 16);
             k_map_fp64_flagged<<<grid, block, 0, ctx->stream>>>(nflag, pr->pair_i, pr->pair_j, d_x, d_y, d_z, d_h,
