@@ -191,10 +191,10 @@ int pairs_destroy(em_pairs *pr);
  *   u_i   = sum_j w_ij             (partition-of-unity check, ascending j).
  *   d_w_out[npairs], d_rho_out[ncell] (device); d_wsum_out[np] may be NULL.
  *   p->precision: 0 = FP64 closed form for every pair.  1 = mixed: an FP32
- *   quadrature of each edge integral (FP64 edge geometry, per-pair sums in
- *   FP64) with a per-pair error bound; pairs whose bound exceeds
- *   p->fp64_threshold |w| + 1e-14, or whose particle lies in a face plane,
- *   are recomputed with the FP64 closed form on the device.
+ *   quadrature of each edge integral (float-float plane and edge geometry,
+ *   per-pair sums in float-float) with a per-pair error bound; pairs whose
+ *   bound exceeds max(p->fp64_threshold |w|, 1e-14), or whose particle lies
+ *   in a face plane, are recomputed with the FP64 closed form on the device.
  *   h_nfp64 (host, may be NULL): number of pairs recomputed in FP64; passing
  *   it makes the call wait for the mixed pass, NULL leaves it asynchronous. */
 int map_exact(em_ctx *ctx, const em_pairs *pr, const double *d_x, const double *d_y, const double *d_z,

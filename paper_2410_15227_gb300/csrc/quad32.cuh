@@ -43,8 +43,9 @@
 //
 // Work is organised in segments: one segment is one kernel piece of one edge
 // (an s-interval cut into m sub-pieces of 8 nodes each) with everything its
-// integrand needs, so that a warp can evaluate the segments of 32 different
-// pairs side by side with one copy of the node loop.
+// integrand needs.  A warp evaluates the sub-pieces of the segments of 32
+// different pairs side by side, one sub-piece per lane, with one copy of the
+// node loop.
 #pragma once
 
 #include <cuda_runtime.h>
@@ -57,16 +58,13 @@ namespace emq {
 
 constexpr int kNodeUnroll = EM_NODE_UNROLL;
 
-__device__ __forceinline__ float gl_x(int i)
-{
-    return i == 0 ? 0.18343464249564978f : i == 1 ? 0.52553240991632899f : i == 2 ? 0.79666647741362673f
-                                                                                  : 0.96028985649753618f;
-}
-__device__ __forceinline__ float gl_w(int i)
-{
-    return i == 0 ? 0.36268378337836166f : i == 1 ? 0.31370664587788688f : i == 2 ? 0.22238103445337443f
-                                                                                  : 0.10122853629037706f;
-}
+// 8-point Gauss-Legendre rule on [-1, 1]: the positive abscissae and their
+// weights (the rule is symmetric); in constant memory, read with an index that
+// is the same on every lane
+static __constant__ float c_gl_x[4] = {0.18343464249564978f, 0.52553240991632899f, 0.79666647741362673f,
+                                0.96028985649753618f};
+static __constant__ float c_gl_w[4] = {0.36268378337836166f, 0.31370664587788688f, 0.22238103445337443f,
+                                0.10122853629037706f};
 
 // Segment fields (see the header comment):
 //   sa, hl  start of the first sub-piece, half-length of every sub-piece
@@ -75,55 +73,55 @@ __device__ __forceinline__ float gl_w(int i)
 //   Rr      reference distance of the difference (R, or 1)
 //   v       2 - Rr, computed where it keeps its relative precision (piece 2)
 //   add     constant added to the difference: K(1) - K(R) when Rr = 1, else 0
-//   meta    m | piece1 << 8 | tilde << 9
+//   meta    m | piece1 << 8 | tilde << 9, m the number of sub-pieces
 constexpr int SEG_PIECE1 = 1 << 8;
 constexpr int SEG_TILDE = 1 << 9;
 
-// int over the segment of [K(Q(s)) - K(R)] / cosh(s) ds
-__device__ __forceinline__ float seg_eval(float sa, float hl, float A, float B2, float c4, float dd, float Rr,
+// int over one sub-piece [mid - hl, mid + hl] of a segment (8 Gauss-Legendre
+// nodes) of [K(Q(s)) - K(R)] / cosh(s) ds.  Q and 1/Q come from one reciprocal
+// square root and a Newton step (about 1 ulp); the other quotients are
+// reciprocals of quantities bounded away from zero.
+__device__ __forceinline__ float sub_eval(float mid, float hl, float A, float B2, float c4, float dd, float Rr,
                                           float vr, float add, int meta)
 {
-    const int m = meta & 255;
     const bool piece1 = (meta & SEG_PIECE1) != 0;
     const bool tilde = (meta & SEG_TILDE) != 0;
     const float R2 = Rr * Rr;
     // piece 1: powers of R; piece 2: powers of v = 2 - Rr
     const float v = piece1 ? Rr : vr;
     const float p2 = v * v, p3 = p2 * v, p4 = p2 * p2;
-    float tot = 0.f;
-    for (int p = 0; p < m; ++p) {
-        const float mid = sa + (2.f * p + 1.f) * hl;
-        float acc = 0.f;
+    const float iRr = __fdividef(1.f, Rr);   // Rr >= 1e-30 wherever it is used
+    float acc = 0.f;
 #pragma unroll kNodeUnroll
-        for (int i = 0; i < 8; ++i) {
-            const float s = mid + ((i & 1) ? -hl : hl) * gl_x(i >> 1);
-            const float em = expm1f(s);
-            const float e = 1.f + em;
-            const float ei = __fdividef(1.f, e);
-            const float ch = 0.5f * (e + ei);
-            const float tau = 0.5f * A * (em * (1.f + ei));
-            const float t2 = tau * tau;
-            const float Q = sqrtf(B2 + t2);
-            const float d = dd + t2;
-            float f;
-            if (piece1) {
-                const float iq = __fdividef(1.f, Q + Rr);
-                const float s5 = (((Q + Rr) * Q + p2) * Q + p3) * Q + p4;
-                const float phf = (1.f / 6.f) - 0.075f * (Q * Q + R2) + 0.025f * s5 * iq;
-                f = tilde ? d * (__fdividef(0.25f * iq, Q * Rr) - phf) : d * phf;
-            } else {
-                const float iQ = __fdividef(1.f, Q);
-                const float u = __fdividef(c4 - t2, 2.f + Q);
-                const float S4 = ((u + v) * u + p2) * u + p3;
-                const float br = u * S4 * (1.f + iQ) + p4 * (1.f + __fdividef(2.f * iQ, Rr));
-                const float x = __fdividef(d, 120.f * (Q + Rr)) * br;
-                f = (tilde ? x : __fdividef(d * iQ, 4.f * Rr * (Q + Rr)) - x) + add;
-            }
-            acc += gl_w(i >> 1) * __fdividef(f, ch);
+    for (int i = 0; i < 8; ++i) {
+        const float s = fmaf((i & 1) ? -hl : hl, c_gl_x[i >> 1], mid);
+        const float em = expm1f(s);
+        const float e = 1.f + em;
+        const float ei = __fdividef(1.f, e);
+        const float ch = 0.5f * (e + ei);
+        const float tau = 0.5f * A * (em * (1.f + ei));
+        const float t2 = tau * tau;
+        const float q2 = B2 + t2;
+        float iQ = rsqrtf(q2);
+        iQ = iQ * fmaf(-0.5f * q2 * iQ, iQ, 1.5f);
+        const float Q = q2 * iQ;
+        const float d = dd + t2;
+        const float iq = __fdividef(1.f, Q + Rr);
+        float f;
+        if (piece1) {
+            const float s5 = (((Q + Rr) * Q + p2) * Q + p3) * Q + p4;
+            const float phf = (1.f / 6.f) - 0.075f * (Q * Q + R2) + 0.025f * s5 * iq;
+            f = tilde ? d * ((0.25f * iq) * iQ * iRr - phf) : d * phf;
+        } else {
+            const float u = __fdividef(c4 - t2, 2.f + Q);
+            const float S4 = ((u + v) * u + p2) * u + p3;
+            const float br = u * S4 * (1.f + iQ) + p4 * (1.f + 2.f * iQ * iRr);
+            const float x = d * iq * (1.f / 120.f) * br;
+            f = (tilde ? x : d * iQ * (0.25f * iRr) * iq - x) + add;
         }
-        tot += acc * hl;
+        acc += c_gl_w[i >> 1] * __fdividef(f, ch);
     }
-    return tot;
+    return acc * hl;
 }
 
 // ---------------------------------------------------------------------------
