@@ -23,9 +23,9 @@ constexpr int WCAND = 256;   // candidate list (power of two for the bitonic sor
 struct WCell {
     double pl[WMAXP][4];
     double v[2][WMAXV][3];
-    float vf[WMAXV][4];   // the current vertices rounded to FP32, w = |x| + |y| + |z|
+    float vf[2][WMAXV][4];   // the vertices rounded to FP32 (same buffers as v), w = |x| + |y| + |z|
     double f[WMAXV];
-    double cd2[WCAND];
+    float cd2[WCAND];        // sort keys of the candidates: squared distances rounded to FP32
     int cid[WCAND];
     int pid[WMAXP];
     int out_list[WMAXV];
@@ -40,18 +40,14 @@ __device__ __forceinline__ bool has_edge(const uint8_t *t, uint8_t a, uint8_t b)
     return (t[0] == a && t[1] == b) || (t[1] == a && t[2] == b) || (t[2] == a && t[0] == b);
 }
 
-// Refresh the FP32 copy of the current vertices (all lanes).
-__device__ __forceinline__ void wsync_vf(WCell &c)
+// The FP32 copy of one vertex.
+__device__ __forceinline__ void set_vf(float *vf, double x, double y, double z)
 {
-    const int cur = c.cur;
-    for (int t = threadIdx.x & 31; t < c.nt; t += 32) {
-        const float x = (float)c.v[cur][t][0], y = (float)c.v[cur][t][1], z = (float)c.v[cur][t][2];
-        c.vf[t][0] = x;
-        c.vf[t][1] = y;
-        c.vf[t][2] = z;
-        c.vf[t][3] = fabsf(x) + fabsf(y) + fabsf(z);
-    }
-    __syncwarp();
+    const float xf = (float)x, yf = (float)y, zf = (float)z;
+    vf[0] = xf;
+    vf[1] = yf;
+    vf[2] = zf;
+    vf[3] = fabsf(xf) + fabsf(yf) + fabsf(zf);
 }
 
 __device__ void wcell_box(WCell &c, const double *box, double gx, double gy, double gz)
@@ -83,10 +79,10 @@ __device__ void wcell_box(WCell &c, const double *box, double gx, double gy, dou
             c.v[0][i][0] = sx ? hi[0] : lo[0];
             c.v[0][i][1] = sy ? hi[1] : lo[1];
             c.v[0][i][2] = sz ? hi[2] : lo[2];
+            set_vf(c.vf[0][i], c.v[0][i][0], c.v[0][i][1], c.v[0][i][2]);
         }
     }
     __syncwarp();
-    wsync_vf(c);
 }
 
 // Drop planes no vertex refers to (one lane; rare).
@@ -129,8 +125,9 @@ __device__ int wclip(WCell &c, double nx, double ny, double nz, double d, int id
         const float nmax = fmaxf(fmaxf(fabsf(nxf), fabsf(nyf)), fabsf(nzf));
         bool maybe = false;
         for (int t = lane; t < nt; t += 32) {
-            const float ff = nxf * c.vf[t][0] + nyf * c.vf[t][1] + nzf * c.vf[t][2] - df;
-            maybe = maybe || ff > -1e-5f * (nmax * c.vf[t][3] + fabsf(df));
+            const float *vf = c.vf[cur][t];
+            const float ff = nxf * vf[0] + nyf * vf[1] + nzf * vf[2] - df;
+            maybe = maybe || ff > -1e-5f * (nmax * vf[3] + fabsf(df));
         }
         if (!__any_sync(0xffffffffu, maybe)) return 0;
     }
@@ -156,6 +153,7 @@ __device__ int wclip(WCell &c, double nx, double ny, double nz, double d, int id
             int pos = nk + __popc(mk & lanemask_lt());
             for (int e = 0; e < 3; ++e) c.tri[nxt][pos][e] = c.tri[cur][t][e];
             for (int e = 0; e < 3; ++e) c.v[nxt][pos][e] = c.v[cur][t][e];
+            for (int e = 0; e < 4; ++e) c.vf[nxt][pos][e] = c.vf[cur][t][e];
         }
         if (out) c.out_list[nout + __popc(mo & lanemask_lt())] = t;
         nk += __popc(mk);
@@ -202,6 +200,7 @@ __device__ int wclip(WCell &c, double nx, double ny, double nz, double d, int id
                 c.v[nxt][pos][0] = px;
                 c.v[nxt][pos][1] = py;
                 c.v[nxt][pos][2] = pz;
+                set_vf(c.vf[nxt][pos], px, py, pz);
             }
         }
         nn += __popc(m);
@@ -219,7 +218,6 @@ __device__ int wclip(WCell &c, double nx, double ny, double nz, double d, int id
         c.cur = nxt;
     }
     __syncwarp();
-    wsync_vf(c);
     return 1;
 }
 
@@ -279,7 +277,7 @@ __device__ int gather(WCell &c, const em::ChunkTree &T, const double *__restrict
         if (hit) {
             int pos = n + __popc(m & lanemask_lt());
             if (pos < WCAND) {
-                c.cd2[pos] = (double)d2f;
+                c.cd2[pos] = d2f;
                 c.cid[pos] = (int)k;
             }
         }
@@ -290,7 +288,7 @@ __device__ int gather(WCell &c, const em::ChunkTree &T, const double *__restrict
     return n > WCAND ? -1 : n;
 }
 
-// Bitonic sort of the first n candidates by (d^2, index), padded with
+// Bitonic sort of the first n candidates by (d^2 in FP32, index), padded with
 // (inf, max) up to the next power of two (at most WCAND).
 __device__ void sort_cand(WCell &c, int n)
 {
@@ -308,7 +306,7 @@ __device__ void sort_cand(WCell &c, int n)
                 int lo = 2 * i - (i & (stride - 1));
                 int hi = lo + stride;
                 bool up = ((lo & size) == 0);
-                double a = c.cd2[lo], b = c.cd2[hi];
+                const float a = c.cd2[lo], b = c.cd2[hi];
                 int ia = c.cid[lo], ib = c.cid[hi];
                 bool gt = (a > b) || (a == b && ia > ib);
                 if (gt == up) {
@@ -351,13 +349,13 @@ __device__ int gather_cutting(WCell &c, const em::ChunkTree &T, const double *__
         }
         // some vertex nearer to the box than to the site
         for (int t = 0; t < nt; ++t) {
-            const float vx = c.vf[t][0], vy = c.vf[t][1], vz = c.vf[t][2];
+            const float vx = c.vf[cur][t][0], vy = c.vf[cur][t][1], vz = c.vf[cur][t][2];
             float dx = fmaxf(fmaxf(lx - vx, vx - hx), 0.f);
             float dy = fmaxf(fmaxf(ly - vy, vy - hy), 0.f);
             float dz = fmaxf(fmaxf(lz - vz, vz - hz), 0.f);
             const float db = dx * dx + dy * dy + dz * dz;
             const float dg = vx * vx + vy * vy + vz * vz;
-            const float S = gabs + babs + c.vf[t][3];
+            const float S = gabs + babs + c.vf[cur][t][3];
             if (db < dg + 1e-5f * S * S) return true;
         }
         return false;
@@ -396,31 +394,42 @@ __device__ int gather_cutting(WCell &c, const em::ChunkTree &T, const double *__
                     const float df = 0.5f * rf * rf, rabs = fabsf(ex) + fabsf(ey) + fabsf(ez);
                     bool maybe = false;
                     for (int t = 0; t < nt && !maybe; ++t) {
-                        const float ff = ex * c.vf[t][0] + ey * c.vf[t][1] + ez * c.vf[t][2] - df;
-                        maybe = ff > -1e-5f * (gabs + rabs + c.vf[t][3]) * (c.vf[t][3] + rabs);
+                        const float *vf = c.vf[cur][t];
+                        const float ff = ex * vf[0] + ey * vf[1] + ez * vf[2] - df;
+                        maybe = ff > -1e-5f * (gabs + rabs + vf[3]) * (vf[3] + rabs);
                     }
                     cand = maybe;
                 }
             }
+            double rx = 0.0, ry = 0.0, rz = 0.0;
             if (cand) {
-                double rx = xs[k] - gx, ry = ys[k] - gy, rz = zs[k] - gz;
+                rx = xs[k] - gx;
+                ry = ys[k] - gy;
+                rz = zs[k] - gz;
                 d2 = rx * rx + ry * ry + rz * rz;
-                if (d2 >= skip2 && d2 < hi2) {
-                    // a vertex beyond the bisector by more than rounding: vertices on an
-                    // already applied bisector sit at |f| ~ 1e-16 d and must not re-qualify
-                    double d = 0.5 * (rx * rx + ry * ry + rz * rz);
-                    const double tol = 1e-12 * d;
-                    for (int t = 0; t < nt && !hit; ++t) {
-                        const double *v = c.v[cur][t];
-                        hit = rx * v[0] + ry * v[1] + rz * v[2] - d > tol;
-                    }
+                cand = d2 >= skip2 && d2 < hi2;
+            }
+            // FP64: a vertex beyond the bisector by more than rounding (vertices on
+            // an already applied bisector sit at |f| ~ 1e-16 d and must not
+            // re-qualify).  One candidate at a time, the lanes over the vertices.
+            for (unsigned cm = __ballot_sync(0xffffffffu, cand); cm; cm &= cm - 1) {
+                const int src = __ffs(cm) - 1;
+                const double qx = __shfl_sync(0xffffffffu, rx, src), qy = __shfl_sync(0xffffffffu, ry, src),
+                             qz = __shfl_sync(0xffffffffu, rz, src);
+                const double d = 0.5 * (qx * qx + qy * qy + qz * qz);
+                const double tol = 1e-12 * d;
+                bool beyond = false;
+                for (int t = lane; t < nt; t += 32) {
+                    const double *v = c.v[cur][t];
+                    beyond = beyond || qx * v[0] + qy * v[1] + qz * v[2] - d > tol;
                 }
+                if (__any_sync(0xffffffffu, beyond) && lane == src) hit = true;
             }
             unsigned m = __ballot_sync(0xffffffffu, hit);
             if (hit) {
                 int pos = n + __popc(m & lanemask_lt());
                 if (pos < WCAND) {
-                    c.cd2[pos] = d2;
+                    c.cd2[pos] = (float)d2;
                     c.cid[pos] = (int)k;
                 }
             }
@@ -437,20 +446,40 @@ __device__ int gather_cutting(WCell &c, const em::ChunkTree &T, const double *__
     return n > WCAND ? -1 : n;
 }
 
-// Clip by the first nc (sorted) candidates; records the cutting ones.
-__device__ int clip_sorted(WCell &c, const double *__restrict__ xs, const double *__restrict__ ys,
-                           const double *__restrict__ zs, const int32_t *__restrict__ perm, int64_t n, double gx,
-                           double gy, double gz, int nc, int32_t *clip_ids, int &nclip)
+// Clip by the first nc (sorted) candidates; records the cutting ones.  A
+// candidate first meets an FP32 side test on the rounded positions (the same
+// band as in gather_cutting, above the rounding of the coordinates): one that
+// every vertex clears cuts nothing and costs no FP64 work.
+__device__ int clip_sorted(WCell &c, const em::ChunkTree &T, const double *__restrict__ xs,
+                           const double *__restrict__ ys, const double *__restrict__ zs,
+                           const int32_t *__restrict__ perm, int64_t n, double gx, double gy, double gz, int nc,
+                           int32_t *clip_ids, int &nclip)
 {
+    const int lane = threadIdx.x & 31;
+    const float gxf = (float)gx, gyf = (float)gy, gzf = (float)gz;
+    const float gabs = fabsf(gxf) + fabsf(gyf) + fabsf(gzf);
     for (int i = 0; i < nc; ++i) {
         int k = c.cid[i];
         if (k < 0 || k >= n) return emv::VS_BOUNDS;
+        {
+            const float4 pk = T.pts[k];
+            const float ex = pk.x - gxf, ey = pk.y - gyf, ez = pk.z - gzf;
+            const float df = 0.5f * (ex * ex + ey * ey + ez * ez), rabs = fabsf(ex) + fabsf(ey) + fabsf(ez);
+            const int cur = c.cur;
+            bool maybe = false;
+            for (int t = lane; t < c.nt; t += 32) {
+                const float *vf = c.vf[cur][t];
+                const float ff = ex * vf[0] + ey * vf[1] + ez * vf[2] - df;
+                maybe = maybe || ff > -1e-5f * (gabs + rabs + vf[3]) * (vf[3] + rabs);
+            }
+            if (!__any_sync(0xffffffffu, maybe)) continue;
+        }
         double dx = xs[k] - gx, dy = ys[k] - gy, dz = zs[k] - gz;
         int r = wclip(c, dx, dy, dz, 0.5 * (dx * dx + dy * dy + dz * dz), perm[k]);
         if (r < 0) return -r;
         if (r > 0 && clip_ids) {   // record the cutting bisectors when asked
             if (nclip >= emv::MAXCLIP) return emv::VS_CLIPS;
-            if ((threadIdx.x & 31) == 0) clip_ids[nclip] = k;
+            if (lane == 0) clip_ids[nclip] = k;
             ++nclip;
         }
     }
@@ -524,7 +553,7 @@ __device__ int wbuild_cell(WCell &c, const em::ChunkTree &T, const double *__res
     double skip2 = -1.0;
     if (nc > 0) {
         sort_cand(c, nc);
-        int st = clip_sorted(c, xs, ys, zs, perm, n, gx, gy, gz, nc, clip_ids, nclip);
+        int st = clip_sorted(c, T, xs, ys, zs, perm, n, gx, gy, gz, nc, clip_ids, nclip);
         if (st) return status | st;
     }
     if (nc >= 0) skip2 = R2;   // every generator nearer than R was applied
@@ -542,7 +571,7 @@ __device__ int wbuild_cell(WCell &c, const em::ChunkTree &T, const double *__res
         if (m < 0) return status | emv::VS_CANDIDATES;
         if (m > 0) {
             sort_cand(c, m);
-            int st = clip_sorted(c, xs, ys, zs, perm, n, gx, gy, gz, m, clip_ids, nclip);
+            int st = clip_sorted(c, T, xs, ys, zs, perm, n, gx, gy, gz, m, clip_ids, nclip);
             if (st) return status | st;
         }
         skip2 = hi2;
