@@ -3,7 +3,9 @@
 #include <cub/device/device_radix_sort.cuh>
 #include <cub/device/device_scan.cuh>
 
+#include <cstdint>
 #include <cstring>
+#include <mutex>
 
 #include "common.cuh"
 
@@ -18,6 +20,32 @@ void em_set_error(const char *fmt, ...)
 }
 
 EM_EXPORT const char *em_last_error(void) { return g_last_error; }
+
+cudaMemPool_t em_device_pool(int device)
+{
+    constexpr int kMaxDevices = 64;
+    static std::mutex mu;
+    static cudaMemPool_t pools[kMaxDevices] = {};
+    static bool tried[kMaxDevices] = {};
+    if (device < 0 || device >= kMaxDevices) return nullptr;
+    std::lock_guard<std::mutex> lock(mu);
+    if (!tried[device]) {
+        tried[device] = true;
+        cudaMemPoolProps props{};
+        props.allocType = cudaMemAllocationTypePinned;
+        props.location.type = cudaMemLocationTypeDevice;
+        props.location.id = device;
+        cudaMemPool_t pool = nullptr;
+        if (cudaMemPoolCreate(&pool, &props) == cudaSuccess) {
+            uint64_t threshold = UINT64_MAX;
+            cudaMemPoolSetAttribute(pool, cudaMemPoolAttrReleaseThreshold, &threshold);
+            pools[device] = pool;
+        } else {
+            cudaGetLastError();   // fall back to the default pool
+        }
+    }
+    return pools[device];
+}
 
 EM_EXPORT void em_params_default(em_params *p)
 {

@@ -60,6 +60,14 @@ void em_set_error(const char *fmt, ...);
         }                                                                                          \
     } while (0)
 
+// The library's memory pool on a device (created on first use; null if the
+// device has none): every allocation below comes from it.  Its release
+// threshold is the maximum, so memory that one call frees stays reserved for
+// the next call instead of going back to the system at each synchronisation
+// (a step maps several GB of scratch); it is returned at process exit.  The
+// device's default pool, and anyone else using it, are not touched.
+cudaMemPool_t em_device_pool(int device);
+
 // Stream-ordered device allocations released together (handle memory, or a
 // call's scratch when used as a local).
 struct DevArena {
@@ -80,7 +88,10 @@ struct DevArena {
     {
         *p = nullptr;
         size_t bytes = (n ? n : 1) * sizeof(T);
-        cudaError_t e = cudaMallocAsync((void **)p, bytes, stream);
+        int dev = 0;
+        cudaMemPool_t pool = cudaGetDevice(&dev) == cudaSuccess ? em_device_pool(dev) : nullptr;
+        cudaError_t e = pool ? cudaMallocFromPoolAsync((void **)p, bytes, pool, stream)
+                             : cudaMallocAsync((void **)p, bytes, stream);
         if (e != cudaSuccess) {
             em_set_error("device allocation of %zu bytes failed: %s", bytes, cudaGetErrorString(e));
             cudaGetLastError();
