@@ -78,6 +78,7 @@ EM_EXPORT int em_ctx_create(em_ctx **ctx, int device, void *stream)
     c->launches = 0;
     c->timing = false;
     c->recorded[0] = c->recorded[1] = false;
+    c->pairs_hint = 0;
     for (auto &e : c->ev) e = nullptr;
     *ctx = c;
     return EM_OK;

@@ -22,6 +22,9 @@ struct em_ctx {
     bool timing;
     cudaEvent_t ev[4];
     bool recorded[2];
+    // size of find_pairs' unsorted hit buffer for the next call: the last
+    // call's pair count plus 1/8 (0: none yet)
+    int64_t pairs_hint;
 };
 
 void em_set_error(const char *fmt, ...);

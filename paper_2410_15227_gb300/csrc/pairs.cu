@@ -10,7 +10,8 @@
 // which is a few ulp of that same scale -- is decided there; only candidates
 // inside the band take the exact FP64 test, which also sets the near flag.
 // The pair set is therefore the FP64 predicate's.  Hits are compacted with a
-// warp ballot, first counted, then written at the cell's scanned offset.
+// warp ballot into a per-warp buffer and written, unordered, at positions
+// reserved with an atomic add; one radix sort by (j, i) puts them in order.
 #include "common.cuh"
 #include "tree_util.cuh"
 
@@ -100,23 +101,45 @@ __device__ __forceinline__ float cell_dist2_f32(float rx, float ry, float rz, in
 }
 
 // One warp per cell: candidate particles from the sphere hierarchy, FP32
-// classification, exact FP64 test inside the band, ballot compaction.  Pass 1 (keys == NULL) writes counts; pass 2
-// writes (j << 32 | i) keys and near flags at the cell's offset.
-__global__ void __launch_bounds__(128) k_cell_pairs(int64_t ncell, em::ChunkTree T, const double *__restrict__ xs,
-                                                     const double *__restrict__ ys, const double *__restrict__ zs,
-                                                     const double *__restrict__ hs, const int32_t *__restrict__ perm,
-                                                     const double *__restrict__ gen, const double *__restrict__ radius,
-                                                     const int64_t *__restrict__ cfo, const int64_t *__restrict__ fvo,
-                                                     const PlaneD *__restrict__ plane, const EdgeD *__restrict__ edge,
-                                                     const PlaneF *__restrict__ plane_f,
-                                                     const EdgeF *__restrict__ edge_f, float margin,
-                                                     int64_t *__restrict__ count,
-                                                     const int64_t *__restrict__ offset, uint64_t *__restrict__ keys,
-                                                     int32_t *__restrict__ nearf)
+// classification, exact FP64 test inside the band, ballot compaction into a
+// per-warp buffer in shared memory.  A full (or the final) buffer is written
+// at a position reserved with one atomic add on the global hit counter, as
+// (j << 32 | i) keys and near flags: unordered, the caller sorts them.  Hits
+// past the capacity are counted but not written; the caller then repeats the
+// pass with room for all of them.
+constexpr int PAIRS_WARPS = 4;
+constexpr int PAIRS_BUF = 128;   // hits a warp holds before writing them out
+
+__global__ void __launch_bounds__(32 * PAIRS_WARPS)
+    k_cell_pairs(int64_t ncell, em::ChunkTree T, const double *__restrict__ xs, const double *__restrict__ ys,
+                 const double *__restrict__ zs, const double *__restrict__ hs, const int32_t *__restrict__ perm,
+                 const double *__restrict__ gen, const double *__restrict__ radius, const int64_t *__restrict__ cfo,
+                 const int64_t *__restrict__ fvo, const PlaneD *__restrict__ plane, const EdgeD *__restrict__ edge,
+                 const PlaneF *__restrict__ plane_f, const EdgeF *__restrict__ edge_f, float margin,
+                 unsigned long long *__restrict__ counter, int64_t capacity, uint64_t *__restrict__ keys,
+                 int32_t *__restrict__ nearf)
 {
+    __shared__ uint64_t buf_key[PAIRS_WARPS][PAIRS_BUF];
+    __shared__ int32_t buf_near[PAIRS_WARPS][PAIRS_BUF];
+    const int w = threadIdx.x >> 5;
     int64_t j = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
-    if (j >= ncell) return;
+    if (j >= ncell) return;   // the whole warp
     const int lane = threadIdx.x & 31;
+    int nb = 0;   // hits in the warp's buffer (the same on every lane)
+    auto write_out = [&]() {
+        unsigned long long at = 0;
+        if (lane == 0) at = atomicAdd(counter, (unsigned long long)nb);
+        at = __shfl_sync(0xffffffffu, at, 0);
+        for (int t = lane; t < nb; t += 32) {
+            const unsigned long long pos = at + (unsigned long long)t;
+            if (pos < (unsigned long long)capacity) {
+                keys[pos] = buf_key[w][t];
+                nearf[pos] = buf_near[w][t];
+            }
+        }
+        __syncwarp();
+        nb = 0;
+    };
     const double gx = gen[3 * j], gy = gen[3 * j + 1], gz = gen[3 * j + 2];
     const double Rj = radius[j];
     const int64_t f0 = cfo[j], f1 = cfo[j + 1];
@@ -124,8 +147,6 @@ __global__ void __launch_bounds__(128) k_cell_pairs(int64_t ncell, em::ChunkTree
     const float Rf = (float)Rj;
     const float gxf = (float)gx, gyf = (float)gy, gzf = (float)gz;
     const float gscale = fabsf(gxf) + fabsf(gyf) + fabsf(gzf);
-    int64_t n = 0;
-    const int64_t base = keys ? offset[j] : 0;
     em::warp_traverse(T, (float)gx, (float)gy, (float)gz, R * R, INT64_MAX, [&](int64_t k, bool valid) {
         bool hit = false, nearb = false;
         // candidates beyond R_j + 2h by the band (which here also covers the
@@ -157,15 +178,17 @@ __global__ void __launch_bounds__(128) k_cell_pairs(int64_t ncell, em::ChunkTree
                 }
             }
         }
-        uint32_t b = __ballot_sync(0xffffffffu, hit);
-        if (keys && hit) {
-            int64_t pos = base + n + __popc(b & ((1u << lane) - 1u));
-            keys[pos] = ((uint64_t)j << 32) | (uint32_t)perm[k];
-            nearf[pos] = nearb ? 1 : 0;
+        const uint32_t b = __ballot_sync(0xffffffffu, hit);
+        if (nb + __popc(b) > PAIRS_BUF) write_out();
+        if (hit) {
+            const int pos = nb + __popc(b & ((1u << lane) - 1u));
+            buf_key[w][pos] = ((uint64_t)j << 32) | (uint32_t)perm[k];
+            buf_near[w][pos] = nearb ? 1 : 0;
         }
-        n += __popc(b);
+        __syncwarp();
+        nb += __popc(b);
     });
-    if (!keys && lane == 0) count[j] = n;
+    if (nb > 0) write_out();
 }
 
 __global__ void k_split_keys(int64_t n, const uint64_t *__restrict__ keys, const int32_t *__restrict__ nearf,
@@ -255,36 +278,43 @@ static int find_pairs_impl(em_ctx *ctx, int64_t np, const double *x, const doubl
     for (int c = 0; c < 6; ++c) ext = fmax(ext, fabs(box[c]));
     const float margin = (float)(4e-7 * (ext + 1.0));
     const int64_t nc = v->ncell;
-    int64_t *count, *offset;
-    EM_TRY(tmp.alloc(&count, nc + 1));
-    EM_TRY(tmp.alloc(&offset, nc + 1));
-    EM_CUDA(cudaMemsetAsync(count + nc, 0, sizeof(int64_t), st));
-    k_cell_pairs<<<em_grid(nc * 32, 128), 128, 0, st>>>(nc, T, xs, ys, zs, hs, perm, v->gen, v->radius,
-                                                         v->cell_face_off, v->face_vert_off, v->plane, v->edge,
-                                                         v->plane_f, v->edge_f, margin, count, nullptr, nullptr,
-                                                         nullptr);
-    EM_LAUNCHED(ctx);
-    EM_TRY(em_exclusive_scan_i64(ctx, count, offset, nc + 1));
+    // one pass into an unsorted buffer sized from the last call (or a guess
+    // on the first), repeated once with the exact size if it overflowed
+    unsigned long long *counter;
+    EM_TRY(tmp.alloc(&counter, 1));
+    int64_t capacity = ctx->pairs_hint > 0 ? ctx->pairs_hint : 64 * np + (1 << 20);
     int64_t total = 0;
-    EM_CUDA(cudaMemcpyAsync(&total, offset + nc, sizeof(int64_t), cudaMemcpyDeviceToHost, st));
-    EM_CUDA(cudaStreamSynchronize(st));
+    uint64_t *keys = nullptr;
+    int32_t *nearf = nullptr;
+    for (int attempt = 0; attempt < 2; ++attempt) {
+        DevArena buf(st, true);   // released on an early return
+        EM_TRY(buf.alloc(&keys, capacity));
+        EM_TRY(buf.alloc(&nearf, capacity));
+        EM_CUDA(cudaMemsetAsync(counter, 0, sizeof *counter, st));
+        k_cell_pairs<<<em_grid(nc * 32, 32 * PAIRS_WARPS), 32 * PAIRS_WARPS, 0, st>>>(
+            nc, T, xs, ys, zs, hs, perm, v->gen, v->radius, v->cell_face_off, v->face_vert_off, v->plane, v->edge,
+            v->plane_f, v->edge_f, margin, counter, capacity, keys, nearf);
+        EM_LAUNCHED(ctx);
+        unsigned long long hits = 0;
+        EM_CUDA(cudaMemcpyAsync(&hits, counter, sizeof hits, cudaMemcpyDeviceToHost, st));
+        EM_CUDA(cudaStreamSynchronize(st));
+        total = (int64_t)hits;
+        if (total <= capacity || total >= INT32_MAX) {
+            // keep the buffers: they belong to the call's scratch from here on
+            for (void *q : buf.ptrs) tmp.ptrs.push_back(q);
+            buf.ptrs.clear();
+            break;
+        }
+        buf.release();
+        capacity = total;
+    }
     if (total >= INT32_MAX) {
         em_set_error("find_pairs: %lld pairs exceed the 2^31 limit of one pair list", (long long)total);
         return EM_ECAPACITY;
     }
+    ctx->pairs_hint = total + total / 8 + 1024;
     pr->npairs = total;
-    uint64_t *keys;
-    int32_t *nearf;
-    EM_TRY(tmp.alloc(&keys, total));
-    EM_TRY(tmp.alloc(&nearf, total));
-    if (total) {
-        k_cell_pairs<<<em_grid(nc * 32, 128), 128, 0, st>>>(nc, T, xs, ys, zs, hs, perm, v->gen, v->radius,
-                                                             v->cell_face_off, v->face_vert_off, v->plane, v->edge,
-                                                             v->plane_f, v->edge_f, margin, count, offset, keys,
-                                                             nearf);
-        EM_LAUNCHED(ctx);
-        EM_TRY(em_sort_pairs_u64(ctx, keys, nearf, total, 32 + em_nbits((uint64_t)nc)));
-    }
+    if (total) EM_TRY(em_sort_pairs_u64(ctx, keys, nearf, total, 32 + em_nbits((uint64_t)nc)));
     EM_TRY(pr->mem.alloc(&pr->pair_i, total));
     EM_TRY(pr->mem.alloc(&pr->pair_j, total));
     EM_TRY(pr->mem.alloc(&pr->near, total));
