@@ -135,28 +135,60 @@ struct Density {
     double n, dn;
 };
 
+// Neighbour candidates that pass the FP32 prefilter are collected in a
+// per-warp buffer and summed in FP64 32 at a time, one per lane, so that the
+// FP64 work (the costly part on GB300, whose FP64 rate is 1/64 of FP32) runs
+// with every lane busy instead of on the few lanes of each 32-point chunk
+// that hold a neighbour.
+constexpr int HS_WARPS = 4;
+constexpr int HS_BUF = 64;   // two batches: a chunk adds at most 32 to fewer than 32
+
+// The FP32 prefilter: candidates clearly beyond 2h skip the FP64 work.  The
+// band, 1e-5 of the coordinates' scale plus 2h, is far above the FP32 rounding
+// of the positions, so no neighbour is dropped.  Appends the warp's passing
+// candidates to buf (nb entries, the same on every lane).
+__device__ __forceinline__ void collect(const em::ChunkTree &T, int64_t k, bool valid, float xaf, float yaf,
+                                        float zaf, float lim2, int32_t *buf, int &nb)
+{
+    const int lane = threadIdx.x & 31;
+    bool cand = false;
+    if (valid) {
+        const float4 pk = T.pts[k];
+        const float ex = pk.x - xaf, ey = pk.y - yaf, ez = pk.z - zaf;
+        cand = ex * ex + ey * ey + ez * ez < lim2;
+    }
+    const unsigned b = __ballot_sync(0xffffffffu, cand);
+    if (cand) buf[nb + __popc(b & ((1u << lane) - 1u))] = (int32_t)k;
+    __syncwarp();
+    nb += __popc(b);
+}
+
+// Drop the first 32 entries of buf (already summed).
+__device__ __forceinline__ void shift32(int32_t *buf, int &nb)
+{
+    const int lane = threadIdx.x & 31;
+    const int32_t v = lane + 32 < nb ? buf[lane + 32] : 0;
+    __syncwarp();
+    if (lane + 32 < nb) buf[lane] = v;
+    __syncwarp();
+    nb -= 32;
+}
+
 // n(h) and dn/dh for the pseudo-particle at (xa, ya, za), summed over the
 // population inside 2h; the result is identical on all lanes.
 __device__ Density warp_density(const em::ChunkTree &T, const double *__restrict__ qx,
                                 const double *__restrict__ qy, const double *__restrict__ qz, double xa, double ya,
-                                double za, double h, float margin)
+                                double za, double h, float margin, int32_t *buf)
 {
+    const int lane = threadIdx.x & 31;
     double s = 0.0, ds = 0.0;
     const double ih = 1.0 / h;
     const double norm = ih * ih * ih * 0.31830988618379067154;   // 1/(pi h^3)
     float R = (float)(2.0 * h) + margin;
-    // FP32 prefilter: candidates of the walk (whole 32-point chunks) that are
-    // clearly beyond 2h skip the FP64 work.  The band, 1e-5 of the
-    // coordinates' scale plus 2h, is far above the FP32 rounding of the
-    // positions, so no neighbour is dropped.
     const float xaf = (float)xa, yaf = (float)ya, zaf = (float)za, h2f = (float)(2.0 * h);
     const float lim = h2f + 1e-5f * (fabsf(xaf) + fabsf(yaf) + fabsf(zaf) + h2f);
     const float lim2 = lim * lim;
-    em::warp_traverse(T, (float)xa, (float)ya, (float)za, R * R, INT64_MAX, [&](int64_t k, bool valid) {
-        if (!valid) return;
-        const float4 pk = T.pts[k];
-        const float ex = pk.x - xaf, ey = pk.y - yaf, ez = pk.z - zaf;
-        if (ex * ex + ey * ey + ez * ez >= lim2) return;
+    auto sum_one = [&](int64_t k) {
         double dx = qx[k] - xa, dy = qy[k] - ya, dz = qz[k] - za;
         double q = sqrt(dx * dx + dy * dy + dz * dz) * ih;
         if (q < 2.0) {
@@ -164,7 +196,17 @@ __device__ Density warp_density(const em::ChunkTree &T, const double *__restrict
             s += w * norm;
             ds += -(3.0 * w + q * em::m4_dw(q)) * norm * ih;
         }
+    };
+    int nb = 0;
+    em::warp_traverse(T, xaf, yaf, zaf, R * R, INT64_MAX, [&](int64_t k, bool valid) {
+        collect(T, k, valid, xaf, yaf, zaf, lim2, buf, nb);
+        if (nb >= 32) {
+            sum_one(buf[lane]);
+            shift32(buf, nb);
+        }
     });
+    if (lane < nb) sum_one(buf[lane]);
+    __syncwarp();
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) {
         s += __shfl_xor_sync(0xffffffffu, s, o);
@@ -176,14 +218,15 @@ __device__ Density warp_density(const em::ChunkTree &T, const double *__restrict
 // Sign of f(h) = h_fact n(h)^(-1/3) - h (Eq. 8) for the bisection, which uses
 // nothing else.  Every term of n is non-negative, so once the running sum
 // exceeds (h_fact / h)^3 (1 + 1e-9) the sign is negative whatever the rest of
-// the sum; the walk stops there.  This matters for the wide first brackets
-// (h up to 1e2 h_0), whose 2h sphere holds a large share of the population.
-// Otherwise the full sum decides, as in warp_density.  Returns the sign of f
-// (+1, 0 or -1).
+// the sum; the walk stops there (checked after each batch of 32 terms).  This
+// matters for the wide first brackets (h up to 1e2 h_0), whose 2h sphere
+// holds a large share of the population.  Otherwise the full sum decides, as
+// in warp_density.  Returns the sign of f (+1, 0 or -1).
 __device__ int warp_f_sign(const em::ChunkTree &T, const double *__restrict__ qx,
-                                const double *__restrict__ qy, const double *__restrict__ qz, double xa, double ya,
-                                double za, double h, double h_fact, float margin)
+                           const double *__restrict__ qy, const double *__restrict__ qz, double xa, double ya,
+                           double za, double h, double h_fact, float margin, int32_t *buf)
 {
+    const int lane = threadIdx.x & 31;
     double s = 0.0;
     const double ih = 1.0 / h;
     const double norm = ih * ih * ih * 0.31830988618379067154;   // 1/(pi h^3)
@@ -193,22 +236,25 @@ __device__ int warp_f_sign(const em::ChunkTree &T, const double *__restrict__ qx
     const float xaf = (float)xa, yaf = (float)ya, zaf = (float)za, h2f = (float)(2.0 * h);
     const float lim = h2f + 1e-5f * (fabsf(xaf) + fabsf(yaf) + fabsf(zaf) + h2f);
     const float lim2 = lim * lim;
+    auto sum_one = [&](int64_t k) {
+        double dx = qx[k] - xa, dy = qy[k] - ya, dz = qz[k] - za;
+        double q = sqrt(dx * dx + dy * dy + dz * dz) * ih;
+        if (q < 2.0) s += em::m4_w(q) * norm;
+    };
+    int nb = 0;
     bool full = em::warp_traverse_until(T, xaf, yaf, zaf, R * R, [&](int64_t k, bool valid) {
-        if (valid) {
-            const float4 pk = T.pts[k];
-            const float ex = pk.x - xaf, ey = pk.y - yaf, ez = pk.z - zaf;
-            if (ex * ex + ey * ey + ez * ez < lim2) {
-                double dx = qx[k] - xa, dy = qy[k] - ya, dz = qz[k] - za;
-                double q = sqrt(dx * dx + dy * dy + dz * dz) * ih;
-                if (q < 2.0) s += em::m4_w(q) * norm;
-            }
-        }
+        collect(T, k, valid, xaf, yaf, zaf, lim2, buf, nb);
+        if (nb < 32) return true;
+        sum_one(buf[lane]);
+        shift32(buf, nb);
         double tot = s;
 #pragma unroll
         for (int o = 16; o > 0; o >>= 1) tot += __shfl_xor_sync(0xffffffffu, tot, o);
         return !(tot > thr);
     });
     if (!full) return -1;
+    if (lane < nb) sum_one(buf[lane]);
+    __syncwarp();
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
     const double f = h_fact * pow(s, -1.0 / 3.0) - h;
@@ -222,6 +268,8 @@ __global__ void k_h_solve(int64_t npseudo, em::ChunkTree T, const double *__rest
                           const double *__restrict__ py, const double *__restrict__ pz, double h_fact, double tol,
                           int max_newton, float margin, double *__restrict__ ph, int32_t *__restrict__ status)
 {
+    __shared__ int32_t bufs[HS_WARPS][HS_BUF];
+    int32_t *buf = bufs[threadIdx.x >> 5];
     int64_t a = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
     if (a >= npseudo) return;
     if (status[a] != -1) return;   // extracted particles keep their own h
@@ -230,7 +278,7 @@ __global__ void k_h_solve(int64_t npseudo, em::ChunkTree T, const double *__rest
     double h = h0;
     bool ok = false;
     for (int it = 0; it < max_newton; ++it) {
-        Density d = warp_density(T, qx, qy, qz, xa, ya, za, h, margin);
+        Density d = warp_density(T, qx, qy, qz, xa, ya, za, h, margin, buf);
         double f = h_fact * pow(d.n, -1.0 / 3.0) - h;                      // Eq. 8
         double fp = -h_fact * d.dn * pow(d.n, -4.0 / 3.0) / 3.0 - 1.0;      // Eq. 9
         double hn = h - f / fp;                                             // Eq. 10
@@ -246,8 +294,8 @@ __global__ void k_h_solve(int64_t npseudo, em::ChunkTree T, const double *__rest
     if (!ok) {
         // bisection on signs only (warp_f_sign)
         double lo = 1e-2 * h0, hi = 1e2 * h0;
-        const int slo = warp_f_sign(T, qx, qy, qz, xa, ya, za, lo, h_fact, margin);
-        const int shi = warp_f_sign(T, qx, qy, qz, xa, ya, za, hi, h_fact, margin);
+        const int slo = warp_f_sign(T, qx, qy, qz, xa, ya, za, lo, h_fact, margin, buf);
+        const int shi = warp_f_sign(T, qx, qy, qz, xa, ya, za, hi, h_fact, margin, buf);
         const bool plo = slo > 0;
         if (slo * shi > 0) {
             h = h0;
@@ -255,7 +303,7 @@ __global__ void k_h_solve(int64_t npseudo, em::ChunkTree T, const double *__rest
         } else {
             for (int k = 0; k < 200 && (hi - lo) > tol * h0; ++k) {
                 double mid = 0.5 * (lo + hi);
-                if ((warp_f_sign(T, qx, qy, qz, xa, ya, za, mid, h_fact, margin) > 0) == plo) lo = mid;
+                if ((warp_f_sign(T, qx, qy, qz, xa, ya, za, mid, h_fact, margin, buf) > 0) == plo) lo = mid;
                 else hi = mid;
             }
             h = 0.5 * (lo + hi);
@@ -342,7 +390,7 @@ static int pseudo_impl(em_ctx *ctx, const em_tree *t, const double *d_hp, int ns
     // float rounding of positions and boxes: widen the search radius
     const float margin = (float)(4e-7 * (ext + 1.0));
     if (np) {
-        k_h_solve<<<em_grid(np * 32, 128), 128, 0, st>>>(np, T, qx, qy, qz, ps->x, ps->y, ps->z, p->h_fact, p->h_tol,
+        k_h_solve<<<em_grid(np * 32, 32 * HS_WARPS), 32 * HS_WARPS, 0, st>>>(np, T, qx, qy, qz, ps->x, ps->y, ps->z, p->h_fact, p->h_tol,
                                                           p->max_newton, margin, ps->h, ps->status);
         EM_LAUNCHED(ctx);
     }
