@@ -402,28 +402,111 @@ __global__ void __launch_bounds__(128) k_map_fp64(int64_t npairs, const int32_t 
 // beyond 2h skipped; its rounding, about 1e-13, is far inside the mixed
 // mode's tolerance); an entry ~k (< 0) marks a particle in a face plane,
 // recomputed with the full form, for which such a face carries nothing.
-__global__ void __launch_bounds__(128) k_map_fp64_flagged(const int *__restrict__ nflag, const int32_t *__restrict__ pi,
-                                                          const int32_t *__restrict__ pj, const double *__restrict__ x,
-                                                          const double *__restrict__ y, const double *__restrict__ z,
-                                                          const double *__restrict__ h, const double *__restrict__ gen,
-                                                          const double *__restrict__ radius,
-                                                          const int64_t *__restrict__ cfo,
-                                                          const int64_t *__restrict__ fvo,
-                                                          const PlaneD *__restrict__ plane,
-                                                          const EdgeD *__restrict__ edge,
-                                                          const int32_t *__restrict__ list, double *__restrict__ w)
+//
+// One warp per pair: the flagged pairs are few (under 1%) and come from
+// unrelated cells, so a thread per pair would leave most of the GPU idle and
+// its lanes walking different faces.  The lanes take the cell's faces (inside
+// test, skip test, K(D)), then the edges of the faces kept, each edge's
+// closed-form term (edge_full / edge_tilde, the same as pair_weight's) times
+// its orientation signs; a fixed-order warp sum adds them up.  A cell with
+// more than FW_MAXF faces (possible only for imported cells) is done by one
+// lane with pair_weight.
+constexpr int FW_WARPS = 4;
+constexpr int FW_MAXF = 64;
+
+__global__ void __launch_bounds__(32 * FW_WARPS) k_map_fp64_flagged(
+    const int *__restrict__ nflag, const int32_t *__restrict__ pi, const int32_t *__restrict__ pj,
+    const double *__restrict__ x, const double *__restrict__ y, const double *__restrict__ z,
+    const double *__restrict__ h, const double *__restrict__ gen, const double *__restrict__ radius,
+    const int64_t *__restrict__ cfo, const int64_t *__restrict__ fvo, const PlaneD *__restrict__ plane,
+    const EdgeD *__restrict__ edge, const int32_t *__restrict__ list, double *__restrict__ w)
 {
+    __shared__ double fD[FW_WARPS][FW_MAXF], fK[FW_WARPS][FW_MAXF];
+    __shared__ int64_t fE0[FW_WARPS][FW_MAXF];
+    __shared__ int fPre[FW_WARPS][FW_MAXF + 1];
+    __shared__ float fSg[FW_WARPS][FW_MAXF];
+    const int wi = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int64_t n = *nflag;
-    for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < n; t += (int64_t)gridDim.x * blockDim.x) {
+    for (int64_t t = blockIdx.x * (int64_t)FW_WARPS + wi; t < n; t += (int64_t)gridDim.x * FW_WARPS) {
         const int32_t code = list[t];
         const int64_t k = code >= 0 ? code : ~code;
         const int i = pi[k], j = pj[k];
-        double err;
         const double rx = x[i] - gen[3 * j], ry = y[i] - gen[3 * j + 1], rz = z[i] - gen[3 * j + 2];
-        w[k] = code >= 0 ? pair_weight<double, false>(rx, ry, rz, h[i], radius[j], cfo[j], cfo[j + 1], fvo, plane,
-                                                      edge, err)
-                         : pair_weight<double, true>(rx, ry, rz, h[i], radius[j], cfo[j], cfo[j + 1], fvo, plane,
-                                                     edge, err);
+        const double hh = h[i], ih = 1.0 / hh;
+        const int64_t f0 = cfo[j];
+        const int nface = (int)(cfo[j + 1] - f0);
+        if (nface > FW_MAXF) {
+            if (lane == 0) {
+                double err;
+                w[k] = code >= 0 ? pair_weight<double, false>(rx, ry, rz, hh, radius[j], f0, f0 + nface, fvo, plane,
+                                                              edge, err)
+                                 : pair_weight<double, true>(rx, ry, rz, hh, radius[j], f0, f0 + nface, fvo, plane,
+                                                             edge, err);
+            }
+            continue;
+        }
+        // inside test over all faces, then the form
+        bool ins = true;
+        if (code >= 0)
+            for (int f = lane; f < nface; f += 32) {
+                const PlaneD pl = plane[f0 + f];
+                ins = ins && !(pl.w - (pl.x * rx + pl.y * ry + pl.z * rz) < 0.0);
+            }
+        ins = __all_sync(0xffffffffu, ins);
+        const bool full = code < 0 || (ins && sqrt(rx * rx + ry * ry + rz * rz) + radius[j] < 2.0 * hh);
+        // faces: distance, constant, and how many edges each contributes
+        for (int base = 0; base < nface; base += 32) {
+            const int f = base + lane;
+            int cnt = 0;
+            if (f < nface) {
+                const PlaneD pl = plane[f0 + f];
+                const double sd = pl.w - (pl.x * rx + pl.y * ry + pl.z * rz);
+                const double D = fabs(sd) * ih;
+                const bool keep = !(sd == 0.0 || (!full && D >= 2.0));
+                fD[wi][f] = D;
+                fK[wi][f] = full ? K_of<double>(D) : K_tilde<double>(D);
+                fE0[wi][f] = fvo[f0 + f];
+                fSg[wi][f] = sd > 0.0 ? 1.f : -1.f;
+                if (keep) cnt = (int)(fvo[f0 + f + 1] - fvo[f0 + f]);
+            }
+            int xs = cnt;   // inclusive scan of the edge counts over this round
+#pragma unroll
+            for (int o = 1; o < 32; o <<= 1) {
+                const int y = __shfl_up_sync(0xffffffffu, xs, o);
+                if (lane >= o) xs += y;
+            }
+            const int carry = base == 0 ? 0 : fPre[wi][base];
+            __syncwarp();
+            if (lane == 0 && base == 0) fPre[wi][0] = 0;
+            if (f < nface) fPre[wi][f + 1] = carry + xs;
+            __syncwarp();
+        }
+        const int ne = fPre[wi][nface];
+        double acc = 0.0, terr = 0.0;
+        for (int e = lane; e < ne; e += 32) {
+            int lo = 0, hi = nface;   // fPre[lo] <= e < fPre[hi]
+            while (hi - lo > 1) {
+                const int mid = (lo + hi) >> 1;
+                if (fPre[wi][mid] <= e) lo = mid;
+                else hi = mid;
+            }
+            const EdgeD E = edge[fE0[wi][lo] + (e - fPre[wi][lo])];
+            const double a = E.cm - (E.mx * rx + E.my * ry + E.mz * rz);
+            if (a == 0.0) continue;
+            const double A = fabs(a) * ih;
+            const double t0 = (E.ce - (E.ex * rx + E.ey * ry + E.ez * rz)) * ih;
+            const double t1 = t0 + E.L * ih;
+            const double c = full ? edge_full<double>(fD[wi][lo], A, t0, t1, fK[wi][lo], terr)
+                                  : edge_tilde<double>(fD[wi][lo], A, t0, t1, fK[wi][lo], terr);
+            acc += (double)fSg[wi][lo] * ((a > 0.0) ? c : -c);
+        }
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+        if (lane == 0) {
+            const double s = acc * Consts<double>::inv_pi;
+            w[k] = full ? s : ((ins ? 1.0 : 0.0) - s);
+        }
+        __syncwarp();
     }
 }
 
@@ -891,8 +974,8 @@ EM_EXPORT int map_exact(em_ctx *ctx, const em_pairs *pr, const double *d_x, cons
                 EM_CUDA(cudaEventRecord(ctx->ev[2], ctx->stream));
             }
             // FP64 recompute of the flagged pairs; the count stays on the device
-            const int grid = (int)std::min<int64_t>((n + block - 1) / block, 152 * 16);
-            k_map_fp64_flagged<<<grid, block, 0, ctx->stream>>>(nflag, pr->pair_i, pr->pair_j, d_x, d_y, d_z, d_h,
+            const int fgrid = (int)std::min<int64_t>((n + FW_WARPS - 1) / FW_WARPS, 152 * 16);
+            k_map_fp64_flagged<<<fgrid, 32 * FW_WARPS, 0, ctx->stream>>>(nflag, pr->pair_i, pr->pair_j, d_x, d_y, d_z, d_h,
                                                                  v->gen, v->radius, v->cell_face_off,
                                                                  v->face_vert_off, v->plane, v->edge, flagged,
                                                                  d_w_out);
@@ -1005,8 +1088,8 @@ EM_EXPORT int map_exact_noalloc(em_ctx *ctx, const em_pairs *pr, const double *d
                 n, pr->pair_i, pr->pair_j, d_x, d_y, d_z, d_h, v->gen, v->radius, v->cell_face_off,
                 v->face_vert_off, v->plane_f, v->plane_fl, v->edge_f, v->edge_fl, (float)p->fp64_threshold, d_w_out, flagged, nflag);
             EM_LAUNCHED(ctx);
-            const int grid = (int)std::min<int64_t>((n + block - 1) / block, 152 * 16);
-            k_map_fp64_flagged<<<grid, block, 0, ctx->stream>>>(nflag, pr->pair_i, pr->pair_j, d_x, d_y, d_z, d_h,
+            const int fgrid = (int)std::min<int64_t>((n + FW_WARPS - 1) / FW_WARPS, 152 * 16);
+            k_map_fp64_flagged<<<fgrid, 32 * FW_WARPS, 0, ctx->stream>>>(nflag, pr->pair_i, pr->pair_j, d_x, d_y, d_z, d_h,
                                                                  v->gen, v->radius, v->cell_face_off,
                                                                  v->face_vert_off, v->plane, v->edge, flagged,
                                                                  d_w_out);
