@@ -62,7 +62,7 @@ typedef struct {
     double fp64_threshold;  /* mixed mode: recompute a pair in FP64 when its estimated FP32 relative error exceeds this */
     int knn_k;              /* build_voronoi: neighbours staged per generator before the exact fallback; default 48 */
     int leaf_max;           /* build_tree: particles per leaf; default 8 */
-    int block_pairs;        /* map_exact launch shape: threads per block (0 = default) */
+    int block_pairs;        /* map_exact: threads per block of the FP64 kernels, one pair per warp (32..128, a multiple of 32; 0 = 128) */
     int reserved[5];
 } em_params;
 

@@ -378,57 +378,40 @@ __device__ __forceinline__ T pair_weight(T rx, T ry, T rz, T h, T radius, int64_
     return full ? w : ((inside ? T(1) : T(0)) - w);
 }
 
-__global__ void __launch_bounds__(128) k_map_fp64(int64_t npairs, const int32_t *__restrict__ pi,
-                                                  const int32_t *__restrict__ pj, const double *__restrict__ x,
-                                                  const double *__restrict__ y, const double *__restrict__ z,
-                                                  const double *__restrict__ h, const double *__restrict__ gen,
-                                                  const double *__restrict__ radius, const int64_t *__restrict__ cfo,
-                                                  const int64_t *__restrict__ fvo, const PlaneD *__restrict__ plane,
-                                                  const EdgeD *__restrict__ edge, const int32_t *__restrict__ list,
-                                                  double *__restrict__ w)
-{
-    int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-    if (t >= npairs) return;
-    int64_t k = list ? (int64_t)list[t] : t;
-    int i = pi[k], j = pj[k];
-    double err;
-    w[k] = pair_weight<double, true>(x[i] - gen[3 * j], y[i] - gen[3 * j + 1], z[i] - gen[3 * j + 2], h[i], radius[j],
-                               cfo[j], cfo[j + 1], fvo, plane, edge, err);
-}
-
-// FP64 recompute of the pairs the FP32 pass flagged; the count is read on
-// the device, so the launch needs no host synchronisation (grid-stride loop).
-// A list entry k >= 0 is recomputed with the FP64 complement form (faces
-// beyond 2h skipped; its rounding, about 1e-13, is far inside the mixed
-// mode's tolerance); an entry ~k (< 0) marks a particle in a face plane,
-// recomputed with the full form, for which such a face carries nothing.
-//
-// One warp per pair: the flagged pairs are few (under 1%) and come from
-// unrelated cells, so a thread per pair would leave most of the GPU idle and
-// its lanes walking different faces.  The lanes take the cell's faces (inside
-// test, skip test, K(D)), then the edges of the faces kept, each edge's
-// closed-form term (edge_full / edge_tilde, the same as pair_weight's) times
-// its orientation signs; a fixed-order warp sum adds them up.  A cell with
+// FP64 closed form, one warp per pair (both the FP64 mode and the recompute
+// of the pairs the mixed pass flagged).  The lanes take the cell's faces
+// (inside test, skip test, K(D)), then the edges of the faces kept, each
+// edge's closed-form term (edge_full / edge_tilde, the same as pair_weight's)
+// times its orientation signs; a fixed-order warp sum adds them up.  Against a
+// thread per pair this keeps the lanes on one pair's edges instead of walking
+// different cells' faces, and a short list still fills the GPU.  A cell with
 // more than FW_MAXF faces (possible only for imported cells) is done by one
 // lane with pair_weight.
+//
+// Entry t of list is k >= 0: pair k in the complement form (faces beyond 2h
+// skipped; its rounding, about 1e-13, is far inside the mixed mode's
+// tolerance), or ~k < 0: pair k in the full form (a particle in a face plane,
+// for which such a face carries nothing).  Without a list, entry t is pair t
+// in the full form (the FP64 mode).
 constexpr int FW_WARPS = 4;
 constexpr int FW_MAXF = 64;
 
-__global__ void __launch_bounds__(32 * FW_WARPS) k_map_fp64_flagged(
-    const int *__restrict__ nflag, const int32_t *__restrict__ pi, const int32_t *__restrict__ pj,
-    const double *__restrict__ x, const double *__restrict__ y, const double *__restrict__ z,
-    const double *__restrict__ h, const double *__restrict__ gen, const double *__restrict__ radius,
-    const int64_t *__restrict__ cfo, const int64_t *__restrict__ fvo, const PlaneD *__restrict__ plane,
-    const EdgeD *__restrict__ edge, const int32_t *__restrict__ list, double *__restrict__ w)
+__device__ __forceinline__ void fp64_pairs_warp(int64_t n, const int32_t *__restrict__ list,
+                                                const int32_t *__restrict__ pi, const int32_t *__restrict__ pj,
+                                                const double *__restrict__ x, const double *__restrict__ y,
+                                                const double *__restrict__ z, const double *__restrict__ h,
+                                                const double *__restrict__ gen, const double *__restrict__ radius,
+                                                const int64_t *__restrict__ cfo, const int64_t *__restrict__ fvo,
+                                                const PlaneD *__restrict__ plane, const EdgeD *__restrict__ edge,
+                                                double *__restrict__ w)
 {
     __shared__ double fD[FW_WARPS][FW_MAXF], fK[FW_WARPS][FW_MAXF];
     __shared__ int64_t fE0[FW_WARPS][FW_MAXF];
     __shared__ int fPre[FW_WARPS][FW_MAXF + 1];
     __shared__ float fSg[FW_WARPS][FW_MAXF];
-    const int wi = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int64_t n = *nflag;
-    for (int64_t t = blockIdx.x * (int64_t)FW_WARPS + wi; t < n; t += (int64_t)gridDim.x * FW_WARPS) {
-        const int32_t code = list[t];
+    const int wi = threadIdx.x >> 5, lane = threadIdx.x & 31, wpb = blockDim.x >> 5;   // wpb <= FW_WARPS
+    for (int64_t t = blockIdx.x * (int64_t)wpb + wi; t < n; t += (int64_t)gridDim.x * wpb) {
+        const int32_t code = list ? list[t] : ~(int32_t)t;
         const int64_t k = code >= 0 ? code : ~code;
         const int i = pi[k], j = pj[k];
         const double rx = x[i] - gen[3 * j], ry = y[i] - gen[3 * j + 1], rz = z[i] - gen[3 * j + 2];
@@ -508,6 +491,29 @@ __global__ void __launch_bounds__(32 * FW_WARPS) k_map_fp64_flagged(
         }
         __syncwarp();
     }
+}
+
+// the flagged pairs of the mixed pass; the count is read on the device, so
+// the launch needs no host synchronisation (grid-stride loop)
+__global__ void __launch_bounds__(32 * FW_WARPS) k_map_fp64_flagged(
+    const int *__restrict__ nflag, const int32_t *__restrict__ pi, const int32_t *__restrict__ pj,
+    const double *__restrict__ x, const double *__restrict__ y, const double *__restrict__ z,
+    const double *__restrict__ h, const double *__restrict__ gen, const double *__restrict__ radius,
+    const int64_t *__restrict__ cfo, const int64_t *__restrict__ fvo, const PlaneD *__restrict__ plane,
+    const EdgeD *__restrict__ edge, const int32_t *__restrict__ list, double *__restrict__ w)
+{
+    fp64_pairs_warp(*nflag, list, pi, pj, x, y, z, h, gen, radius, cfo, fvo, plane, edge, w);
+}
+
+// every pair, full form (the FP64 mode)
+__global__ void __launch_bounds__(32 * FW_WARPS) k_map_fp64(
+    int64_t npairs, const int32_t *__restrict__ pi, const int32_t *__restrict__ pj, const double *__restrict__ x,
+    const double *__restrict__ y, const double *__restrict__ z, const double *__restrict__ h,
+    const double *__restrict__ gen, const double *__restrict__ radius, const int64_t *__restrict__ cfo,
+    const int64_t *__restrict__ fvo, const PlaneD *__restrict__ plane, const EdgeD *__restrict__ edge,
+    double *__restrict__ w)
+{
+    fp64_pairs_warp(npairs, nullptr, pi, pj, x, y, z, h, gen, radius, cfo, fvo, plane, edge, w);
 }
 
 // FP32 bulk pass (quadrature form, see quad32.cuh).
@@ -949,10 +955,9 @@ EM_EXPORT int map_exact(em_ctx *ctx, const em_pairs *pr, const double *d_x, cons
     if (n) {
         if (ctx->timing) EM_CUDA(cudaEventRecord(ctx->ev[0], ctx->stream));
         if (p->precision == 0) {
-            k_map_fp64<<<em_grid(n, block), block, 0, ctx->stream>>>(n, pr->pair_i, pr->pair_j, d_x, d_y, d_z, d_h,
-                                                                     v->gen, v->radius, v->cell_face_off,
-                                                                     v->face_vert_off, v->plane, v->edge, nullptr,
-                                                                     d_w_out);
+            k_map_fp64<<<(int)std::min<int64_t>((n + block / 32 - 1) / (block / 32), 152 * 64), block, 0,
+                         ctx->stream>>>(n, pr->pair_i, pr->pair_j, d_x, d_y, d_z, d_h, v->gen, v->radius,
+                                        v->cell_face_off, v->face_vert_off, v->plane, v->edge, d_w_out);
             EM_LAUNCHED(ctx);
             if (ctx->timing) {
                 EM_CUDA(cudaEventRecord(ctx->ev[1], ctx->stream));
@@ -974,8 +979,8 @@ EM_EXPORT int map_exact(em_ctx *ctx, const em_pairs *pr, const double *d_x, cons
                 EM_CUDA(cudaEventRecord(ctx->ev[2], ctx->stream));
             }
             // FP64 recompute of the flagged pairs; the count stays on the device
-            const int fgrid = (int)std::min<int64_t>((n + FW_WARPS - 1) / FW_WARPS, 152 * 16);
-            k_map_fp64_flagged<<<fgrid, 32 * FW_WARPS, 0, ctx->stream>>>(nflag, pr->pair_i, pr->pair_j, d_x, d_y, d_z, d_h,
+            const int fgrid = (int)std::min<int64_t>((n + block / 32 - 1) / (block / 32), 152 * 64);
+            k_map_fp64_flagged<<<fgrid, block, 0, ctx->stream>>>(nflag, pr->pair_i, pr->pair_j, d_x, d_y, d_z, d_h,
                                                                  v->gen, v->radius, v->cell_face_off,
                                                                  v->face_vert_off, v->plane, v->edge, flagged,
                                                                  d_w_out);
@@ -1074,10 +1079,9 @@ EM_EXPORT int map_exact_noalloc(em_ctx *ctx, const em_pairs *pr, const double *d
     if (h_nfp64) *h_nfp64 = 0;
     if (n) {
         if (p->precision == 0) {
-            k_map_fp64<<<em_grid(n, block), block, 0, ctx->stream>>>(n, pr->pair_i, pr->pair_j, d_x, d_y, d_z, d_h,
-                                                                     v->gen, v->radius, v->cell_face_off,
-                                                                     v->face_vert_off, v->plane, v->edge, nullptr,
-                                                                     d_w_out);
+            k_map_fp64<<<(int)std::min<int64_t>((n + block / 32 - 1) / (block / 32), 152 * 64), block, 0,
+                         ctx->stream>>>(n, pr->pair_i, pr->pair_j, d_x, d_y, d_z, d_h, v->gen, v->radius,
+                                        v->cell_face_off, v->face_vert_off, v->plane, v->edge, d_w_out);
             EM_LAUNCHED(ctx);
         } else {
             int32_t *flagged;
@@ -1088,8 +1092,8 @@ EM_EXPORT int map_exact_noalloc(em_ctx *ctx, const em_pairs *pr, const double *d
                 n, pr->pair_i, pr->pair_j, d_x, d_y, d_z, d_h, v->gen, v->radius, v->cell_face_off,
                 v->face_vert_off, v->plane_f, v->plane_fl, v->edge_f, v->edge_fl, (float)p->fp64_threshold, d_w_out, flagged, nflag);
             EM_LAUNCHED(ctx);
-            const int fgrid = (int)std::min<int64_t>((n + FW_WARPS - 1) / FW_WARPS, 152 * 16);
-            k_map_fp64_flagged<<<fgrid, 32 * FW_WARPS, 0, ctx->stream>>>(nflag, pr->pair_i, pr->pair_j, d_x, d_y, d_z, d_h,
+            const int fgrid = (int)std::min<int64_t>((n + block / 32 - 1) / (block / 32), 152 * 64);
+            k_map_fp64_flagged<<<fgrid, block, 0, ctx->stream>>>(nflag, pr->pair_i, pr->pair_j, d_x, d_y, d_z, d_h,
                                                                  v->gen, v->radius, v->cell_face_off,
                                                                  v->face_vert_off, v->plane, v->edge, flagged,
                                                                  d_w_out);

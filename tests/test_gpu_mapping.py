@@ -53,13 +53,13 @@ def case(request, orc):
     return _case(orc, w)
 
 
-def run_gpu(ctx, c, precision=0, threshold=1e-6):
+def run_gpu(ctx, c, precision=0, threshold=1e-6, block_pairs=0):
     w = c["w"]
     vor = import_cells(ctx, c["cells"])
     pr = api.pairs_from_list(ctx, dev(c["pairs"].pair_i, torch.int32), dev(c["pairs"].pair_j, torch.int32),
                              w.n, vor)
     res = api.map_exact(ctx, pr, dev(w.x), dev(w.y), dev(w.z), dev(w.h), dev(w.m), vor,
-                        api.Params(precision=precision, fp64_threshold=threshold))
+                        api.Params(precision=precision, fp64_threshold=threshold, block_pairs=block_pairs))
     torch.cuda.synchronize()
     return vor, pr, res
 
@@ -82,6 +82,18 @@ def test_map_exact_deterministic(ctx, case, precision):
     _, _, (a, ra, ua, na) = run_gpu(ctx, case, precision, 1e-5)
     _, _, (b, rb, ub, nb) = run_gpu(ctx, case, precision, 1e-5)
     assert torch.equal(a, b) and torch.equal(ra, rb) and torch.equal(ua, ub) and na == nb
+
+
+@pytest.mark.parametrize("block_pairs", [32, 64, 96])
+def test_map_exact_fp64_block_shape(ctx, case, block_pairs):
+    """The FP64 kernels compute each pair with one warp whatever the block
+    size, so every launch shape gives the same bits."""
+    _, _, (a, ra, _, _) = run_gpu(ctx, case, 0)
+    _, _, (b, rb, _, _) = run_gpu(ctx, case, 0, block_pairs=block_pairs)
+    assert torch.equal(a, b) and torch.equal(ra, rb)
+    _, _, (c, _, _, nc) = run_gpu(ctx, case, 1, 1e-5)
+    _, _, (d, _, _, nd) = run_gpu(ctx, case, 1, 1e-5, block_pairs=block_pairs)
+    assert torch.equal(c, d) and nc == nd
 
 
 def test_map_exact_mixed(ctx, case):
