@@ -280,56 +280,65 @@ WORK = {
     "pseudo_1e6": dict(faces=15.64, faces_used=11.33, edges_used=60.65, subpieces=58.54),
     "sphere_1e5": dict(faces=15.23, faces_used=7.93, edges_used=43.36, subpieces=40.33),
 }
-# FP64 flops (FMA = 2) of the FP32 pass, counted in its source: per face the
-# inside test and the plane distance (13), per face within reach the
-# reference distance, D^2 - 1, 4 - D^2 and the face constants (45); the edge
-# geometry is float-float FP32 (about 130 FP32 flops per edge of those faces)
-FP64_FLOPS_FACE, FP64_FLOPS_USED_FACE, FP64_FLOPS_EDGE = 13, 45, 0
-FP32_FLOPS_EDGE = 130
-# FP32 flops per quadrature node (common part 15, piece-2 integrand 21), with
-# expm1, sqrt and about six reciprocals on the SFU besides
-FP32_FLOPS_NODE = 36
-# nominal GB300 rates: FP64 1.25 TFLOP/s (152 SMs x 2 DFMA/clk x 2 x 2.07 GHz);
-# FP32 152 SMs x 128 lanes x 2 x 2.07 GHz
-FP64_PEAK_TFLOPS = 1.25
+# Work of the FP32 pass per unit, counted in its source (FMA = 2 flops):
+#  - per quadrature node 42 FP32 flops (common part 22, the kernel piece's
+#    integrand about 20) and 5 SFU operations (expm1, the reciprocals of e,
+#    Q + R and cosh, and rsqrt for Q; piece 2 adds one more reciprocal);
+#  - per edge of a face within reach 150 FP32 flops of float-float geometry
+#    (two offset dot products, four products, four sums);
+#  - per face 60 (float-float plane distance and, for faces within reach,
+#    the face constants), and 18 per edge of a face within reach for the FP32
+#    distance to the polygon;
+#  - per 8-node sub-piece 14 for the float-float accumulation;
+#  - per pair about 30 FP64 flops (r = x - g, 1/h, the final sums).
+FP32_FLOPS_NODE, SFU_OPS_NODE = 42, 5
+FP32_FLOPS_EDGE, FP32_FLOPS_FACE, FP32_FLOPS_POLY_EDGE, FP32_FLOPS_SUBPIECE = 150, 60, 18, 14
+FP64_FLOPS_PAIR = 30
+# nominal GB300 rates: FP32 152 SMs x 128 lanes x 2 x 2.07 GHz; SFU 16 per
+# clock per SM; FP64 1.25 TFLOP/s (152 SMs x 2 DFMA/clk x 2 x 2.07 GHz)
 FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.07e9 / 1e12
+SFU_PEAK_TOPS = 152 * 16 * 2.07e9 / 1e12
+FP64_PEAK_TFLOPS = 1.25
 # DRAM traffic of one k_map_fp32 launch per pair (ncu, dram__bytes_read.sum +
 # dram__bytes_write.sum over the pairs of the launch), per workload
-TRAFFIC_PER_PAIR = {"pseudo_1e6": 109.2, "sphere_1e5": 64.3}
+TRAFFIC_PER_PAIR = {"pseudo_1e6": 108.9, "sphere_1e5": 63.7}
 
 
 def roofline(npairs, ms, precision, workload):
     """Dominant kernel of map_exact.  Mixed mode: the FP32 pass k_map_fp32,
-    whose busiest pipe is FP64 (per-face geometry and face constants; ncu:
-    FP64 pipe ~70% busy, FMA ~33%, issue ~67%), so the roofline is the FP64
-    rate with the FP64 flops counted above; the FP32 work's rate is reported
-    beside it.  FP64 mode: the closed
-    form k_map_fp64, with the same geometry count over all faces and edges
-    (its transcendental calls are not counted)."""
+    which is bound by instruction issue on FP32 and integer work (ncu: issue
+    slots ~80% used, no pipe saturated), so its roofline is the FP32 rate with
+    the FP32 flops counted above; the SFU and FP64 rates are reported beside
+    it.  FP64 mode: the closed form k_map_fp64 against the FP64 rate, with the
+    same geometry count over all faces and edges (its transcendental calls are
+    not counted)."""
     wk = WORK[workload]
-    if precision == "mixed":
-        f64 = (FP64_FLOPS_FACE * wk["faces"] + FP64_FLOPS_USED_FACE * wk["faces_used"]
-               + FP64_FLOPS_EDGE * wk["edges_used"])
-        f32 = FP32_FLOPS_NODE * 8 * wk["subpieces"] + FP32_FLOPS_EDGE * wk["edges_used"]
-    else:
-        # the closed form: per face the plane distance, per edge of every face
-        # the FP64 geometry (22 flops; transcendental calls not counted)
-        edges_all = wk["edges_used"] * wk["faces"] / wk["faces_used"]
-        f64 = 13 * wk["faces"] + 22 * edges_all
-        f32 = 0.0
     t = ms * 1e-3
+    if precision == "mixed":
+        nodes = 8 * wk["subpieces"]
+        f32 = (FP32_FLOPS_NODE * nodes + FP32_FLOPS_SUBPIECE * wk["subpieces"]
+               + (FP32_FLOPS_EDGE + FP32_FLOPS_POLY_EDGE) * wk["edges_used"] + FP32_FLOPS_FACE * wk["faces"])
+        achieved = npairs * f32 / t / 1e12
+        tr = TRAFFIC_PER_PAIR.get(workload)
+        sfu = npairs * SFU_OPS_NODE * nodes / t / 1e12
+        f64 = npairs * FP64_FLOPS_PAIR / t / 1e12
+        return {"bound": "alu", "achieved": achieved, "peak": FP32_PEAK_TFLOPS, "unit": "TFLOP/s",
+                "frac": achieved / FP32_PEAK_TFLOPS, "traffic": tr * npairs if tr else None,
+                "kernel": "k_map_fp32", "pipe": "fp32", "flops_per_pair": f32, "kernel_ms": ms,
+                "peak_source": "nominal GB300 FP32 rate (152 SMs x 128 lanes x 2 flop x 2.07 GHz)",
+                "sfu": {"achieved": sfu, "peak": SFU_PEAK_TOPS, "unit": "Top/s", "frac": sfu / SFU_PEAK_TOPS,
+                        "ops_per_pair": SFU_OPS_NODE * nodes},
+                "fp64": {"achieved": f64, "peak": FP64_PEAK_TFLOPS, "frac": f64 / FP64_PEAK_TFLOPS,
+                         "flops_per_pair": FP64_FLOPS_PAIR}}
+    # the closed form: per face the plane distance, per edge of every face
+    # the FP64 geometry (22 flops; transcendental calls not counted)
+    edges_all = wk["edges_used"] * wk["faces"] / wk["faces_used"]
+    f64 = 13 * wk["faces"] + 22 * edges_all
     achieved = npairs * f64 / t / 1e12
-    tr = TRAFFIC_PER_PAIR.get(workload) if precision == "mixed" else None
-    out = {"bound": "alu", "achieved": achieved, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
-           "frac": achieved / FP64_PEAK_TFLOPS, "traffic": tr * npairs if tr else None,
-           "kernel": "k_map_fp32" if precision == "mixed" else "k_map_fp64", "pipe": "fp64",
-           "flops_per_pair": f64, "kernel_ms": ms,
-           "peak_source": "nominal GB300 FP64 rate (152 SMs x 2 DFMA/clk x 2 flop x 2.07 GHz)"}
-    if f32:
-        a32 = npairs * f32 / t / 1e12
-        out["fp32_quadrature"] = {"achieved": a32, "peak": FP32_PEAK_TFLOPS, "frac": a32 / FP32_PEAK_TFLOPS,
-                                  "flops_per_pair": f32}
-    return out
+    return {"bound": "alu", "achieved": achieved, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
+            "frac": achieved / FP64_PEAK_TFLOPS, "traffic": None, "kernel": "k_map_fp64", "pipe": "fp64",
+            "flops_per_pair": f64, "kernel_ms": ms,
+            "peak_source": "nominal GB300 FP64 rate (152 SMs x 2 DFMA/clk x 2 flop x 2.07 GHz)"}
 
 
 def run_e2e(args, w, step, device):
