@@ -24,11 +24,11 @@ struct WCell {
     double pl[WMAXP][4];
     double v[2][WMAXV][3];
     float vf[2][WMAXV][4];   // the vertices rounded to FP32 (same buffers as v), w = |x| + |y| + |z|
-    double f[WMAXV];
+    uint8_t side[WMAXV];     // clip in progress: 1 if the vertex lies beyond the plane
     float cd2[WCAND];        // sort keys of the candidates: squared distances rounded to FP32
     int cid[WCAND];
     int pid[WMAXP];
-    int out_list[WMAXV];
+    uint8_t out_list[WMAXV];   // clip in progress: the removed vertices
     uint8_t tri[2][WMAXV][4];
     int np, nt, cur, ncand, err;
 };
@@ -131,11 +131,19 @@ __device__ int wclip(WCell &c, double nx, double ny, double nz, double d, int id
         }
         if (!__any_sync(0xffffffffu, maybe)) return 0;
     }
+    // the side of each vertex: from its FP32 value where that clears the band
+    // (then the FP64 value has the same sign), else from the FP64 value
+    const float nxf = (float)nx, nyf = (float)ny, nzf = (float)nz, df = (float)d;
+    const float nmax = fmaxf(fmaxf(fabsf(nxf), fabsf(nyf)), fabsf(nzf));
+    auto fval = [&](int t) { return nx * c.v[cur][t][0] + ny * c.v[cur][t][1] + nz * c.v[cur][t][2] - d; };
     bool any = false;
     for (int t = lane; t < nt; t += 32) {
-        double f = nx * c.v[cur][t][0] + ny * c.v[cur][t][1] + nz * c.v[cur][t][2] - d;
-        c.f[t] = f;
-        any = any || f > 0.0;
+        const float *vf = c.vf[cur][t];
+        const float ff = nxf * vf[0] + nyf * vf[1] + nzf * vf[2] - df;
+        const float band = 1e-5f * (nmax * vf[3] + fabsf(df));
+        const bool out = ff > band ? true : (ff < -band ? false : fval(t) > 0.0);
+        c.side[t] = out ? 1 : 0;
+        any = any || out;
     }
     if (!__any_sync(0xffffffffu, any)) return 0;
     __syncwarp();
@@ -146,7 +154,7 @@ __device__ int wclip(WCell &c, double nx, double ny, double nz, double d, int id
     for (int base = 0; base < nt; base += 32) {
         int t = base + lane;
         bool in = t < nt;
-        bool keep = in && !(c.f[t] > 0.0);
+        bool keep = in && !c.side[t];
         bool out = in && !keep;
         unsigned mk = __ballot_sync(0xffffffffu, keep), mo = __ballot_sync(0xffffffffu, out);
         if (keep) {
@@ -155,7 +163,7 @@ __device__ int wclip(WCell &c, double nx, double ny, double nz, double d, int id
             for (int e = 0; e < 3; ++e) c.v[nxt][pos][e] = c.v[cur][t][e];
             for (int e = 0; e < 4; ++e) c.vf[nxt][pos][e] = c.vf[cur][t][e];
         }
-        if (out) c.out_list[nout + __popc(mo & lanemask_lt())] = t;
+        if (out) c.out_list[nout + __popc(mo & lanemask_lt())] = (uint8_t)t;
         nk += __popc(mk);
         nout += __popc(mo);
     }
@@ -181,9 +189,10 @@ __device__ int wclip(WCell &c, double nx, double ny, double nz, double d, int id
                 }
             if (u < 0) {
                 bad = true;
-            } else if (!(c.f[u] > 0.0)) {
+            } else if (!c.side[u]) {
                 newv = true;
-                double fu = c.f[u], ft = c.f[t];
+                // the edge's end values in FP64 (fu <= 0 < ft, as their sides say)
+                const double fu = fval(u), ft = fval(t);
                 double s = fu / (fu - ft);
                 px = c.v[cur][u][0] + s * (c.v[cur][t][0] - c.v[cur][u][0]);
                 py = c.v[cur][u][1] + s * (c.v[cur][t][1] - c.v[cur][u][1]);
