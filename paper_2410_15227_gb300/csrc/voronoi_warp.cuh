@@ -23,13 +23,18 @@ constexpr int WCAND = 256;   // candidate list (power of two for the bitonic sor
 struct WCell {
     double pl[WMAXP][4];
     double v[2][WMAXV][3];
-    float vf[2][WMAXV][4];   // the vertices rounded to FP32 (same buffers as v), w = |x| + |y| + |z|
-    uint8_t side[WMAXV];     // clip in progress: 1 if the vertex lies beyond the plane
+    float vf[WMAXV][4];      // the current vertices rounded to FP32, w = |x| + |y| + |z|
+    // clip in progress: 1 if the vertex lies beyond the plane, then its new
+    // index (0xff if removed)
+    uint8_t side[WMAXV];
     float cd2[WCAND];        // sort keys of the candidates: squared distances rounded to FP32
     int cid[WCAND];
     int pid[WMAXP];
     uint8_t out_list[WMAXV];   // clip in progress: the removed vertices
     uint8_t tri[2][WMAXV][4];
+    // adj[t][e]: the vertex across edge e of vertex t, i.e. the one whose
+    // triangle holds the reversed edge (tri[t][e + 1], tri[t][e])
+    uint8_t adj[2][WMAXV][4];
     int np, nt, cur, ncand, err;
 };
 
@@ -79,8 +84,14 @@ __device__ void wcell_box(WCell &c, const double *box, double gx, double gy, dou
             c.v[0][i][0] = sx ? hi[0] : lo[0];
             c.v[0][i][1] = sy ? hi[1] : lo[1];
             c.v[0][i][2] = sz ? hi[2] : lo[2];
-            set_vf(c.vf[0][i], c.v[0][i][0], c.v[0][i][1], c.v[0][i][2]);
+            set_vf(c.vf[i], c.v[0][i][0], c.v[0][i][1], c.v[0][i][2]);
         }
+        for (int i = 0; i < 8; ++i)
+            for (int e = 0; e < 3; ++e) {
+                const uint8_t a = c.tri[0][i][e], b = c.tri[0][i][(e + 1) % 3];
+                for (int s = 0; s < 8; ++s)
+                    if (has_edge(c.tri[0][s], b, a)) c.adj[0][i][e] = (uint8_t)s;
+            }
     }
     __syncwarp();
 }
@@ -125,7 +136,7 @@ __device__ int wclip(WCell &c, double nx, double ny, double nz, double d, int id
         const float nmax = fmaxf(fmaxf(fabsf(nxf), fabsf(nyf)), fabsf(nzf));
         bool maybe = false;
         for (int t = lane; t < nt; t += 32) {
-            const float *vf = c.vf[cur][t];
+            const float *vf = c.vf[t];
             const float ff = nxf * vf[0] + nyf * vf[1] + nzf * vf[2] - df;
             maybe = maybe || ff > -1e-5f * (nmax * vf[3] + fabsf(df));
         }
@@ -138,7 +149,7 @@ __device__ int wclip(WCell &c, double nx, double ny, double nz, double d, int id
     auto fval = [&](int t) { return nx * c.v[cur][t][0] + ny * c.v[cur][t][1] + nz * c.v[cur][t][2] - d; };
     bool any = false;
     for (int t = lane; t < nt; t += 32) {
-        const float *vf = c.vf[cur][t];
+        const float *vf = c.vf[t];
         const float ff = nxf * vf[0] + nyf * vf[1] + nzf * vf[2] - df;
         const float band = 1e-5f * (nmax * vf[3] + fabsf(df));
         const bool out = ff > band ? true : (ff < -band ? false : fval(t) > 0.0);
@@ -149,48 +160,66 @@ __device__ int wclip(WCell &c, double nx, double ny, double nz, double d, int id
     __syncwarp();
     if (c.np >= WMAXP && wcompact(c) >= WMAXP) return -emv::VS_CAPACITY;
     const int q = c.np;
-    // kept vertices, in order, into the other buffer; removed ones listed
+    // new index of every kept vertex (order kept), in side[]; removed ones listed
     int nk = 0, nout = 0;
     for (int base = 0; base < nt; base += 32) {
-        int t = base + lane;
-        bool in = t < nt;
-        bool keep = in && !c.side[t];
-        bool out = in && !keep;
-        unsigned mk = __ballot_sync(0xffffffffu, keep), mo = __ballot_sync(0xffffffffu, out);
-        if (keep) {
-            int pos = nk + __popc(mk & lanemask_lt());
-            for (int e = 0; e < 3; ++e) c.tri[nxt][pos][e] = c.tri[cur][t][e];
-            for (int e = 0; e < 3; ++e) c.v[nxt][pos][e] = c.v[cur][t][e];
-            for (int e = 0; e < 4; ++e) c.vf[nxt][pos][e] = c.vf[cur][t][e];
-        }
+        const int t = base + lane;
+        const bool in = t < nt;
+        const bool keep = in && !c.side[t];
+        const bool out = in && !keep;
+        const unsigned mk = __ballot_sync(0xffffffffu, keep), mo = __ballot_sync(0xffffffffu, out);
+        if (in) c.side[t] = keep ? (uint8_t)(nk + __popc(mk & lanemask_lt())) : (uint8_t)0xff;
         if (out) c.out_list[nout + __popc(mo & lanemask_lt())] = (uint8_t)t;
         nk += __popc(mk);
         nout += __popc(mo);
     }
     __syncwarp();
     if (nk == 0) return -emv::VS_TOPOLOGY;
-    // one task per (removed vertex, edge): a new vertex where the kept neighbour lies
+    // kept vertices into the other buffer, their neighbours renumbered (those
+    // across a cut edge are set below); the FP32 copy moves within its buffer
+    // (a vertex never moves up, and each round reads before it writes)
+    for (int base = 0; base < nt; base += 32) {
+        const int t = base + lane;
+        const int pos = t < nt ? c.side[t] : 0xff;
+        float vfk[4];
+        if (pos != 0xff) {
+            for (int e = 0; e < 3; ++e) {
+                c.tri[nxt][pos][e] = c.tri[cur][t][e];
+                const int s_ = c.adj[cur][t][e];
+                c.adj[nxt][pos][e] = s_ < nt ? c.side[s_] : (uint8_t)0xff;
+                c.v[nxt][pos][e] = c.v[cur][t][e];
+            }
+            for (int e = 0; e < 4; ++e) vfk[e] = c.vf[t][e];
+        }
+        __syncwarp();
+        if (pos != 0xff)
+            for (int e = 0; e < 4; ++e) c.vf[pos][e] = vfk[e];
+        __syncwarp();
+    }
+    // one task per (removed vertex, edge): a new vertex where the neighbour
+    // across the edge is kept, with the two linked to each other
     int nn = nk;
     bool bad = false;
     for (int base = 0; base < 3 * nout; base += 32) {
-        int k = base + lane;
+        const int k = base + lane;
         bool newv = false;
         uint8_t a = 0, b = 0;
+        int upos = 0, ue = 0;
         double px = 0, py = 0, pz = 0;
         if (k < 3 * nout) {
-            int t = c.out_list[k / 3], e = k % 3;
+            const int t = c.out_list[k / 3], e = k % 3;
             a = c.tri[cur][t][e];
             b = c.tri[cur][t][(e + 1) % 3];
-            int u = -1;
-            for (int s = 0; s < nt; ++s)
-                if (has_edge(c.tri[cur][s], b, a)) {
-                    u = s;
-                    break;
-                }
-            if (u < 0) {
-                bad = true;
-            } else if (!c.side[u]) {
+            const int u = c.adj[cur][t][e];
+            if (u >= nt) {
+                bad = true;   // inconsistent neighbours: reported, never followed
+            } else if (c.side[u] != 0xff) {
                 newv = true;
+                upos = c.side[u];
+                // the edge of u that is (b, a)
+                const uint8_t *tu = c.tri[cur][u];
+                ue = (tu[0] == b && tu[1] == a) ? 0 : ((tu[1] == b && tu[2] == a) ? 1 : 2);
+                bad = bad || !(tu[ue] == b && tu[(ue + 1) % 3] == a);
                 // the edge's end values in FP64 (fu <= 0 < ft, as their sides say)
                 const double fu = fval(u), ft = fval(t);
                 double s = fu / (fu - ft);
@@ -206,14 +235,31 @@ __device__ int wclip(WCell &c, double nx, double ny, double nz, double d, int id
                 c.tri[nxt][pos][0] = a;
                 c.tri[nxt][pos][1] = b;
                 c.tri[nxt][pos][2] = (uint8_t)q;
+                c.adj[nxt][pos][0] = (uint8_t)upos;
+                c.adj[nxt][upos][ue] = (uint8_t)pos;
                 c.v[nxt][pos][0] = px;
                 c.v[nxt][pos][1] = py;
                 c.v[nxt][pos][2] = pz;
-                set_vf(c.vf[nxt][pos], px, py, pz);
+                set_vf(c.vf[pos], px, py, pz);
             }
         }
         nn += __popc(m);
     }
+    __syncwarp();
+    // the new vertices around the new face q: (a, b, q) meets the one whose
+    // a is this b across (b, q), and the one whose b is this a across (q, a)
+    if (nn <= WMAXV)
+        for (int n = nk + lane; n < nn; n += 32) {
+            const uint8_t an = c.tri[nxt][n][0], bn = c.tri[nxt][n][1];
+            int m1 = -1, m2 = -1;
+            for (int o = nk; o < nn; ++o) {
+                if (c.tri[nxt][o][0] == bn) m1 = o;
+                if (c.tri[nxt][o][1] == an) m2 = o;
+            }
+            bad = bad || m1 < 0 || m2 < 0;
+            c.adj[nxt][n][1] = (uint8_t)(m1 < 0 ? 0 : m1);
+            c.adj[nxt][n][2] = (uint8_t)(m2 < 0 ? 0 : m2);
+        }
     if (__any_sync(0xffffffffu, bad)) return -emv::VS_TOPOLOGY;
     if (nn > WMAXV) return -emv::VS_CAPACITY;
     if (lane == 0) {
@@ -358,13 +404,13 @@ __device__ int gather_cutting(WCell &c, const em::ChunkTree &T, const double *__
         }
         // some vertex nearer to the box than to the site
         for (int t = 0; t < nt; ++t) {
-            const float vx = c.vf[cur][t][0], vy = c.vf[cur][t][1], vz = c.vf[cur][t][2];
+            const float vx = c.vf[t][0], vy = c.vf[t][1], vz = c.vf[t][2];
             float dx = fmaxf(fmaxf(lx - vx, vx - hx), 0.f);
             float dy = fmaxf(fmaxf(ly - vy, vy - hy), 0.f);
             float dz = fmaxf(fmaxf(lz - vz, vz - hz), 0.f);
             const float db = dx * dx + dy * dy + dz * dz;
             const float dg = vx * vx + vy * vy + vz * vz;
-            const float S = gabs + babs + c.vf[cur][t][3];
+            const float S = gabs + babs + c.vf[t][3];
             if (db < dg + 1e-5f * S * S) return true;
         }
         return false;
@@ -403,7 +449,7 @@ __device__ int gather_cutting(WCell &c, const em::ChunkTree &T, const double *__
                     const float df = 0.5f * rf * rf, rabs = fabsf(ex) + fabsf(ey) + fabsf(ez);
                     bool maybe = false;
                     for (int t = 0; t < nt && !maybe; ++t) {
-                        const float *vf = c.vf[cur][t];
+                        const float *vf = c.vf[t];
                         const float ff = ex * vf[0] + ey * vf[1] + ez * vf[2] - df;
                         maybe = ff > -1e-5f * (gabs + rabs + vf[3]) * (vf[3] + rabs);
                     }
@@ -474,10 +520,9 @@ __device__ int clip_sorted(WCell &c, const em::ChunkTree &T, const double *__res
             const float4 pk = T.pts[k];
             const float ex = pk.x - gxf, ey = pk.y - gyf, ez = pk.z - gzf;
             const float df = 0.5f * (ex * ex + ey * ey + ez * ez), rabs = fabsf(ex) + fabsf(ey) + fabsf(ez);
-            const int cur = c.cur;
             bool maybe = false;
             for (int t = lane; t < c.nt; t += 32) {
-                const float *vf = c.vf[cur][t];
+                const float *vf = c.vf[t];
                 const float ff = ex * vf[0] + ey * vf[1] + ez * vf[2] - df;
                 maybe = maybe || ff > -1e-5f * (gabs + rabs + vf[3]) * (vf[3] + rabs);
             }
@@ -590,6 +635,8 @@ __device__ int wbuild_cell(WCell &c, const em::ChunkTree &T, const double *__res
 
 // Face loop of plane q (one lane): vertex indices counter-clockwise seen from
 // outside; returns the length (0 if the plane holds no vertex, -1 on error).
+// From a vertex t holding q at position r, the next vertex around q is the
+// one across t's edge (tri[t][r + 2], q).
 __device__ int wface_loop(const WCell &c, int q, uint8_t *loop, int maxn)
 {
     const int cur = c.cur, nt = c.nt;
@@ -602,15 +649,9 @@ __device__ int wface_loop(const WCell &c, int q, uint8_t *loop, int maxn)
         if (n >= maxn) return -1;
         loop[n++] = (uint8_t)t;
         const uint8_t *tr = c.tri[cur][t];
-        int r = tr[0] == q ? 0 : (tr[1] == q ? 1 : 2);
-        uint8_t y = tr[(r + 2) % 3];
-        int nx = -1;
-        for (int s = 0; s < nt; ++s)
-            if (has_edge(c.tri[cur][s], (uint8_t)q, y)) {
-                nx = s;
-                break;
-            }
-        if (nx < 0) return -1;
+        const int r = tr[0] == q ? 0 : (tr[1] == q ? 1 : 2);
+        const int nx = c.adj[cur][t][(r + 2) % 3];
+        if (nx >= nt) return -1;
         t = nx;
     } while (t != t0);
     return n;
