@@ -121,6 +121,7 @@ __global__ void __launch_bounds__(32 * PAIRS_WARPS)
 {
     __shared__ uint64_t buf_key[PAIRS_WARPS][PAIRS_BUF];
     __shared__ int32_t buf_near[PAIRS_WARPS][PAIRS_BUF];
+    __shared__ int32_t cand_buf[PAIRS_WARPS][64];   // a chunk adds at most 32 to fewer than 32
     const int w = threadIdx.x >> 5;
     int64_t j = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
     if (j >= ncell) return;   // the whole warp
@@ -147,19 +148,11 @@ __global__ void __launch_bounds__(32 * PAIRS_WARPS)
     const float Rf = (float)Rj;
     const float gxf = (float)gx, gyf = (float)gy, gzf = (float)gz;
     const float gscale = fabsf(gxf) + fabsf(gyf) + fabsf(gzf);
-    em::warp_traverse(T, (float)gx, (float)gy, (float)gz, R * R, INT64_MAX, [&](int64_t k, bool valid) {
+    // the exact classification of one candidate (lanes with act); hits go to
+    // the warp's output buffer
+    auto classify = [&](int64_t k, bool act) {
         bool hit = false, nearb = false;
-        // candidates beyond R_j + 2h by the band (which here also covers the
-        // FP32 rounding of the coordinates themselves) are dropped before any FP64
-        bool cand = valid;
-        if (cand) {
-            const float4 pk = T.pts[k];
-            const float ex = pk.x - gxf, ey = pk.y - gyf, ez = pk.z - gzf;
-            const float d = sqrtf(ex * ex + ey * ey + ez * ez);
-            const float h2f = 2.f * (float)hs[k];
-            cand = d < Rf + h2f + 1e-5f * (gscale + Rf + d + h2f);
-        }
-        if (cand) {
+        if (act) {
             const double rx = xs[k] - gx, ry = ys[k] - gy, rz = zs[k] - gz;
             const double h2 = 2.0 * hs[k];
             const float rxf = (float)rx, ryf = (float)ry, rzf = (float)rz, h2f = (float)h2;
@@ -187,7 +180,36 @@ __global__ void __launch_bounds__(32 * PAIRS_WARPS)
         }
         __syncwarp();
         nb += __popc(b);
+    };
+    // candidates within R_j + 2h (+ the band, which here also covers the FP32
+    // rounding of the coordinates) collect in a per-warp buffer and are
+    // classified 32 at a time, so that the per-candidate work runs with every
+    // lane busy instead of on the lanes of each 32-point chunk that passed
+    int nc = 0;
+    int32_t *cb = cand_buf[w];
+    em::warp_traverse(T, (float)gx, (float)gy, (float)gz, R * R, INT64_MAX, [&](int64_t k, bool valid) {
+        bool cand = false;
+        if (valid) {
+            const float4 pk = T.pts[k];
+            const float ex = pk.x - gxf, ey = pk.y - gyf, ez = pk.z - gzf;
+            const float d = sqrtf(ex * ex + ey * ey + ez * ez);
+            const float h2f = 2.f * (float)hs[k];
+            cand = d < Rf + h2f + 1e-5f * (gscale + Rf + d + h2f);
+        }
+        const unsigned cm = __ballot_sync(0xffffffffu, cand);
+        if (cand) cb[nc + __popc(cm & ((1u << lane) - 1u))] = (int32_t)k;
+        __syncwarp();
+        nc += __popc(cm);
+        if (nc >= 32) {
+            classify(cb[lane], true);
+            const int32_t rest = lane + 32 < nc ? cb[lane + 32] : 0;
+            __syncwarp();
+            if (lane + 32 < nc) cb[lane] = rest;
+            __syncwarp();
+            nc -= 32;
+        }
     });
+    if (nc > 0) classify(lane < nc ? cb[lane] : 0, lane < nc);
     if (nb > 0) write_out();
 }
 
