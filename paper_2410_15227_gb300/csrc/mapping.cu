@@ -546,6 +546,9 @@ namespace {
 #ifndef EM_MQ_WARPS
 #define EM_MQ_WARPS 2
 #endif
+#ifndef EM_GL4_MAXLEN
+#define EM_GL4_MAXLEN 0.125   // longest segment (in s) integrated with 4 points
+#endif
 #ifndef EM_MQ_MINB
 #define EM_MQ_MINB 0   // minimum resident blocks per SM asked of the compiler (0: none)
 #endif
@@ -560,17 +563,18 @@ struct SegQueue {
     float sa[MQ_SLOTS][32], hl[MQ_SLOTS][32], A[MQ_SLOTS][32], B2[MQ_SLOTS][32], c4[MQ_SLOTS][32];
     float dd[MQ_SLOTS][32], Rr[MQ_SLOTS][32], vv[MQ_SLOTS][32], add[MQ_SLOTS][32], scale[MQ_SLOTS][32];
     int meta[MQ_SLOTS][32];
-    int first[MQ_SLOTS][32];            // index of a slot's first sub-piece among its lane's (INT_MAX if empty)
-    float vhi[MQ_CHUNK], vlo[MQ_CHUNK];   // scale * integral of each evaluated sub-piece (float-float)
+    int first[MQ_SLOTS][32];            // index of a segment's first 4-node slot among its lane's (INT_MAX if empty)
+    float vhi[MQ_CHUNK], vlo[MQ_CHUNK];   // scale * integral of each evaluated slot (float-float)
     int pre[33];
 };
 
 // Evaluate every queued segment of the warp and add each lane's results to
 // its pair.  Called with the warp converged.  The work is spread by
-// sub-piece (8 quadrature nodes): lane L's segments hold M_L sub-pieces in
-// slot order, the warp numbers all of them L by L and evaluates them 32 at a
-// time, whoever owns them, so that a segment cut into many sub-pieces does
-// not hold up the lanes.  Each result, times its segment's signed factor, is
+// slot (4 quadrature nodes: a 4-point segment, or half of an 8-point
+// sub-piece): lane L's segments hold M_L slots in queue order, the warp
+// numbers all of them L by L and evaluates them 32 at a time, whoever owns
+// them, so that a segment cut into many sub-pieces does not hold up the
+// lanes.  Each result, times its segment's signed factor, is
 // kept exactly as a float-float product; the owner then adds its own results
 // in order into its float-float sum (to about 2^-44 of the magnitudes), which
 // keeps the sum bit-reproducible, and their magnitudes in FP32: they only
@@ -581,7 +585,10 @@ __device__ __forceinline__ void mq_flush(SegQueue &q, int lane, int cnt, emq::ff
 #pragma unroll
     for (int sl = 0; sl < MQ_SLOTS; ++sl) {
         q.first[sl][lane] = sl < cnt ? M : INT_MAX;
-        if (sl < cnt) M += q.meta[sl][lane] & 255;
+        if (sl < cnt) {
+            const int mt = q.meta[sl][lane];
+            M += (mt & emq::SEG_GL4) ? (mt & 255) : 2 * (mt & 255);   // 4-point: 1 slot, 8-point: 2 per sub-piece
+        }
     }
     int x = M;
 #pragma unroll
@@ -593,7 +600,7 @@ __device__ __forceinline__ void mq_flush(SegQueue &q, int lane, int cnt, emq::ff
     q.pre[lane + 1] = x;
     if (lane == 0) q.pre[0] = 0;
     __syncwarp();
-    const int mine0 = x - M;   // this lane's sub-pieces are [mine0, x)
+    const int mine0 = x - M;   // this lane's slots are [mine0, x)
     for (int c0 = 0; c0 < total; c0 += MQ_CHUNK) {
         const int c1 = min(total, c0 + MQ_CHUNK);
         for (int t = c0 + lane; t < c1; t += 32) {
@@ -608,11 +615,15 @@ __device__ __forceinline__ void mq_flush(SegQueue &q, int lane, int cnt, emq::ff
             int sl = 0;
 #pragma unroll
             for (int k = 1; k < MQ_SLOTS; ++k) sl += q.first[k][lo] <= r ? 1 : 0;
-            const int p = r - q.first[sl][lo];
+            const int rr = r - q.first[sl][lo];
+            const int mt = q.meta[sl][lo];
+            const bool gl4 = (mt & emq::SEG_GL4) != 0;
+            const int p = gl4 ? rr : rr >> 1;           // the sub-piece
+            const int half = gl4 ? 2 : (rr & 1);        // which 4 nodes of its rule
             const float hl = q.hl[sl][lo];
-            const float val = emq::sub_eval(fmaf(2.f * (float)p + 1.f, hl, q.sa[sl][lo]), hl, q.A[sl][lo],
-                                            q.B2[sl][lo], q.c4[sl][lo], q.dd[sl][lo], q.Rr[sl][lo], q.vv[sl][lo],
-                                            q.add[sl][lo], q.meta[sl][lo]);
+            const float val = emq::slot_eval(fmaf(2.f * (float)p + 1.f, hl, q.sa[sl][lo]), hl, half, q.A[sl][lo],
+                                             q.B2[sl][lo], q.c4[sl][lo], q.dd[sl][lo], q.Rr[sl][lo], q.vv[sl][lo],
+                                             q.add[sl][lo], mt);
             const emq::ff v = emq::ff_two_prod(q.scale[sl][lo], val);
             q.vhi[t - c0] = v.hi;
             q.vlo[t - c0] = v.lo;
@@ -698,6 +709,8 @@ __device__ __forceinline__ void mq_push_g(SegQueue &q, int lane, int &cnt, float
     const int tflag = tilde ? emq::SEG_TILDE : 0;
     auto push = [&](int piece, float s0, float s1) {
         const float len = s1 - s0;
+        // 4 points for a short segment, else 8 on sub-pieces of length <= 2
+        const bool gl4 = len <= (float)EM_GL4_MAXLEN;
         const int m = len > 2.f ? (int)ceilf(0.5f * len) : 1;   // <= 36: A >= 1e-30, |tau| <= 2
         const int sl = cnt++;
         q.sa[sl][lane] = s0;
@@ -711,7 +724,7 @@ __device__ __forceinline__ void mq_push_g(SegQueue &q, int lane, int &cnt, float
         q.vv[sl][lane] = ref1 ? 1.f : fs.v;
         q.add[sl][lane] = ref1 ? fs.C1 : 0.f;
         q.scale[sl][lane] = sc;
-        q.meta[sl][lane] = m | (piece == 1 ? emq::SEG_PIECE1 : 0) | tflag;
+        q.meta[sl][lane] = m | (piece == 1 ? emq::SEG_PIECE1 : 0) | tflag | (gl4 ? emq::SEG_GL4 : 0);
     };
     // piece 1 is |tau| in [ua, b1], piece 2 in [a2, b2]; when both are present
     // they meet at t1, whose s is computed once

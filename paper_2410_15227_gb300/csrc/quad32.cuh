@@ -14,8 +14,9 @@
 // Substituting tau = A sinh(s) turns A dtau/(A^2 + tau^2) into ds/cosh(s):
 //     (D/pi) int [K~(Q(s)) - K~(R)] / cosh(s) ds,  Q(s)^2 = D^2 + A^2 cosh^2 s,
 // an integrand that is smooth on the scale of s = 1 however small A is; it is
-// integrated by 8-point Gauss-Legendre on sub-pieces of length <= 2 in s,
-// split at the kernel's breakpoints Q = 1 and Q = 2.  Beyond Q = 2, K~(Q) = 0
+// integrated by Gauss-Legendre on sub-pieces of length <= 2 in s (8 points;
+// 4 for a segment of length <= 1/8, see SEG_GL4), split at the kernel's
+// breakpoints Q = 1 and Q = 2.  Beyond Q = 2, K~(Q) = 0
 // and the piece is -K~(R) times an angle, taken analytically.
 //
 // Every piece of the integrand K(Q) - K(R) is formed as an exact factored
@@ -42,10 +43,9 @@
 // particle inside a cell that lies entirely within 2h of it.
 //
 // Work is organised in segments: one segment is one kernel piece of one edge
-// (an s-interval cut into m sub-pieces of 8 nodes each) with everything its
-// integrand needs.  A warp evaluates the sub-pieces of the segments of 32
-// different pairs side by side, one sub-piece per lane, with one copy of the
-// node loop.
+// (an s-interval cut into m sub-pieces) with everything its integrand needs.
+// A warp evaluates the segments of 32 different pairs side by side in slots
+// of 4 nodes, one slot per lane, with one copy of the node loop.
 #pragma once
 
 #include <cuda_runtime.h>
@@ -58,13 +58,16 @@ namespace emq {
 
 constexpr int kNodeUnroll = EM_NODE_UNROLL;
 
-// 8-point Gauss-Legendre rule on [-1, 1]: the positive abscissae and their
-// weights (the rule is symmetric); in constant memory, read with an index that
-// is the same on every lane
-static __constant__ float c_gl_x[4] = {0.18343464249564978f, 0.52553240991632899f, 0.79666647741362673f,
-                                0.96028985649753618f};
-static __constant__ float c_gl_w[4] = {0.36268378337836166f, 0.31370664587788688f, 0.22238103445337443f,
-                                0.10122853629037706f};
+// Gauss-Legendre rules on [-1, 1], by their positive abscissae and weights
+// (the rules are symmetric), in two-node halves: half 0 and half 1 of the
+// 8-point rule, and the 4-point rule.  A "slot" is one half: 4 nodes.
+__device__ __forceinline__ void rule_half(int r, float &x0, float &w0, float &x1, float &w1)
+{
+    x0 = r == 0 ? 0.18343464249564978f : (r == 1 ? 0.79666647741362673f : 0.33998104358485626f);
+    w0 = r == 0 ? 0.36268378337836166f : (r == 1 ? 0.22238103445337443f : 0.65214515486254614f);
+    x1 = r == 0 ? 0.52553240991632899f : (r == 1 ? 0.96028985649753618f : 0.86113631159405258f);
+    w1 = r == 0 ? 0.31370664587788688f : (r == 1 ? 0.10122853629037706f : 0.34785484513745386f);
+}
 
 // Segment fields (see the header comment):
 //   sa, hl  start of the first sub-piece, half-length of every sub-piece
@@ -73,16 +76,29 @@ static __constant__ float c_gl_w[4] = {0.36268378337836166f, 0.31370664587788688
 //   Rr      reference distance of the difference (R, or 1)
 //   v       2 - Rr, computed where it keeps its relative precision (piece 2)
 //   add     constant added to the difference: K(1) - K(R) when Rr = 1, else 0
-//   meta    m | piece1 << 8 | tilde << 9, m the number of sub-pieces
+//   meta    m | piece1 << 8 | tilde << 9 | gl4 << 10, m the number of sub-pieces
+// The rule: within a piece the integrand is analytic in the strip
+// |Im s| < pi/2 (its singularities are the branch points of Q(s), where
+// B^2 + A^2 sinh^2 s = 0 with B >= A, and the poles of 1/cosh s; the kernel's
+// breakpoints are piece boundaries), so an n-point Gauss-Legendre rule on a
+// sub-piece of length L converges like rho^(-2n), rho = pi/L + sqrt(1 +
+// (pi/L)^2) the Bernstein ellipse that fits in the strip.  Sub-pieces of
+// length <= 2 take 8 points.  A short segment takes 4 points as one
+// sub-piece; the integrand's size near the strip's edge (Q ~ D for a particle
+// close to the face plane) makes the constant large, so the length limit is
+// set by measurement against the FP64 closed form over every pair: 1/2 and 1/4
+// leave errors of 3e-4 and 1e-4 |w|, 1/8 (the limit used, EM_GL4_MAXLEN)
+// none that the 8-point rule does not also have.
 constexpr int SEG_PIECE1 = 1 << 8;
 constexpr int SEG_TILDE = 1 << 9;
+constexpr int SEG_GL4 = 1 << 10;
 
-// int over one sub-piece [mid - hl, mid + hl] of a segment (8 Gauss-Legendre
-// nodes) of [K(Q(s)) - K(R)] / cosh(s) ds.  Q and 1/Q come from one reciprocal
-// square root and a Newton step (about 1 ulp); the other quotients are
-// reciprocals of quantities bounded away from zero.
-__device__ __forceinline__ float sub_eval(float mid, float hl, float A, float B2, float c4, float dd, float Rr,
-                                          float vr, float add, int meta)
+// One slot: int over the 4 nodes mid +- hl x0, mid +- hl x1 of half r of the
+// rule (see rule_half) of [K(Q(s)) - K(R)] / cosh(s) ds.  Q and 1/Q come from
+// one reciprocal square root and a Newton step (about 1 ulp); the other
+// quotients are reciprocals of quantities bounded away from zero.
+__device__ __forceinline__ float slot_eval(float mid, float hl, int r, float A, float B2, float c4, float dd,
+                                           float Rr, float vr, float add, int meta)
 {
     const bool piece1 = (meta & SEG_PIECE1) != 0;
     const bool tilde = (meta & SEG_TILDE) != 0;
@@ -91,10 +107,12 @@ __device__ __forceinline__ float sub_eval(float mid, float hl, float A, float B2
     const float v = piece1 ? Rr : vr;
     const float p2 = v * v, p3 = p2 * v, p4 = p2 * p2;
     const float iRr = __fdividef(1.f, Rr);   // Rr >= 1e-30 wherever it is used
+    float xk[2], wk[2];
+    rule_half(r, xk[0], wk[0], xk[1], wk[1]);
     float acc = 0.f;
 #pragma unroll kNodeUnroll
-    for (int i = 0; i < 8; ++i) {
-        const float s = fmaf((i & 1) ? -hl : hl, c_gl_x[i >> 1], mid);
+    for (int i = 0; i < 4; ++i) {
+        const float s = fmaf((i & 1) ? -hl : hl, xk[i >> 1], mid);
         const float em = expm1f(s);
         const float e = 1.f + em;
         const float ei = __fdividef(1.f, e);
@@ -119,7 +137,7 @@ __device__ __forceinline__ float sub_eval(float mid, float hl, float A, float B2
             const float x = d * iq * (1.f / 120.f) * br;
             f = (tilde ? x : d * iQ * (0.25f * iRr) * iq - x) + add;
         }
-        acc += c_gl_w[i >> 1] * __fdividef(f, ch);
+        acc += wk[i >> 1] * __fdividef(f, ch);
     }
     return acc * hl;
 }
