@@ -272,13 +272,14 @@ def reduce_over_ranks(t_ms, units, world, device):
 
 
 # Algorithmic work of map_exact per pair, per workload: the cell's faces, the
-# faces within reach (D < 2 and R < 2 in units of h) and their edges, and the
-# 8-node quadrature sub-pieces, averaged over random pairs of each workload
-# with a CPU model of the FP32 pass (6,000 pairs of the 1e6 cloud, 3,683 of
-# the 1e5 sphere).
+# faces within reach (D < 2 and R < 2 in units of h) and their edges, counted
+# over random pairs of each workload with a CPU model of the FP32 pass (6,000
+# pairs of the 1e6 cloud, 3,683 of the 1e5 sphere), and the quadrature's
+# 4-node slots (a 4-point segment, or half of an 8-point sub-piece), counted
+# over every pair of one launch by an instrumented build.
 WORK = {
-    "pseudo_1e6": dict(faces=15.64, faces_used=11.33, edges_used=60.65, subpieces=58.54),
-    "sphere_1e5": dict(faces=15.23, faces_used=7.93, edges_used=43.36, subpieces=40.33),
+    "pseudo_1e6": dict(faces=15.64, faces_used=11.33, edges_used=60.65, slots=88.43),
+    "sphere_1e5": dict(faces=15.23, faces_used=7.93, edges_used=43.36, slots=72.05),
 }
 # Work of the FP32 pass per unit, counted in its source (FMA = 2 flops):
 #  - per quadrature node 42 FP32 flops (common part 22, the kernel piece's
@@ -289,10 +290,10 @@ WORK = {
 #  - per face 60 (float-float plane distance and, for faces within reach,
 #    the face constants), and 18 per edge of a face within reach for the FP32
 #    distance to the polygon;
-#  - per 8-node sub-piece 14 for the float-float accumulation;
+#  - per 4-node slot 14 for the float-float accumulation;
 #  - per pair about 30 FP64 flops (r = x - g, 1/h, the final sums).
 FP32_FLOPS_NODE, SFU_OPS_NODE = 42, 5
-FP32_FLOPS_EDGE, FP32_FLOPS_FACE, FP32_FLOPS_POLY_EDGE, FP32_FLOPS_SUBPIECE = 150, 60, 18, 14
+FP32_FLOPS_EDGE, FP32_FLOPS_FACE, FP32_FLOPS_POLY_EDGE, FP32_FLOPS_SLOT = 150, 60, 18, 14
 FP64_FLOPS_PAIR = 30
 # nominal GB300 rates: FP32 152 SMs x 128 lanes x 2 x 2.07 GHz; SFU 16 per
 # clock per SM; FP64 1.25 TFLOP/s (152 SMs x 2 DFMA/clk x 2 x 2.07 GHz)
@@ -315,8 +316,8 @@ def roofline(npairs, ms, precision, workload):
     wk = WORK[workload]
     t = ms * 1e-3
     if precision == "mixed":
-        nodes = 8 * wk["subpieces"]
-        f32 = (FP32_FLOPS_NODE * nodes + FP32_FLOPS_SUBPIECE * wk["subpieces"]
+        nodes = 4 * wk["slots"]
+        f32 = (FP32_FLOPS_NODE * nodes + FP32_FLOPS_SLOT * wk["slots"]
                + (FP32_FLOPS_EDGE + FP32_FLOPS_POLY_EDGE) * wk["edges_used"] + FP32_FLOPS_FACE * wk["faces"])
         achieved = npairs * f32 / t / 1e12
         tr = TRAFFIC_PER_PAIR.get(workload)
