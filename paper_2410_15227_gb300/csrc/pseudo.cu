@@ -174,6 +174,32 @@ __device__ __forceinline__ void shift32(int32_t *buf, int &nb)
     nb -= 32;
 }
 
+// q = sqrt(q2) from an FP32 reciprocal square root and two FP64 Newton steps
+// (about 1 ulp, several FP64 instructions fewer than the FP64 square root);
+// below 1e-30 q is 0 (W then differs from W(0) by about 1e-30).
+__device__ __forceinline__ double q_of(double q2)
+{
+    if (!(q2 > 1e-30)) return 0.0;
+    double r = (double)rsqrtf((float)q2);
+    r = r * (1.5 - 0.5 * q2 * r * r);
+    r = r * (1.5 - 0.5 * q2 * r * r);
+    return q2 * r;
+}
+
+// The M4 spline w(q) and g(q) = 3 w(q) + q w'(q), the two sums of the
+// solver, for q < 2 (q2 = q^2).
+__device__ __forceinline__ void m4_wg(double q, double q2, double &w, double &g)
+{
+    if (q < 1.0) {
+        w = 1.0 + q2 * (-1.5 + 0.75 * q);
+        g = 3.0 + q2 * (-7.5 + 4.5 * q);
+    } else {
+        const double t = 2.0 - q, t2 = t * t;
+        w = 0.25 * t2 * t;
+        g = 0.75 * t2 * (t - q);
+    }
+}
+
 // n(h) and dn/dh for the pseudo-particle at (xa, ya, za), summed over the
 // population inside 2h; the result is identical on all lanes.
 __device__ Density warp_density(const em::ChunkTree &T, const double *__restrict__ qx,
@@ -188,13 +214,17 @@ __device__ Density warp_density(const em::ChunkTree &T, const double *__restrict
     const float xaf = (float)xa, yaf = (float)ya, zaf = (float)za, h2f = (float)(2.0 * h);
     const float lim = h2f + 1e-5f * (fabsf(xaf) + fabsf(yaf) + fabsf(zaf) + h2f);
     const float lim2 = lim * lim;
+    // sums of w and of g = 3w + q w' over the neighbours; n = norm sum w,
+    // dn/dh = -norm sum g / h
+    const double ih2 = ih * ih;
     auto sum_one = [&](int64_t k) {
-        double dx = qx[k] - xa, dy = qy[k] - ya, dz = qz[k] - za;
-        double q = sqrt(dx * dx + dy * dy + dz * dz) * ih;
-        if (q < 2.0) {
-            double w = em::m4_w(q);
-            s += w * norm;
-            ds += -(3.0 * w + q * em::m4_dw(q)) * norm * ih;
+        const double dx = qx[k] - xa, dy = qy[k] - ya, dz = qz[k] - za;
+        const double q2 = (dx * dx + dy * dy + dz * dz) * ih2;
+        if (q2 < 4.0) {
+            double w, g;
+            m4_wg(q_of(q2), q2, w, g);
+            s += w;
+            ds += g;
         }
     };
     int nb = 0;
@@ -212,7 +242,7 @@ __device__ Density warp_density(const em::ChunkTree &T, const double *__restrict
         s += __shfl_xor_sync(0xffffffffu, s, o);
         ds += __shfl_xor_sync(0xffffffffu, ds, o);
     }
-    return Density{s, ds};
+    return Density{s * norm, -ds * norm * ih};
 }
 
 // Sign of f(h) = h_fact n(h)^(-1/3) - h (Eq. 8) for the bisection, which uses
@@ -236,10 +266,16 @@ __device__ int warp_f_sign(const em::ChunkTree &T, const double *__restrict__ qx
     const float xaf = (float)xa, yaf = (float)ya, zaf = (float)za, h2f = (float)(2.0 * h);
     const float lim = h2f + 1e-5f * (fabsf(xaf) + fabsf(yaf) + fabsf(zaf) + h2f);
     const float lim2 = lim * lim;
+    // the sum of w; the walk stops once norm sum w exceeds thr
+    const double ih2 = ih * ih, thrw = thr / norm;
     auto sum_one = [&](int64_t k) {
-        double dx = qx[k] - xa, dy = qy[k] - ya, dz = qz[k] - za;
-        double q = sqrt(dx * dx + dy * dy + dz * dz) * ih;
-        if (q < 2.0) s += em::m4_w(q) * norm;
+        const double dx = qx[k] - xa, dy = qy[k] - ya, dz = qz[k] - za;
+        const double q2 = (dx * dx + dy * dy + dz * dz) * ih2;
+        if (q2 < 4.0) {
+            double w, g;
+            m4_wg(q_of(q2), q2, w, g);
+            s += w;
+        }
     };
     int nb = 0;
     bool full = em::warp_traverse_until(T, xaf, yaf, zaf, R * R, [&](int64_t k, bool valid) {
@@ -250,14 +286,14 @@ __device__ int warp_f_sign(const em::ChunkTree &T, const double *__restrict__ qx
         double tot = s;
 #pragma unroll
         for (int o = 16; o > 0; o >>= 1) tot += __shfl_xor_sync(0xffffffffu, tot, o);
-        return !(tot > thr);
+        return !(tot > thrw);
     });
     if (!full) return -1;
     if (lane < nb) sum_one(buf[lane]);
     __syncwarp();
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
-    const double f = h_fact * pow(s, -1.0 / 3.0) - h;
+    const double f = h_fact * pow(s * norm, -1.0 / 3.0) - h;
     return f > 0.0 ? 1 : (f < 0.0 ? -1 : 0);
 }
 

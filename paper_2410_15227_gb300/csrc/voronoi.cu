@@ -73,10 +73,10 @@ __device__ void emit_faces(const WCell &c, double gx, double gy, double gz, int 
             } else {
                 const int cur = c.cur;
                 double nx = c.pl[q][0], ny = c.pl[q][1], nz = c.pl[q][2];
-                double ln = sqrt(nx * nx + ny * ny + nz * nz);
-                nx /= ln;
-                ny /= ln;
-                nz /= ln;
+                const double ln = sqrt(nx * nx + ny * ny + nz * nz), il = 1.0 / ln;
+                nx *= il;
+                ny *= il;
+                nz *= il;
                 normals[3 * fi] = nx;
                 normals[3 * fi + 1] = ny;
                 normals[3 * fi + 2] = nz;
@@ -93,7 +93,7 @@ __device__ void emit_faces(const WCell &c, double gx, double gy, double gz, int 
                     verts[3 * (fvi + i) + 2] = pa[2] + gz;
                 }
                 double area = 0.5 * (ax * nx + ay * ny + az * nz);
-                v += area * (c.pl[q][3] / ln) / 3.0;
+                v += area * (c.pl[q][3] * il) * (1.0 / 3.0);
             }
         }
         fbase += __popc(m);
