@@ -168,7 +168,13 @@ int voronoi_destroy(em_voronoi *v);
  * All particle-cell pairs whose kernel support meets the cell:
  * dist(x_i, V_j) < 2 h_i (the "particle-cell pairs" whose number sets the
  * mapping cost, Section 1).  Pairs are sorted by (cell j, particle i).
- *   d_x, d_y, d_z, d_h: np (pseudo-)particles (device). */
+ *   d_x, d_y, d_z, d_h: np (pseudo-)particles (device).
+ *   npairs (host, may be NULL): the pair count.
+ * One pass writes the hits, unordered, into a buffer sized from the
+ * context's previous pair count (plus 1/8; a guess on the first call) and a
+ * radix sort orders them; a call that finds more pairs than the buffer holds
+ * repeats the pass once with the exact size.  Synchronises the stream to
+ * read the count.  EM_ECAPACITY if the pairs reach 2^31. */
 int find_pairs(em_ctx *ctx, int64_t np, const double *d_x, const double *d_y, const double *d_z,
                const double *d_h, const em_voronoi *v, em_pairs **out, int64_t *npairs);
 /* Import a pair list sorted by (j, i) (device int32 arrays). */
