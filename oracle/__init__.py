@@ -81,7 +81,7 @@ def _declare(L):
     L.orc_build_tree.argtypes = [_i64, _p, _p, _p, _p, _p, _i32, _i64] + [_p] * 16
     L.orc_select.restype = _i64
     L.orc_select.argtypes = [_i64, _p, _p, _p, _p, _p, _p, _p, _p, _i32, _p, _d, _d, _d,
-                             _i64, _p, _p, _p, _p]
+                             _i64, _p, _p, _p, _p, _p]
     L.orc_h_solve.restype = None
     L.orc_h_solve.argtypes = [_i64, _p, _p, _p, _i64, _p, _p, _p, _p, _d, _d, _i32, _p, _p,
                               _p, _i32]
@@ -425,8 +425,14 @@ class Selection:
         return int(self.kind.shape[0])
 
 
-def select(tree: Tree, sources, r_part, r_leaf, theta) -> Selection:
+def select(tree: Tree, sources, r_part, r_leaf, theta, force=None) -> Selection:
+    """Adaptive tree-walk (Section 2.4.1, Eq. 4).  force: optional per-node flags
+    from the refinement check (refine_fail): a flagged node is opened, a flagged
+    leaf has its particles extracted."""
     src = _f64(np.asarray(sources).reshape(-1, 3))
+    fz = None if force is None else np.ascontiguousarray(np.asarray(force, dtype=np.uint8))
+    if fz is not None and fz.shape[0] != tree.nnode:
+        raise ValueError("force: one flag per tree node")
     cap = tree.perm.shape[0] + tree.nnode + 8
     kind = np.zeros(cap, np.int32)
     ref = np.zeros(cap, np.int64)
@@ -437,7 +443,8 @@ def select(tree: Tree, sources, r_part, r_leaf, theta) -> Selection:
                             _ptr(tree.first), _ptr(tree.count), _ptr(_f64(com[:, 0])),
                             _ptr(_f64(com[:, 1])), _ptr(_f64(com[:, 2])), _ptr(tree.size),
                             src.shape[0], _ptr(src), float(r_part), float(r_leaf), float(theta),
-                            cap, _ptr(kind), _ptr(ref), _ptr(pop), _ptr(npop))
+                            cap, _ptr(kind), _ptr(ref), _ptr(pop), _ptr(npop),
+                            None if fz is None else _ptr(fz))
     if nout < 0:
         raise RuntimeError("oracle select: output overflow")
     return Selection(kind[:nout].copy(), ref[:nout].copy(), pop[:int(npop[0])].copy())
@@ -490,10 +497,11 @@ class Pseudo:
 
 def make_pseudo_particles(x, y, z, m, h_particle, box, sources, r_part, r_leaf, theta,
                           h_fact=1.2, tol=1e-13, max_newton=50, leaf_max=8, nthreads=None,
-                          solve=True):
-    """Tree build, adaptive tree-walk and node h-solver (Sections 2.2, 2.4)."""
+                          solve=True, force=None):
+    """Tree build, adaptive tree-walk and node h-solver (Sections 2.2, 2.4);
+    force: per-node refinement flags (see select)."""
     t = build_tree(x, y, z, m, box, leaf_max)
-    sel = select(t, sources, r_part, r_leaf, theta)
+    sel = select(t, sources, r_part, r_leaf, theta, force)
     x, y, z, m = (np.asarray(a, dtype=np.float64) for a in (x, y, z, m))
     hp = np.asarray(h_particle, dtype=np.float64)
     n = sel.n
@@ -519,3 +527,51 @@ def make_pseudo_particles(x, y, z, m, h_particle, box, sources, r_part, r_leaf, 
         ph[isn] = hh
         st[isn] = s
     return Pseudo(px, py, pz, ph, pm, org, first, cnt, st), t, sel
+
+
+# ---------------------------------------------------------------------------
+# Adaptive refinement (Section 2.4.1, Eq. 5)
+# ---------------------------------------------------------------------------
+
+def refine_limit(size, size_root, K):
+    """Eq. 5: the neutral-fraction threshold of a node of size s,
+    f_neu,limit = (1/K) (K - 1 / (s / s_root)); -inf for a node of size 0."""
+    size = np.asarray(size, dtype=np.float64)
+    with np.errstate(divide="ignore"):
+        return (K - size_root / size) / K
+
+
+def refine_fail(tree: Tree, nodes, f_neu, K):
+    """Mask over nodes: under-resolved when f_neu < f_neu,limit(s_node) (Eq. 5).
+    NaN (a pseudo-particle without pairs) does not fail."""
+    nodes = np.asarray(nodes, dtype=np.int64)
+    return np.asarray(f_neu) < refine_limit(tree.size[nodes], tree.size[0], K)
+
+
+def refine(x, y, z, m, h_particle, box, sources, r_part, r_leaf, theta, cells: Cells, f_cell, K,
+           max_iter=20, h_fact=1.2, tol=1e-13, leaf_max=8, nthreads=None):
+    """The adaptive tree-walk iterations of Section 2.4.1: select, map, map the
+    cells' neutral fraction back onto the pseudo-particles, flag the nodes that
+    fail Eq. 5, and select again with them opened (a failing leaf has its
+    particles extracted, which is what raising r_part does for it), until no
+    node fails.  Returns (pseudo, tree, selection, force flags, iterations,
+    f_neu per pseudo-particle of the last round)."""
+    force = None
+    for it in range(1, max_iter + 1):
+        ps, t, sel = make_pseudo_particles(x, y, z, m, h_particle, box, sources, r_part, r_leaf, theta,
+                                           h_fact=h_fact, tol=tol, leaf_max=leaf_max, nthreads=nthreads,
+                                           force=force)
+        if force is None:
+            force = np.zeros(t.nnode, np.uint8)
+        pairs = find_pairs(ps.x, ps.y, ps.z, ps.h, cells, nthreads)
+        w = map_exact(pairs, ps.x, ps.y, ps.z, ps.h, cells, nthreads)
+        fn = map_back(pairs, w, f_cell, ps.n)
+        isn = sel.kind == 0
+        nodes = sel.ref[isn]
+        bad = nodes[refine_fail(t, nodes, fn[isn], K)]
+        new = bad[force[bad] == 0]
+        if new.shape[0] == 0:
+            return ps, t, sel, force, it, fn
+        force[new] = 1
+    return ps, t, sel, force, max_iter, fn
+

@@ -166,11 +166,15 @@ int64_t orc_build_tree(int64_t n, const double *x, const double *y, const double
  * and the h-solver population (selected nodes plus the leaves whose particles
  * were extracted), pop_node[]: node indices in the same order.
  * Returns the number of pseudo-particles (npop in *npop_out), or -1 on overflow. */
+/* The adaptive tree-walk (Section 2.4.1, Eq. 4).  force (one byte per node,
+ * may be NULL) marks nodes that the refinement check of Eq. 5 found
+ * under-resolved: such an internal node is opened, such a leaf has its
+ * particles extracted, whatever the distance criteria say. */
 int64_t orc_select(int64_t nnode, const int32_t *nchild, const int64_t *first_child, const int64_t *first,
                    const int64_t *count, const double *cx, const double *cy, const double *cz,
                    const double *size, int nsrc, const double *src, double r_part, double r_leaf,
                    double theta, int64_t max_out, int32_t *kind, int64_t *ref, int64_t *pop_node,
-                   int64_t *npop_out)
+                   int64_t *npop_out, const uint8_t *force)
 {
     (void)nnode;
     int64_t *stack = (int64_t *)malloc(sizeof(int64_t) * 8 * 64 + sizeof(int64_t));
@@ -186,8 +190,9 @@ int64_t orc_select(int64_t nnode, const int32_t *nchild, const int64_t *first_ch
             if (q < r2) r2 = q;
         }
         int open;
+        const int forced = force != NULL && force[a] != 0;
         if (nchild[a] == 0) {
-            if (r2 < rp2) {
+            if (r2 < rp2 || forced) {
                 if (nout + count[a] > max_out) { free(stack); return -1; }
                 for (int64_t k = first[a]; k < first[a] + count[a]; ++k) {
                     kind[nout] = 1; ref[nout] = k; ++nout;
@@ -197,7 +202,7 @@ int64_t orc_select(int64_t nnode, const int32_t *nchild, const int64_t *first_ch
             }
             open = 0;
         } else {
-            open = (r2 < rl2) || (size[a] * size[a] > th2 * r2);
+            open = forced || (r2 < rl2) || (size[a] * size[a] > th2 * r2);
         }
         if (open) {
             for (int64_t c = first_child[a] + nchild[a] - 1; c >= first_child[a]; --c) stack[sp++] = c;
