@@ -129,6 +129,33 @@ int tree_destroy(em_tree *t);
  * Returns EM_ENOTCONV (with outputs valid) when some solve fell back to h_0. */
 int make_pseudo_particles(em_ctx *ctx, const em_tree *t, const double *d_h_particle, int nsrc,
                           const double *h_src, const em_params *p, em_pseudo **out);
+/* The adaptive refinement of Section 2.4.1 (Eq. 5).  make_pseudo_particles_
+ * forced is make_pseudo_particles with per-node flags from refine_check:
+ * d_force[n_nodes] (device, one byte per tree node, in tree_get's order); a
+ * flagged internal node is opened whatever Eq. 4 says, a flagged leaf has its
+ * particles extracted (what raising r_part does for it).  EM_EINVAL when
+ * d_force is NULL. */
+int make_pseudo_particles_forced(em_ctx *ctx, const em_tree *t, const double *d_h_particle, int nsrc,
+                                 const double *h_src, const em_params *p, const uint8_t *d_force,
+                                 em_pseudo **out);
+/* Eq. 5: a node pseudo-particle is under-resolved when its neutral fraction
+ * f_neu is below f_neu,limit = (K - s_root / s_node) / K, K > 1 (s_node the
+ * node's size, s_root the root's).  ps must come from t.
+ *   d_f_neu[n_pseudo] (device): the neutral fraction of each pseudo-particle
+ *     (e.g. map_back of the cells' values); NaN (no pair) and nodes of size 0
+ *     never fail; extracted particles are not checked.
+ *   flag_leaves: 1 flags failing leaves too (their particles are extracted
+ *     in the next walk); 0 leaves them unflagged, for the form of Section
+ *     2.4.1 where a failing leaf makes the caller raise r_part and r_leaf.
+ *   d_force[n_nodes] (device, in/out): set to 1 for every failing internal
+ *     node (and leaf, with flag_leaves) not yet flagged.
+ *   *h_nnew (host): the number of nodes flagged by this call.
+ *   *h_nleaf (host, may be NULL): the number of failing leaves.
+ * The iteration stops when *h_nnew is 0 (and, without flag_leaves, *h_nleaf
+ * is 0).  Synchronises the stream to read the counts.  EM_EINVAL for K <= 1,
+ * a flag_leaves other than 0 or 1, or a NULL pointer other than h_nleaf. */
+int refine_check(em_ctx *ctx, const em_pseudo *ps, const em_tree *t, const double *d_f_neu, double K,
+                 int flag_leaves, uint8_t *d_force, int64_t *h_nnew, int64_t *h_nleaf);
 /* n_pseudo; n_status[4]: counts of solver status 0 Newton, 1 bisection,
  * 2 fallback h_0, 3 individual particle (may be NULL). */
 int pseudo_info(const em_pseudo *ps, int64_t *n_pseudo, int64_t *n_status);

@@ -549,13 +549,20 @@ def refine_fail(tree: Tree, nodes, f_neu, K):
 
 
 def refine(x, y, z, m, h_particle, box, sources, r_part, r_leaf, theta, cells: Cells, f_cell, K,
-           max_iter=20, h_fact=1.2, tol=1e-13, leaf_max=8, nthreads=None):
+           max_iter=20, leaf_step=0.0, h_fact=1.2, tol=1e-13, leaf_max=8, nthreads=None):
     """The adaptive tree-walk iterations of Section 2.4.1: select, map, map the
     cells' neutral fraction back onto the pseudo-particles, flag the nodes that
-    fail Eq. 5, and select again with them opened (a failing leaf has its
-    particles extracted, which is what raising r_part does for it), until no
-    node fails.  Returns (pseudo, tree, selection, force flags, iterations,
-    f_neu per pseudo-particle of the last round)."""
+    fail Eq. 5, and select again with the flagged internal nodes opened, until
+    no node fails.
+
+    A failing leaf cannot be opened.  With leaf_step > 0, as in Section 2.4.1
+    and the runs of Section 3.3, r_part and r_leaf both grow by leaf_step for
+    the next walk whenever some leaf fails; the leaf itself is not flagged.
+    With leaf_step = 0 the failing leaf is flagged and its particles are
+    extracted in the next walk, the local form of raising r_part for it.
+
+    Returns (pseudo, tree, selection, force flags, iterations, f_neu per
+    pseudo-particle of the last round, (r_part, r_leaf) of the last round)."""
     force = None
     for it in range(1, max_iter + 1):
         ps, t, sel = make_pseudo_particles(x, y, z, m, h_particle, box, sources, r_part, r_leaf, theta,
@@ -569,9 +576,18 @@ def refine(x, y, z, m, h_particle, box, sources, r_part, r_leaf, theta, cells: C
         isn = sel.kind == 0
         nodes = sel.ref[isn]
         bad = nodes[refine_fail(t, nodes, fn[isn], K)]
+        leaf = t.nchild[bad] == 0
+        if leaf_step > 0:
+            grow = bool(np.any(leaf))
+            bad = bad[~leaf]
+        else:
+            grow = False
         new = bad[force[bad] == 0]
-        if new.shape[0] == 0:
-            return ps, t, sel, force, it, fn
+        if new.shape[0] == 0 and not grow:
+            return ps, t, sel, force, it, fn, (r_part, r_leaf)
         force[new] = 1
-    return ps, t, sel, force, max_iter, fn
+        if grow:
+            r_part += leaf_step
+            r_leaf += leaf_step
+    return ps, t, sel, force, max_iter, fn, (r_part, r_leaf)
 

@@ -47,6 +47,8 @@ SIGNATURES = {
     "tree_get": (I32, [P, P] + [P] * 11),
     "tree_destroy": (I32, [P]),
     "make_pseudo_particles": (I32, [P, P, P, I32, P, PPAR, PP]),
+    "make_pseudo_particles_forced": (I32, [P, P, P, I32, P, PPAR, P, PP]),
+    "refine_check": (I32, [P, P, P, P, D, I32, P, PI64, PI64]),
     "pseudo_info": (I32, [P, PI64, PI64]),
     "pseudo_get": (I32, [P, P] + [P] * 9),
     "pseudo_destroy": (I32, [P]),

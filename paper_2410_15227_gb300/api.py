@@ -8,7 +8,7 @@ tensors allocated by torch.
 from __future__ import annotations
 
 import ctypes as C
-from dataclasses import dataclass, fields
+from dataclasses import dataclass, fields, replace
 
 import torch
 
@@ -214,16 +214,64 @@ def build_tree(ctx: Context, x, y, z, m, box, leaf_max: int = 8) -> Tree:
     return Tree(ctx, h)
 
 
-def make_pseudo_particles(ctx: Context, tree: Tree, h_particle, sources, params: Params) -> Pseudo:
+def make_pseudo_particles(ctx: Context, tree: Tree, h_particle, sources, params: Params,
+                          force: torch.Tensor | None = None) -> Pseudo:
+    """force: optional uint8 flags, one per tree node (refine_check), for
+    make_pseudo_particles_forced."""
     src = [float(v) for v in torch.as_tensor(sources, dtype=torch.float64).reshape(-1).tolist()]
     arr = (C.c_double * len(src))(*src)
     p = params.native()
     h = C.c_void_p()
-    n, _, _ = tree.info()
-    N.call("make_pseudo_particles", ctx.handle, tree.handle, _ptr(h_particle, f64, n, "h"),
-           len(src) // 3, C.cast(arr, C.c_void_p), C.byref(p), C.byref(h),
-           allow=(N.EM_OK, N.EM_ENOTCONV))
+    n, nnode, _ = tree.info()
+    if force is None:
+        N.call("make_pseudo_particles", ctx.handle, tree.handle, _ptr(h_particle, f64, n, "h"),
+               len(src) // 3, C.cast(arr, C.c_void_p), C.byref(p), C.byref(h),
+               allow=(N.EM_OK, N.EM_ENOTCONV))
+    else:
+        N.call("make_pseudo_particles_forced", ctx.handle, tree.handle, _ptr(h_particle, f64, n, "h"),
+               len(src) // 3, C.cast(arr, C.c_void_p), C.byref(p), _ptr(force, torch.uint8, nnode, "force"),
+               C.byref(h), allow=(N.EM_OK, N.EM_ENOTCONV))
     return Pseudo(ctx, h)
+
+
+def refine_check(ctx: Context, ps: Pseudo, tree: Tree, f_neu, K: float, force: torch.Tensor,
+                 flag_leaves: bool = True) -> tuple[int, int]:
+    """Flags (in force) the node pseudo-particles that fail Eq. 5, leaves only
+    with flag_leaves; returns (newly flagged nodes, failing leaves)."""
+    n, _ = ps.info()
+    _, nnode, _ = tree.info()
+    k, nl = C.c_int64(), C.c_int64()
+    N.call("refine_check", ctx.handle, ps.handle, tree.handle, _ptr(f_neu, f64, n, "f_neu"), float(K),
+           int(bool(flag_leaves)), _ptr(force, torch.uint8, nnode, "force"), C.byref(k), C.byref(nl))
+    return k.value, nl.value
+
+
+def refine(ctx: Context, tree: Tree, h_particle, sources, params: Params, vor: "Voronoi", f_cell, K: float,
+           max_iter: int = 20, leaf_step: float = 0.0):
+    """The iteration of Section 2.4.1 as a sequence of library calls:
+    make_pseudo_particles(_forced), find_pairs, map_exact, map_back of the
+    cells' neutral fraction f_cell, refine_check; until no node fails Eq. 5
+    anew.  A failing leaf is flagged for extraction (leaf_step = 0) or, with
+    leaf_step > 0, raises r_part and r_leaf by leaf_step for the next walk
+    (Sections 2.4.1 and 3.3).  Returns (pseudo, pairs, w, force, iterations,
+    f_neu, (r_part, r_leaf) of the last walk)."""
+    _, nnode, _ = tree.info()
+    force = torch.zeros(nnode, dtype=torch.uint8, device=ctx.device)
+    p = replace(params)
+    for it in range(1, max_iter + 1):
+        ps = make_pseudo_particles(ctx, tree, h_particle, sources, p, force)
+        g = ps.get()
+        pr = find_pairs(ctx, g["x"], g["y"], g["z"], g["h"], vor)
+        w, _, _, _ = map_exact(ctx, pr, g["x"], g["y"], g["z"], g["h"], g["m"], vor, p)
+        f_neu, _ = map_back(ctx, pr, w, f_cell)
+        nnew, nleaf = refine_check(ctx, ps, tree, f_neu, K, force, flag_leaves=leaf_step <= 0)
+        grow = leaf_step > 0 and nleaf > 0
+        if nnew == 0 and not grow:
+            return ps, pr, w, force, it, f_neu, (p.r_part, p.r_leaf)
+        if grow:
+            p.r_part += leaf_step
+            p.r_leaf += leaf_step
+    return ps, pr, w, force, max_iter, f_neu, (p.r_part, p.r_leaf)
 
 
 def build_voronoi(ctx: Context, gx, gy, gz, box, params: Params | None = None) -> Voronoi:

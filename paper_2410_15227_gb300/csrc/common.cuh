@@ -139,6 +139,7 @@ struct em_pseudo {
     double *x = nullptr, *y = nullptr, *z = nullptr, *h = nullptr, *m = nullptr;
     int64_t *origin = nullptr;
     int32_t *first = nullptr, *count = nullptr, *status = nullptr;
+    int32_t *node = nullptr;   // [n] tree node of a node pseudo-particle, -1 for an extracted particle
     explicit em_pseudo(cudaStream_t s) : mem(s) {}
 };
 

@@ -25,7 +25,7 @@ enum : uint8_t { F_LEAF = 1, F_EXTRACT = 2, F_OPEN = 4, F_REACHED = 8 };
 __global__ void k_node_flags(int64_t nnode, const int32_t *__restrict__ nchild, const double *__restrict__ cx,
                              const double *__restrict__ cy, const double *__restrict__ cz,
                              const double *__restrict__ size, int nsrc, const double *__restrict__ src, double rp2,
-                             double rl2, double th2, uint8_t *__restrict__ flags)
+                             double rl2, double th2, const uint8_t *__restrict__ force, uint8_t *__restrict__ flags)
 {
     int64_t a = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     if (a >= nnode) return;
@@ -37,12 +37,15 @@ __global__ void k_node_flags(int64_t nnode, const int32_t *__restrict__ nchild, 
         r2 = q < r2 ? q : r2;
     }
     uint8_t f = 0;
+    // a node the refinement check found under-resolved (Eq. 5) is opened, or
+    // if a leaf has its particles extracted
+    const bool forced = force != nullptr && force[a] != 0;
     if (nchild[a] == 0) {
         f |= F_LEAF;
-        if (r2 < rp2) f |= F_EXTRACT;
+        if (r2 < rp2 || forced) f |= F_EXTRACT;
     } else {
         // open inside r_leaf, or when theta^2 < (s/r)^2 (Eq. 4)
-        if (r2 < rl2 || __dmul_rn(size[a], size[a]) > __dmul_rn(th2, r2)) f |= F_OPEN;
+        if (forced || r2 < rl2 || __dmul_rn(size[a], size[a]) > __dmul_rn(th2, r2)) f |= F_OPEN;
     }
     flags[a] = f;
 }
@@ -90,7 +93,8 @@ __global__ void k_emit(int64_t n, const int32_t *__restrict__ start, const int32
                        double *__restrict__ px, double *__restrict__ py, double *__restrict__ pz,
                        double *__restrict__ ph, double *__restrict__ pm, int64_t *__restrict__ origin,
                        int32_t *__restrict__ pfirst, int32_t *__restrict__ pcount, int32_t *__restrict__ status,
-                       double *__restrict__ popx, double *__restrict__ popy, double *__restrict__ popz)
+                       int32_t *__restrict__ pnode, double *__restrict__ popx, double *__restrict__ popy,
+                       double *__restrict__ popz)
 {
     int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     if (k >= n) return;
@@ -105,6 +109,7 @@ __global__ void k_emit(int64_t n, const int32_t *__restrict__ start, const int32
             origin[q] = (int64_t)label[a];
             pfirst[q] = first[a];
             pcount[q] = count[a];
+            pnode[q] = a;
             status[q] = -1;   // to be solved
             // h_0 = h_fact (2 s_node) (Eq. 11); a one-particle node starts from its particle's h
             ph[q] = (count[a] == 1 || size[a] == 0.0) ? hpart[perm[first[a]]] : (2.0 * h_fact) * size[a];
@@ -116,6 +121,7 @@ __global__ void k_emit(int64_t n, const int32_t *__restrict__ start, const int32
             origin[q] = -(int64_t)perm[k] - 1;
             pfirst[q] = (int32_t)k;
             pcount[q] = 1;
+            pnode[q] = -1;
             status[q] = 3;
             ph[q] = hpart[perm[k]];
         }
@@ -363,7 +369,7 @@ __global__ void k_status_count(int64_t n, const int32_t *__restrict__ status, un
 }  // namespace
 
 static int pseudo_impl(em_ctx *ctx, const em_tree *t, const double *d_hp, int nsrc, const double *h_src,
-                       const em_params *p, em_pseudo *ps)
+                       const em_params *p, const uint8_t *d_force, em_pseudo *ps)
 {
     cudaStream_t st = ctx->stream;
     const int64_t n = t->n, nn = t->nnode;
@@ -383,7 +389,7 @@ static int pseudo_impl(em_ctx *ctx, const em_tree *t, const double *d_hp, int ns
     EM_CUDA(cudaMemsetAsync(popstart, 0, n * sizeof(int32_t), st));
     const double rp2 = p->r_part * p->r_part, rl2 = p->r_leaf * p->r_leaf, th2 = p->theta * p->theta;
     k_node_flags<<<em_grid(nn, 256), 256, 0, st>>>(nn, t->nchild, t->cx, t->cy, t->cz, t->size, nsrc, src, rp2, rl2,
-                                                   th2, flags);
+                                                   th2, d_force, flags);
     EM_LAUNCHED(ctx);
     k_reached<<<em_grid(nn, 256), 256, 0, st>>>(nn, t->parent, flags);
     EM_LAUNCHED(ctx);
@@ -410,6 +416,7 @@ static int pseudo_impl(em_ctx *ctx, const em_tree *t, const double *d_hp, int ns
     EM_TRY(m.alloc(&ps->first, np));
     EM_TRY(m.alloc(&ps->count, np));
     EM_TRY(m.alloc(&ps->status, np));
+    EM_TRY(m.alloc(&ps->node, np));
     double *qx, *qy, *qz;
     EM_TRY(tmp.alloc(&qx, npop));
     EM_TRY(tmp.alloc(&qy, npop));
@@ -417,7 +424,7 @@ static int pseudo_impl(em_ctx *ctx, const em_tree *t, const double *d_hp, int ns
     k_emit<<<em_grid(n, 256), 256, 0, st>>>(n, start, pidx, owner, popstart, popidx, t->label, t->first, t->count,
                                             t->mass, t->cx, t->cy, t->cz, t->size, t->xs, t->ys, t->zs, t->ms,
                                             t->perm, d_hp, p->h_fact, ps->x, ps->y, ps->z, ps->h, ps->m, ps->origin,
-                                            ps->first, ps->count, ps->status, qx, qy, qz);
+                                            ps->first, ps->count, ps->status, ps->node, qx, qy, qz);
     EM_LAUNCHED(ctx);
     em::ChunkTree T;
     EM_TRY(em_chunk_tree_build(ctx, tmp, npop, qx, qy, qz, nullptr, 0.0, &T));
@@ -444,8 +451,8 @@ static int pseudo_impl(em_ctx *ctx, const em_tree *t, const double *d_hp, int ns
     return EM_OK;
 }
 
-EM_EXPORT int make_pseudo_particles(em_ctx *ctx, const em_tree *t, const double *d_h_particle, int nsrc,
-                                    const double *h_src, const em_params *p, em_pseudo **out)
+static int make_pseudo(em_ctx *ctx, const em_tree *t, const double *d_h_particle, int nsrc, const double *h_src,
+                       const em_params *p, const uint8_t *d_force, em_pseudo **out)
 {
     EM_CHECK_ARG(ctx && t && d_h_particle && h_src && p && out);
     EM_CHECK_ARG(nsrc >= 1 && nsrc <= 4096);
@@ -454,7 +461,7 @@ EM_EXPORT int make_pseudo_particles(em_ctx *ctx, const em_tree *t, const double 
     *out = nullptr;
     em_pseudo *ps = new em_pseudo(ctx->stream);
     ps->device = ctx->device;
-    int rc = pseudo_impl(ctx, t, d_h_particle, nsrc, h_src, p, ps);
+    int rc = pseudo_impl(ctx, t, d_h_particle, nsrc, h_src, p, d_force, ps);
     if (rc) {
         ps->mem.release();
         delete ps;
@@ -462,4 +469,69 @@ EM_EXPORT int make_pseudo_particles(em_ctx *ctx, const em_tree *t, const double 
     }
     *out = ps;
     return ps->nstatus[2] ? EM_ENOTCONV : EM_OK;
+}
+
+EM_EXPORT int make_pseudo_particles(em_ctx *ctx, const em_tree *t, const double *d_h_particle, int nsrc,
+                                    const double *h_src, const em_params *p, em_pseudo **out)
+{
+    return make_pseudo(ctx, t, d_h_particle, nsrc, h_src, p, nullptr, out);
+}
+
+EM_EXPORT int make_pseudo_particles_forced(em_ctx *ctx, const em_tree *t, const double *d_h_particle, int nsrc,
+                                           const double *h_src, const em_params *p, const uint8_t *d_force,
+                                           em_pseudo **out)
+{
+    EM_CHECK_ARG(d_force);
+    return make_pseudo(ctx, t, d_h_particle, nsrc, h_src, p, d_force, out);
+}
+
+namespace {
+
+// Eq. 5 for every node pseudo-particle: under-resolved when its neutral
+// fraction is below (K - s_root / s_node) / K (NaN, a pseudo-particle without
+// pairs, does not fail; nor does a node of size 0).  cnt[1] counts the failing
+// leaves.  A failing internal node not yet flagged, and a failing leaf when
+// flag_leaves is set, gets its flag and is counted in cnt[0].
+__global__ void k_refine_check(int64_t np, const int32_t *__restrict__ node, const int32_t *__restrict__ nchild,
+                               const double *__restrict__ size, const double *__restrict__ f_neu, double K,
+                               int flag_leaves, uint8_t *__restrict__ force, unsigned long long *__restrict__ cnt)
+{
+    const int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (q >= np) return;
+    const int32_t a = node[q];
+    if (a < 0 || !(size[a] > 0.0)) return;
+    const double lim = (K - size[0] / size[a]) / K;
+    if (!(f_neu[q] < lim)) return;
+    const bool leaf = nchild[a] == 0;
+    if (leaf) atomicAdd(&cnt[1], 1ull);
+    if ((!leaf || flag_leaves) && !force[a]) {
+        force[a] = 1;
+        atomicAdd(&cnt[0], 1ull);
+    }
+}
+
+}  // namespace
+
+EM_EXPORT int refine_check(em_ctx *ctx, const em_pseudo *ps, const em_tree *t, const double *d_f_neu, double K,
+                           int flag_leaves, uint8_t *d_force, int64_t *h_nnew, int64_t *h_nleaf)
+{
+    EM_CHECK_ARG(ctx && ps && t && d_f_neu && d_force && h_nnew);
+    EM_CHECK_ARG(K > 1.0);
+    EM_CHECK_ARG(flag_leaves == 0 || flag_leaves == 1);
+    *h_nnew = 0;
+    if (h_nleaf) *h_nleaf = 0;
+    if (ps->n == 0 || t->nnode == 0) return EM_OK;
+    DevArena tmp(ctx->stream, true);
+    unsigned long long *cnt;
+    EM_TRY(tmp.alloc(&cnt, 2));
+    EM_CUDA(cudaMemsetAsync(cnt, 0, 2 * sizeof *cnt, ctx->stream));
+    k_refine_check<<<em_grid(ps->n, 256), 256, 0, ctx->stream>>>(ps->n, ps->node, t->nchild, t->size, d_f_neu, K,
+                                                                 flag_leaves, d_force, cnt);
+    EM_LAUNCHED(ctx);
+    unsigned long long h[2] = {0, 0};
+    EM_CUDA(cudaMemcpyAsync(h, cnt, sizeof h, cudaMemcpyDeviceToHost, ctx->stream));
+    EM_CUDA(cudaStreamSynchronize(ctx->stream));
+    *h_nnew = (int64_t)h[0];
+    if (h_nleaf) *h_nleaf = (int64_t)h[1];
+    return EM_OK;
 }

@@ -75,8 +75,8 @@ def test_refine_loop(orc, small):
     f_cell = np.where(np.linalg.norm(cells.gen, axis=1) < 0.3, 0.0, 1.0)
     K = 20.0
     ps0, _, _ = orc.make_pseudo_particles(w.x, w.y, w.z, w.m, w.h, w.box, SRC, 0.05, 0.1, 0.3)
-    ps, t, sel, force, it, fn = orc.refine(w.x, w.y, w.z, w.m, w.h, w.box, SRC, 0.05, 0.1, 0.3, cells,
-                                           f_cell, K, max_iter=30)
+    ps, t, sel, force, it, fn, radii = orc.refine(w.x, w.y, w.z, w.m, w.h, w.box, SRC, 0.05, 0.1, 0.3, cells,
+                                                  f_cell, K, max_iter=30)
     assert 2 <= it < 30                       # refinement happened, and ended
     isn = sel.kind == 0
     nodes = sel.ref[isn]
@@ -85,3 +85,26 @@ def test_refine_loop(orc, small):
     assert _covers_all(t, sel, w.n)
     # the flagged nodes are opened (internal) or extracted (leaves)
     assert not np.any(force[nodes])
+    assert radii == (0.05, 0.1)             # the radii stay put when failing leaves are extracted
+
+
+def test_refine_loop_radii_growth(orc, small):
+    """The form of Section 2.4.1 and Section 3.3: a failing leaf raises r_part
+    and r_leaf by a step for the next walk instead of being flagged."""
+    w, _ = small
+    cells = orc.voronoi(w.gx, w.gy, w.gz, w.box)
+    f_cell = np.where(np.linalg.norm(cells.gen, axis=1) < 0.3, 0.0, 1.0)
+    K, step = 20.0, 0.05
+    ps, t, sel, force, it, fn, (rp, rl) = orc.refine(w.x, w.y, w.z, w.m, w.h, w.box, SRC, 0.05, 0.1, 0.3,
+                                                     cells, f_cell, K, max_iter=30, leaf_step=step)
+    assert 2 <= it < 30
+    isn = sel.kind == 0
+    nodes = sel.ref[isn]
+    assert not np.any(orc.refine_fail(t, nodes, fn[isn], K))
+    assert not np.any(force[t.nchild == 0])  # no leaf is ever flagged in this form
+    k = round((rp - 0.05) / step)
+    assert k >= 1 and rp == pytest.approx(0.05 + k * step) and rl == pytest.approx(0.1 + k * step)
+    # the last walk is the plain walk with the grown radii and the flags
+    again = orc.select(t, SRC, rp, rl, 0.3, force=force)
+    assert np.array_equal(again.kind, sel.kind) and np.array_equal(again.ref, sel.ref)
+    assert _covers_all(t, sel, w.n)
