@@ -48,6 +48,8 @@ def parse():
     ap.add_argument("--precision", choices=("mixed", "fp64"), default="mixed")
     ap.add_argument("--theta", type=float, default=THETA)
     ap.add_argument("--fp64-threshold", type=float, default=1e-5)
+    ap.add_argument("--h-tol", type=float, default=1e-13,
+                    help="Newton tolerance |dh|/h_0 of the node h-solver; the paper runs 1e-2")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cache", default=os.path.join(ROOT, "_cache"))
@@ -139,7 +141,7 @@ def run_ours(args, rank, world):
     f_cell = dv(np.random.default_rng([5, 3]).random(w.ngen))
     src = np.zeros((1, 3))
     P = api.Params(r_part=w.params["r_part"], r_leaf=w.params["r_leaf"], theta=args.theta,
-                   h_fact=w.params["h_fact"], h_tol=1e-13,
+                   h_fact=w.params["h_fact"], h_tol=args.h_tol,
                    precision=1 if args.precision == "mixed" else 0,
                    fp64_threshold=args.fp64_threshold)
     stream = torch.cuda.current_stream(device)
@@ -243,7 +245,7 @@ def run_ours(args, rank, world):
                config={"workload": WORKLOADS[args.workload][0], "particles": w.n, "cells": w.ngen,
                        "pseudo_particles": out["npseudo"] if pseudo else None, "pairs_per_step": out["npairs"],
                        "theta": args.theta, "r_part": w.params["r_part"], "r_leaf": w.params["r_leaf"],
-                       "precision": args.precision, "fp64_threshold": args.fp64_threshold,
+                       "precision": args.precision, "fp64_threshold": args.fp64_threshold, "h_tol": args.h_tol,
                        "l2": "flushed between steps (258 MiB write)", "parallelism": f"replicas x{world}"},
                map_exact_ms=statistics.mean(t_map), map_exact_pairs_per_s=out["npairs"] / (statistics.mean(t_map) * 1e-3),
                accuracy=acc, gpu_launches=launches, clocks=ck)

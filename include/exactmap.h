@@ -63,7 +63,9 @@ typedef struct {
     int knn_k;              /* build_voronoi: neighbours staged per generator before the exact fallback; default 48 */
     int leaf_max;           /* build_tree: particles per leaf; default 8 */
     int block_pairs;        /* map_exact: threads per block of the FP64 kernels, one pair per warp (32..128, a multiple of 32; 0 = 128) */
-    int reserved[5];
+    int h0_above;           /* make_pseudo_particles: with more pseudo-particles than this, every node takes h_0 (Eq. 11) and
+                               the neighbour search and solver are skipped (Section 2.4.2; the paper uses 10^6); 0 = never */
+    int reserved[4];
 } em_params;
 
 void em_params_default(em_params *p);
@@ -126,7 +128,11 @@ int tree_destroy(em_tree *t);
  *   d_h_particle: n particle smoothing lengths (device, original order)
  *   h_src: nsrc source positions (host, xyz interleaved), nsrc >= 1
  * Pseudo-particles are ordered by their first constituent in Morton order.
- * Returns EM_ENOTCONV (with outputs valid) when some solve fell back to h_0. */
+ * With p->h0_above > 0 and more than p->h0_above pseudo-particles (nodes and
+ * extracted particles together), no node is solved: each takes h_0 with
+ * status 2 (Section 2.4.2).
+ * Returns EM_ENOTCONV (with outputs valid) when some solve fell back to h_0;
+ * EM_OK when every node took h_0 through h0_above. */
 int make_pseudo_particles(em_ctx *ctx, const em_tree *t, const double *d_h_particle, int nsrc,
                           const double *h_src, const em_params *p, em_pseudo **out);
 /* The adaptive refinement of Section 2.4.1 (Eq. 5).  make_pseudo_particles_

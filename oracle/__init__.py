@@ -497,9 +497,12 @@ class Pseudo:
 
 def make_pseudo_particles(x, y, z, m, h_particle, box, sources, r_part, r_leaf, theta,
                           h_fact=1.2, tol=1e-13, max_newton=50, leaf_max=8, nthreads=None,
-                          solve=True, force=None):
+                          solve=True, force=None, h0_above=0):
     """Tree build, adaptive tree-walk and node h-solver (Sections 2.2, 2.4);
-    force: per-node refinement flags (see select)."""
+    force: per-node refinement flags (see select).  With h0_above > 0 and
+    more pseudo-particles than that (nodes and extracted particles), every
+    node takes h_0 of Eq. 11 (status 2) without the neighbour search, as
+    Section 2.4.2 does above 10^6 pseudo-particles."""
     t = build_tree(x, y, z, m, box, leaf_max)
     sel = select(t, sources, r_part, r_leaf, theta, force)
     x, y, z, m = (np.asarray(a, dtype=np.float64) for a in (x, y, z, m))
@@ -520,7 +523,10 @@ def make_pseudo_particles(x, y, z, m, h_particle, box, sources, r_part, r_leaf, 
     ph[~isn] = hp[parts]
     org[~isn] = -(parts + 1)
     first[~isn], cnt[~isn] = sel.ref[~isn], 1
-    if solve and nodes.shape[0]:
+    if h0_above > 0 and n > h0_above and nodes.shape[0]:
+        ph[isn] = h_initial(t, nodes, hp, h_fact)
+        st[isn] = 2
+    elif solve and nodes.shape[0]:
         h0 = h_initial(t, nodes, hp, h_fact)
         hh, s, _ = h_solve(t.com[sel.pop_node], t.com[nodes], h0, h_fact, tol, max_newton,
                            nthreads)

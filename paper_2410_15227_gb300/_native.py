@@ -20,7 +20,8 @@ class EmParams(C.Structure):
     _fields_ = [("r_part", C.c_double), ("r_leaf", C.c_double), ("theta", C.c_double),
                 ("h_fact", C.c_double), ("h_tol", C.c_double), ("max_newton", C.c_int),
                 ("precision", C.c_int), ("fp64_threshold", C.c_double), ("knn_k", C.c_int),
-                ("leaf_max", C.c_int), ("block_pairs", C.c_int), ("reserved", C.c_int * 5)]
+                ("leaf_max", C.c_int), ("block_pairs", C.c_int), ("h0_above", C.c_int),
+                ("reserved", C.c_int * 4)]
 
 
 P = C.c_void_p

@@ -29,6 +29,7 @@ class Params:
     knn_k: int = 48
     leaf_max: int = 8
     block_pairs: int = 0
+    h0_above: int = 0             # > 0: with more pseudo-particles than this, every node takes h_0 (Eq. 11)
 
     def native(self) -> N.EmParams:
         p = N.EmParams()

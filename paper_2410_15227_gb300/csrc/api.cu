@@ -62,6 +62,7 @@ EM_EXPORT void em_params_default(em_params *p)
     p->knn_k = 48;
     p->leaf_max = 8;
     p->block_pairs = 0;
+    p->h0_above = 0;
 }
 
 EM_EXPORT int em_ctx_create(em_ctx **ctx, int device, void *stream)

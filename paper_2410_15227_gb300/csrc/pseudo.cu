@@ -93,8 +93,8 @@ __global__ void k_emit(int64_t n, const int32_t *__restrict__ start, const int32
                        double *__restrict__ px, double *__restrict__ py, double *__restrict__ pz,
                        double *__restrict__ ph, double *__restrict__ pm, int64_t *__restrict__ origin,
                        int32_t *__restrict__ pfirst, int32_t *__restrict__ pcount, int32_t *__restrict__ status,
-                       int32_t *__restrict__ pnode, double *__restrict__ popx, double *__restrict__ popy,
-                       double *__restrict__ popz)
+                       int32_t *__restrict__ pnode, int32_t node_status, double *__restrict__ popx,
+                       double *__restrict__ popy, double *__restrict__ popz)
 {
     int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     if (k >= n) return;
@@ -110,7 +110,7 @@ __global__ void k_emit(int64_t n, const int32_t *__restrict__ start, const int32
             pfirst[q] = first[a];
             pcount[q] = count[a];
             pnode[q] = a;
-            status[q] = -1;   // to be solved
+            status[q] = node_status;   // -1: to be solved; 2: takes h_0 without a solve
             // h_0 = h_fact (2 s_node) (Eq. 11); a one-particle node starts from its particle's h
             ph[q] = (count[a] == 1 || size[a] == 0.0) ? hpart[perm[first[a]]] : (2.0 * h_fact) * size[a];
         } else {
@@ -406,6 +406,9 @@ static int pseudo_impl(em_ctx *ctx, const em_tree *t, const double *d_hp, int ns
     const int64_t np = (int64_t)h4[0] + h4[1], npop = (int64_t)h4[2] + h4[3];
     ps->n = np;
     ps->npop = npop;
+    // more pseudo-particles than h0_above: every node keeps h_0, no neighbour
+    // search and no solve (Section 2.4.2)
+    const bool bypass = p->h0_above > 0 && np > (int64_t)p->h0_above;
     DevArena &m = ps->mem;
     EM_TRY(m.alloc(&ps->x, np));
     EM_TRY(m.alloc(&ps->y, np));
@@ -424,17 +427,18 @@ static int pseudo_impl(em_ctx *ctx, const em_tree *t, const double *d_hp, int ns
     k_emit<<<em_grid(n, 256), 256, 0, st>>>(n, start, pidx, owner, popstart, popidx, t->label, t->first, t->count,
                                             t->mass, t->cx, t->cy, t->cz, t->size, t->xs, t->ys, t->zs, t->ms,
                                             t->perm, d_hp, p->h_fact, ps->x, ps->y, ps->z, ps->h, ps->m, ps->origin,
-                                            ps->first, ps->count, ps->status, ps->node, qx, qy, qz);
+                                            ps->first, ps->count, ps->status, ps->node, bypass ? 2 : -1, qx, qy,
+                                            qz);
     EM_LAUNCHED(ctx);
-    em::ChunkTree T;
-    EM_TRY(em_chunk_tree_build(ctx, tmp, npop, qx, qy, qz, nullptr, 0.0, &T));
-    double ext = 0.0;
-    for (int k = 0; k < 6; ++k) ext = fmax(ext, fabs(t->box[k]));
-    // float rounding of positions and boxes: widen the search radius
-    const float margin = (float)(4e-7 * (ext + 1.0));
-    if (np) {
-        k_h_solve<<<em_grid(np * 32, 32 * HS_WARPS), 32 * HS_WARPS, 0, st>>>(np, T, qx, qy, qz, ps->x, ps->y, ps->z, p->h_fact, p->h_tol,
-                                                          p->max_newton, margin, ps->h, ps->status);
+    if (np && !bypass) {
+        em::ChunkTree T;
+        EM_TRY(em_chunk_tree_build(ctx, tmp, npop, qx, qy, qz, nullptr, 0.0, &T));
+        double ext = 0.0;
+        for (int k = 0; k < 6; ++k) ext = fmax(ext, fabs(t->box[k]));
+        // float rounding of positions and boxes: widen the search radius
+        const float margin = (float)(4e-7 * (ext + 1.0));
+        k_h_solve<<<em_grid(np * 32, 32 * HS_WARPS), 32 * HS_WARPS, 0, st>>>(
+            np, T, qx, qy, qz, ps->x, ps->y, ps->z, p->h_fact, p->h_tol, p->max_newton, margin, ps->h, ps->status);
         EM_LAUNCHED(ctx);
     }
     unsigned long long *cnt;
@@ -457,7 +461,7 @@ static int make_pseudo(em_ctx *ctx, const em_tree *t, const double *d_h_particle
     EM_CHECK_ARG(ctx && t && d_h_particle && h_src && p && out);
     EM_CHECK_ARG(nsrc >= 1 && nsrc <= 4096);
     EM_CHECK_ARG(p->theta >= 0.0 && p->r_part >= 0.0 && p->r_leaf >= 0.0 && p->h_fact > 0.0);
-    EM_CHECK_ARG(p->h_tol > 0.0 && p->max_newton >= 0);
+    EM_CHECK_ARG(p->h_tol > 0.0 && p->max_newton >= 0 && p->h0_above >= 0);
     *out = nullptr;
     em_pseudo *ps = new em_pseudo(ctx->stream);
     ps->device = ctx->device;
@@ -468,7 +472,8 @@ static int make_pseudo(em_ctx *ctx, const em_tree *t, const double *d_h_particle
         return rc;
     }
     *out = ps;
-    return ps->nstatus[2] ? EM_ENOTCONV : EM_OK;
+    const bool bypass = p->h0_above > 0 && ps->n > (int64_t)p->h0_above;
+    return ps->nstatus[2] && !bypass ? EM_ENOTCONV : EM_OK;
 }
 
 EM_EXPORT int make_pseudo_particles(em_ctx *ctx, const em_tree *t, const double *d_h_particle, int nsrc,

@@ -91,3 +91,43 @@ def test_pseudo_mass_conservation(ctx):
         cover[f:f + c] += 1
     assert torch.all(cover == 1)
     assert abs(g["m"].sum().item() - w.m.sum()) < 1e-13
+
+
+def test_pseudo_h0_bypass(ctx, orc):
+    """Above h0_above pseudo-particles every node takes h_0 (Eq. 11), bit for
+    bit with the oracle, with status 2 and no solve (Section 2.4.2)."""
+    w = CLOUDS["sphere"]
+    src = np.zeros((1, 3))
+    tg = api.build_tree(ctx, dev(w.x), dev(w.y), dev(w.z), dev(w.m), w.box, 8)
+    pg = api.make_pseudo_particles(ctx, tg, dev(w.h), src, api.Params(theta=0.3))
+    n, _ = pg.info()
+    ps_o, _, _ = orc.make_pseudo_particles(w.x, w.y, w.z, w.m, w.h, w.box, src, 0.05, 0.1, 0.3, h0_above=n - 1)
+    before = ctx.launches
+    pb = api.make_pseudo_particles(ctx, tg, dev(w.h), src, api.Params(theta=0.3, h0_above=n - 1))
+    nlaunch = ctx.launches - before
+    g = {k: v.cpu().numpy() for k, v in pb.get().items()}
+    assert np.array_equal(g["origin"], ps_o.origin)
+    assert np.array_equal(g["h"], ps_o.h) and np.array_equal(g["status"], ps_o.status)
+    nb, st = pb.info()
+    assert nb == n and st[0] == 0 and st[1] == 0 and st[2] + st[3] == n
+    # at exactly h0_above the solver runs as without it
+    pn = api.make_pseudo_particles(ctx, tg, dev(w.h), src, api.Params(theta=0.3, h0_above=n))
+    assert torch.equal(pn.get()["h"], pg.get()["h"])
+    assert ctx.launches - before - nlaunch > nlaunch   # the solve launches more kernels
+
+
+@pytest.mark.parametrize("theta", [0.2, 0.5])
+def test_pseudo_h_paper_tolerance(ctx, orc, theta):
+    """The paper's Newton tolerance |dh|/h_0 < 1e-2 (Section 2.4.2): the same
+    iterates on both sides, so the same h to rounding and the same status."""
+    w = CLOUDS["sphere"]
+    src = np.zeros((1, 3))
+    ps_o, _, _ = orc.make_pseudo_particles(w.x, w.y, w.z, w.m, w.h, w.box, src, 0.05, 0.1, theta,
+                                           h_fact=1.2, tol=1e-2)
+    tg = api.build_tree(ctx, dev(w.x), dev(w.y), dev(w.z), dev(w.m), w.box, 8)
+    pg = api.make_pseudo_particles(ctx, tg, dev(w.h), src, api.Params(theta=theta, h_tol=1e-2))
+    g = {k: v.cpu().numpy() for k, v in pg.get().items()}
+    assert np.array_equal(g["origin"], ps_o.origin)
+    assert np.array_equal(g["status"], ps_o.status)
+    rel = np.abs(g["h"] / ps_o.h - 1)
+    assert np.all(rel[g["status"] <= 1] < 1e-12), rel.max()

@@ -198,3 +198,28 @@ def test_map_back_constant_and_linear(orc):
     a = orc.map_back(pairs, wts, 2 * f1 - 3 * f2, w.n)
     b = 2 * orc.map_back(pairs, wts, f1, w.n) - 3 * orc.map_back(pairs, wts, f2, w.n)
     assert np.max(np.abs(a - b)) < 1e-13
+
+
+def test_h0_bypass(orc, cloud):
+    """Above h0_above pseudo-particles no node is solved: each keeps h_0 of
+    Eq. 11, 2 h_fact s_node (a one-particle node its particle's h), with
+    status 2 (Section 2.4.2); at exactly h0_above the solver still runs."""
+    w = cloud
+    args = (w.x, w.y, w.z, w.m, w.h, w.box, np.zeros((1, 3)), 0.05, 0.1, 0.5)
+    ps, t, sel = orc.make_pseudo_particles(*args)
+    n = ps.n
+    pb, _, selb = orc.make_pseudo_particles(*args, h0_above=n - 1)
+    assert np.array_equal(selb.kind, sel.kind) and np.array_equal(selb.ref, sel.ref)
+    isn = sel.kind == 0
+    nodes = sel.ref[isn]
+    multi = (t.count[nodes] > 1) & (t.size[nodes] > 0)
+    assert multi.sum() > 10
+    assert np.array_equal(pb.h[isn][multi], 2 * 1.2 * t.size[nodes][multi])
+    one = t.count[nodes] == 1
+    assert np.array_equal(pb.h[isn][one], w.h[t.perm[t.first[nodes[one]]]])
+    assert np.all(pb.status[isn] == 2) and np.all(pb.status[~isn] == 3)
+    assert np.array_equal(pb.h[~isn], ps.h[~isn])
+    # the solved h differ from h_0: the bypass is not a no-op
+    assert np.mean(np.abs(ps.h[isn][multi] / pb.h[isn][multi] - 1) > 1e-3) > 0.5
+    pn, _, _ = orc.make_pseudo_particles(*args, h0_above=n)
+    assert np.array_equal(pn.h, ps.h) and np.array_equal(pn.status, ps.status)
