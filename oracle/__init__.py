@@ -17,6 +17,8 @@ What it computes, by the paper's sections and equations:
   (Section 2.4.1, Eq. 4), node h-solver (Section 2.4.2, Eqs. 6-11), inverse
   mapping f_i = sum_j w_ij f_j / sum_j w_ij and constituent inheritance
   (Section 2.3 and Section 2.5).
+* Cell centroids and Lloyd's iteration on the sites (Section 2.3); the
+  adaptive refinement of the tree-walk (Section 2.4.1, Eq. 5).
 
 Parity pins live in ``tests/test_oracle_*.py``.
 """
@@ -533,6 +535,50 @@ def make_pseudo_particles(x, y, z, m, h_particle, box, sources, r_part, r_leaf, 
         ph[isn] = hh
         st[isn] = s
     return Pseudo(px, py, pz, ph, pm, org, first, cnt, st), t, sel
+
+
+# ---------------------------------------------------------------------------
+# Lloyd regularisation of the sites (Section 2.3)
+# ---------------------------------------------------------------------------
+
+def cell_centroids(cells: Cells):
+    """Centroid c_j = (1/V_j) integral over V_j of r d^3r of every stored cell,
+    and the volume V_j, from the cell's faces.  Each face is fanned into
+    triangles (v_0, v_k, v_k+1); each triangle with the generator g spans a
+    tetrahedron of signed volume a.(b x c)/6 (a, b, c its corners relative
+    to g) and centroid g + (a + b + c)/4.  The tetrahedra tile the convex
+    cell, so the volume-weighted mean of their centroids is the cell's."""
+    nc = cells.ncell
+    cen = np.zeros((nc, 3))
+    vol = np.zeros(nc)
+    for j in range(nc):
+        g = cells.gen[j]
+        m1 = np.zeros(3)
+        v6 = 0.0
+        for verts, _, _ in cells.faces(j):
+            a = verts[0] - g
+            for k in range(1, verts.shape[0] - 1):
+                b = verts[k] - g
+                c = verts[k + 1] - g
+                t6 = float(np.dot(a, np.cross(b, c)))
+                v6 += t6
+                m1 += t6 * (a + b + c)
+        vol[j] = v6 / 6.0
+        cen[j] = g + m1 / (4.0 * v6)
+    return cen, vol
+
+
+def lloyd(gx, gy, gz, box, iters=5, nthreads=None):
+    """Lloyd's iteration (Section 2.3 applies five before the mapping): build
+    the Voronoi cells clipped to the box and move every site to its cell's
+    centroid, iters times.  Returns the sites after the last move."""
+    g = np.stack([_f64(gx), _f64(gy), _f64(gz)], axis=1)
+    for _ in range(iters):
+        cells = voronoi(g[:, 0], g[:, 1], g[:, 2], box, nthreads=nthreads)
+        cen, _ = cell_centroids(cells)
+        g = np.empty_like(g)
+        g[cells.cell_ids] = cen
+    return g[:, 0].copy(), g[:, 1].copy(), g[:, 2].copy()
 
 
 # ---------------------------------------------------------------------------
