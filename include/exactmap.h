@@ -191,6 +191,18 @@ int voronoi_from_cells(em_ctx *ctx, int64_t ncell, int64_t nface, int64_t nfv, c
                        const int64_t *d_cell_face_off, const int64_t *d_face_vert_off,
                        const double *d_verts, const double *d_normals, const int64_t *d_nbr,
                        const double *d_volume, em_voronoi **out);
+/* Centroid of every cell, (1/V_j) times the integral of r over cell j: the
+ * move of Lloyd's iteration (Section 2.3).  d_cx, d_cy, d_cz: ncell doubles
+ * each (device, caller-owned), in generator order.  Enqueued, no sync. */
+int voronoi_centroids(em_ctx *ctx, const em_voronoi *v, double *d_cx, double *d_cy, double *d_cz);
+/* Lloyd's iteration on the sites (Section 2.3 applies five before the
+ * mapping): iters times, build the cells of the sites clipped to h_box and
+ * move every site to its cell's centroid.  d_gx, d_gy, d_gz (device, in/out,
+ * ngen each) hold the sites; p as for build_voronoi (knn_k).  Errors as for
+ * build_voronoi (EM_EINVAL for coincident sites or a site outside the box);
+ * on an error the sites hold the last completed move.  iters = 0 is a no-op. */
+int lloyd(em_ctx *ctx, int64_t ngen, double *d_gx, double *d_gy, double *d_gz, const double *h_box, int iters,
+          const em_params *p);
 int voronoi_info(const em_voronoi *v, int64_t *ncell, int64_t *nface, int64_t *nfv);
 /* Copy out in the same layout as voronoi_from_cells (any may be NULL). */
 int voronoi_get(em_ctx *ctx, const em_voronoi *v, int64_t *d_cell_face_off, int64_t *d_face_vert_off,

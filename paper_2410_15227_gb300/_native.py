@@ -56,6 +56,8 @@ SIGNATURES = {
     "build_voronoi": (I32, [P, I64, P, P, P, P, PPAR, PP]),
     "voronoi_from_cells": (I32, [P, I64, I64, I64, P, P, P, P, P, P, P, PP]),
     "voronoi_info": (I32, [P, PI64, PI64, PI64]),
+    "voronoi_centroids": (I32, [P, P, P, P, P]),
+    "lloyd": (I32, [P, I64, P, P, P, P, I32, PPAR]),
     "voronoi_get": (I32, [P, P] + [P] * 6),
     "voronoi_destroy": (I32, [P]),
     "find_pairs": (I32, [P, I64, P, P, P, P, P, PP, PI64]),

@@ -285,6 +285,26 @@ def build_voronoi(ctx: Context, gx, gy, gz, box, params: Params | None = None) -
     return Voronoi(ctx, h)
 
 
+def voronoi_centroids(ctx: Context, vor: Voronoi):
+    """Centroid of every cell (Section 2.3, the move of Lloyd's iteration),
+    as three device tensors in generator order."""
+    nc, _, _ = vor.info()
+    cx, cy, cz = ctx.empty(nc), ctx.empty(nc), ctx.empty(nc)
+    N.call("voronoi_centroids", ctx.handle, vor.handle, _ptr(cx, f64, nc), _ptr(cy, f64, nc), _ptr(cz, f64, nc))
+    return cx, cy, cz
+
+
+def lloyd(ctx: Context, gx, gy, gz, box, iters: int = 5, params: Params | None = None):
+    """Lloyd's iteration on the sites (Section 2.3: five before the mapping),
+    in place on the device tensors gx, gy, gz, which are returned."""
+    n = gx.numel()
+    p = (params or Params()).native()
+    bp, _keep = _box(box)
+    N.call("lloyd", ctx.handle, n, _ptr(gx, f64, n, "gx"), _ptr(gy, f64, n, "gy"), _ptr(gz, f64, n, "gz"),
+           bp, int(iters), C.byref(p))
+    return gx, gy, gz
+
+
 def voronoi_from_cells(ctx: Context, gen, cell_face_off, face_vert_off, verts, normals, nbr,
                        volume) -> Voronoi:
     nc = cell_face_off.numel() - 1

@@ -181,10 +181,56 @@ __global__ void k_finish_offsets(int64_t *face_vert_off, int64_t nface, int64_t 
     face_vert_off[nface] = nfv;
 }
 
+// Centroid of every cell, the move of Lloyd's iteration (Section 2.3).  One
+// warp per cell, lanes over its faces; a face is fanned into triangles
+// (v_0, v_k, v_k+1), and each triangle with the generator g spans a
+// tetrahedron of signed volume a.(b x c)/6 (corners relative to g) and
+// centroid g + (a + b + c)/4.  The warp sums the volume-weighted centroids
+// in a fixed butterfly order.
+__global__ void k_cell_centroid(int64_t ncell, const double *__restrict__ gen, const int64_t *__restrict__ cfo,
+                                const int64_t *__restrict__ fvo, const double *__restrict__ verts,
+                                double *__restrict__ cx, double *__restrict__ cy, double *__restrict__ cz)
+{
+    const int64_t j = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
+    const int lane = threadIdx.x & 31;
+    if (j >= ncell) return;   // whole warps leave together
+    const double gx = gen[3 * j], gy = gen[3 * j + 1], gz = gen[3 * j + 2];
+    double v6 = 0.0, mx = 0.0, my = 0.0, mz = 0.0;
+    for (int64_t f = cfo[j] + lane; f < cfo[j + 1]; f += 32) {
+        const int64_t k0 = fvo[f], k1 = fvo[f + 1];
+        const double ax = verts[3 * k0] - gx, ay = verts[3 * k0 + 1] - gy, az = verts[3 * k0 + 2] - gz;
+        double bx = verts[3 * k0 + 3] - gx, by = verts[3 * k0 + 4] - gy, bz = verts[3 * k0 + 5] - gz;
+        for (int64_t k = k0 + 2; k < k1; ++k) {
+            const double ex = verts[3 * k] - gx, ey = verts[3 * k + 1] - gy, ez = verts[3 * k + 2] - gz;
+            const double t6 = ax * (by * ez - bz * ey) + ay * (bz * ex - bx * ez) + az * (bx * ey - by * ex);
+            v6 += t6;
+            mx += t6 * (ax + bx + ex);
+            my += t6 * (ay + by + ey);
+            mz += t6 * (az + bz + ez);
+            bx = ex;
+            by = ey;
+            bz = ez;
+        }
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        v6 += __shfl_xor_sync(0xffffffffu, v6, o);
+        mx += __shfl_xor_sync(0xffffffffu, mx, o);
+        my += __shfl_xor_sync(0xffffffffu, my, o);
+        mz += __shfl_xor_sync(0xffffffffu, mz, o);
+    }
+    if (lane == 0) {
+        const double s = 1.0 / (4.0 * v6);
+        cx[j] = gx + mx * s;
+        cy[j] = gy + my * s;
+        cz[j] = gz + mz * s;
+    }
+}
+
 }  // namespace
 
 static int voronoi_impl(em_ctx *ctx, int64_t ngen, const double *gx, const double *gy, const double *gz,
-                        const em_params *p, em_voronoi *v)
+                        const em_params *p, em_voronoi *v, bool prepare = true)
 {
     cudaStream_t st = ctx->stream;
     DevArena tmp(st, true);
@@ -272,7 +318,7 @@ static int voronoi_impl(em_ctx *ctx, int64_t ngen, const double *gx, const doubl
     EM_LAUNCHED(ctx);
     k_finish_offsets<<<1, 1, 0, st>>>(v->face_vert_off, v->nface, v->nfv);
     EM_LAUNCHED(ctx);
-    return em_prepare_cells(ctx, v);
+    return prepare ? em_prepare_cells(ctx, v) : EM_OK;
 }
 
 EM_EXPORT int build_voronoi(em_ctx *ctx, int64_t ngen, const double *d_gx, const double *d_gy, const double *d_gz,
@@ -292,5 +338,36 @@ EM_EXPORT int build_voronoi(em_ctx *ctx, int64_t ngen, const double *d_gx, const
         return rc;
     }
     *out = v;
+    return EM_OK;
+}
+
+EM_EXPORT int voronoi_centroids(em_ctx *ctx, const em_voronoi *v, double *d_cx, double *d_cy, double *d_cz)
+{
+    EM_CHECK_ARG(ctx && v && d_cx && d_cy && d_cz);
+    if (v->ncell == 0) return EM_OK;
+    k_cell_centroid<<<em_grid(v->ncell * 32, 256), 256, 0, ctx->stream>>>(v->ncell, v->gen, v->cell_face_off,
+                                                                         v->face_vert_off, v->verts, d_cx, d_cy,
+                                                                         d_cz);
+    EM_LAUNCHED(ctx);
+    return EM_OK;
+}
+
+EM_EXPORT int lloyd(em_ctx *ctx, int64_t ngen, double *d_gx, double *d_gy, double *d_gz, const double *h_box,
+                    int iters, const em_params *p)
+{
+    EM_CHECK_ARG(ctx && h_box && p && d_gx && d_gy && d_gz);
+    EM_CHECK_ARG(ngen >= 1 && ngen < INT32_MAX && iters >= 0);
+    EM_CHECK_ARG(h_box[1] > h_box[0] && h_box[3] > h_box[2] && h_box[5] > h_box[4]);
+    for (int it = 0; it < iters; ++it) {
+        // the cells only (no derived geometry for the mapping), then the move;
+        // the cell records are freed in stream order after the move
+        em_voronoi v(ctx->stream);
+        v.device = ctx->device;
+        for (int k = 0; k < 6; ++k) v.box[k] = h_box[k];
+        int rc = voronoi_impl(ctx, ngen, d_gx, d_gy, d_gz, p, &v, false);
+        if (rc == EM_OK) rc = voronoi_centroids(ctx, &v, d_gx, d_gy, d_gz);
+        v.mem.release();
+        if (rc) return rc;
+    }
     return EM_OK;
 }

@@ -311,7 +311,7 @@ __device__ int gather(WCell &c, const em::ChunkTree &T, const double *__restrict
     // are checked in FP64.
     const float gxf = (float)gx, gyf = (float)gy, gzf = (float)gz;
     const float gabs = fabsf(gxf) + fabsf(gyf) + fabsf(gzf);
-    const float rhi = sqrtf((float)hi2) * (1.f + 1e-5f) + 1e-5f * gabs;
+    float rhi = sqrtf((float)hi2) * (1.f + 1e-5f) + 1e-5f * gabs;
     const float rlo = lo2 > 0.0 ? sqrtf((float)lo2) * (1.f - 1e-5f) - 1e-5f * gabs : -1.f;
     const float rtiny = 1e-5f * (gabs + rhi);
     em::warp_traverse(T, gxf, gyf, gzf, R * R, INT64_MAX, [&](int64_t k, bool valid) {
@@ -378,12 +378,17 @@ __device__ void sort_cand(WCell &c, int n)
 
 // Generators k != s whose bisector cuts the current cell (some vertex v has
 // f = r_k.v - |r_k|^2/2 > 0, r_k = g_k - g), excluding those nearer than
-// sqrt(skip2) (already applied).  Boxes are skipped when every vertex is at
-// least as close to the site as to the box.  Returns the count, -1 if it
-// exceeds WCAND (the first WCAND found are kept).
+// sqrt(skip2) (already applied), up to the window's end hi2.  Boxes are
+// skipped when every vertex is at least as close to the site as to the box.
+// When the list would overflow, the walk keeps the candidates whose FP32 key
+// is below the median key k and goes on with hi2 narrowed to the float p just
+// below k: every generator with d2 < p has a key <= p, so none is lost, and a
+// kept one a little beyond p is only applied early (the half-spaces commute;
+// once applied it no longer cuts).  Returns the count with hi2 the window
+// actually covered, or -1 if the window cannot narrow (ties at the median).
 __device__ int gather_cutting(WCell &c, const em::ChunkTree &T, const double *__restrict__ xs,
                               const double *__restrict__ ys, const double *__restrict__ zs, int64_t s, double gx,
-                              double gy, double gz, double skip2, double hi2)
+                              double gy, double gz, double skip2, double &hi2)
 {
     const int lane = threadIdx.x & 31;
     const int cur = c.cur, nt = c.nt;
@@ -392,7 +397,7 @@ __device__ int gather_cutting(WCell &c, const em::ChunkTree &T, const double *__
     // dropped only where the exact test would drop it too.
     const float gxf = (float)gx, gyf = (float)gy, gzf = (float)gz;
     const float gabs = fabsf(gxf) + fabsf(gyf) + fabsf(gzf);
-    const float rhi = sqrtf((float)hi2) * (1.f + 1e-5f) + 1e-5f * gabs;
+    float rhi = sqrtf((float)hi2) * (1.f + 1e-5f) + 1e-5f * gabs;
     const float rlo = skip2 > 0.0 ? sqrtf((float)skip2) * (1.f - 1e-5f) - 1e-5f * gabs : -1.f;
     auto box_can_cut = [&](const float4 lo, const float4 hi) -> bool {
         const float babs = fabsf(lo.x) + fabsf(lo.y) + fabsf(lo.z) + fabsf(hi.x) + fabsf(hi.y) + fabsf(hi.z);
@@ -481,6 +486,24 @@ __device__ int gather_cutting(WCell &c, const em::ChunkTree &T, const double *__
                 if (__any_sync(0xffffffffu, beyond) && lane == src) hit = true;
             }
             unsigned m = __ballot_sync(0xffffffffu, hit);
+            if (n + __popc(m) > WCAND) {
+                // narrow the window to the nearer half of the list (n <= WCAND here)
+                sort_cand(c, n);
+                const float kth = c.cd2[n / 2];
+                const float pf = nextafterf(kth, 0.f);
+                const double p2 = (double)pf;
+                int keep = 0;   // the sorted prefix below the median key
+                for (int b = 0; b < n; b += 32) {
+                    const int i = b + lane;
+                    keep += __popc(__ballot_sync(0xffffffffu, i < n && c.cd2[i] < kth));
+                }
+                if (!(kth > 0.f) || !(p2 > skip2) || !(p2 < hi2) || keep == 0) return -1;
+                n = keep;
+                hi2 = p2;
+                rhi = sqrtf(pf) * (1.f + 1e-5f) + 1e-5f * gabs;
+                hit = hit && d2 < hi2;
+                m = __ballot_sync(0xffffffffu, hit);
+            }
             if (hit) {
                 int pos = n + __popc(m & lanemask_lt());
                 if (pos < WCAND) {
