@@ -29,6 +29,7 @@ METRIC = "particle-cell pairs mapped/s (mixed vs FP64) at stated max rel. err; %
 WORKLOADS = {
     "pseudo_1e6": ("pseudo_1M_particles_262k_cells", True),
     "sphere_1e5": ("sphere_100k_particles_25k_cells", False),
+    "batched_64": ("batched_64_snapshots", True),
 }
 # pseudo-particle selection: r_part, r_leaf from the paper's Table 1 runs; theta
 # chosen so that the cloud yields about 1e5 pseudo-particles (102,908)
@@ -44,7 +45,9 @@ def parse():
     ap.add_argument("--impl", choices=("ours", "reference"), default="ours")
     ap.add_argument("--workload", choices=tuple(WORKLOADS), default="pseudo_1e6",
                     help="pseudo_1e6: 1e6-particle cloud through the tree and pseudo-particles (the "
-                         "benchmark); sphere_1e5: 1e5 particles mapped directly (smaller case)")
+                         "benchmark); sphere_1e5: 1e5 particles mapped directly (smaller case); "
+                         "batched_64: 64 independent snapshots of 1e3-1e5 particles through map_batch")
+    ap.add_argument("--workers", type=int, default=8, help="batched_64: host threads (streams) of map_batch")
     ap.add_argument("--precision", choices=("mixed", "fp64"), default="mixed")
     ap.add_argument("--theta", type=float, default=THETA)
     ap.add_argument("--fp64-threshold", type=float, default=1e-5)
@@ -258,6 +261,71 @@ def run_ours(args, rank, world):
     return res
 
 
+def run_batched(args, rank, world):
+    """64 independent snapshots (N_s log-uniform in [1e3, 1e5], a quarter as
+    many sites) through map_batch, the whole path per snapshot.  The work
+    spans several streams and map_batch returns when all have finished, so a
+    step is timed by the host clock between two device synchronisations."""
+    import numpy as np
+    import torch
+
+    from paper_2410_15227_gb300 import api, inputs
+
+    dev_index = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(dev_index)
+    device = torch.device("cuda", dev_index)
+    ws = inputs.workload_batched()
+    dv = lambda a: torch.as_tensor(np.ascontiguousarray(a), dtype=torch.float64, device=device)
+    snaps = [dict(x=dv(w.x), y=dv(w.y), z=dv(w.z), m=dv(w.m), h=dv(w.h), gx=dv(w.gx), gy=dv(w.gy), gz=dv(w.gz),
+                  box=w.box, sources=np.zeros((1, 3)), f_cell=dv(np.random.default_rng([5, s]).random(w.ngen)))
+             for s, w in enumerate(ws)]
+    pp = inputs.PSEUDO_PARAMS
+    P = api.Params(r_part=pp["r_part"], r_leaf=pp["r_leaf"], theta=args.theta, h_fact=pp["h_fact"],
+                   h_tol=args.h_tol, precision=1 if args.precision == "mixed" else 0,
+                   fp64_threshold=args.fp64_threshold)
+    flush = torch.empty(2 * L2_BYTES // 8, dtype=torch.float64, device=device)
+
+    def step(nworkers):
+        flush.zero_()
+        torch.cuda.synchronize()
+        t = time.perf_counter()
+        res, launches = api.map_batch(dev_index, snaps, P, nworkers=nworkers)
+        torch.cuda.synchronize()
+        return (time.perf_counter() - t) * 1e3, sum(r["npairs"] for r in res), launches, res
+
+    for _ in range(args.warmup):
+        step(args.workers)
+    serial_ms = min(step(1)[0] for _ in range(2))
+    if world > 1:
+        torch.distributed.barrier()
+    torch.cuda.synchronize()
+    clocks = ClockSampler(dev_index)
+    clocks.start()
+    t_ms, npairs, launches = 0.0, 0, 0
+    for _ in range(args.steps):
+        ms, n, nl, res = step(args.workers)
+        t_ms += ms
+        npairs += n
+        launches += nl
+    if world > 1:
+        torch.distributed.barrier()
+    ck = clocks.stop()
+    tmax, units = reduce_over_ranks(t_ms, npairs, world, device)
+    per_step = npairs // args.steps
+    return dict(metric=METRIC, value=units / (tmax * 1e-3), unit="pairs/s", n_gpus=world, steps=args.steps,
+                warmup=args.warmup, ms_per_step=tmax / args.steps, higher_is_better=True, scaling="weak",
+                vs_baseline=None, dtype="f32+f64" if args.precision == "mixed" else "f64", data="synthetic",
+                config={"workload": WORKLOADS[args.workload][0], "snapshots": len(ws),
+                        "particles": int(sum(w.n for w in ws)), "cells": int(sum(w.ngen for w in ws)),
+                        "pseudo_particles": int(sum(r["npseudo"] for r in res)), "pairs_per_step": per_step,
+                        "theta": args.theta, "r_part": pp["r_part"], "r_leaf": pp["r_leaf"],
+                        "precision": args.precision, "fp64_threshold": args.fp64_threshold, "h_tol": args.h_tol,
+                        "workers": args.workers, "timing": "host clock between device syncs around map_batch",
+                        "l2": "flushed between steps (258 MiB write)", "parallelism": f"replicas x{world}"},
+                serial_ms_per_step=serial_ms, serial_pairs_per_s=per_step / (serial_ms * 1e-3),
+                gpu_launches=launches, clocks=ck, roofline=None, e2e=None, cpu_baseline=None)
+
+
 def reduce_over_ranks(t_ms, units, world, device):
     """Whole-job figures across ranks: the slowest rank's timed milliseconds
     and the units (pairs) all ranks processed.  One process per GPU; on one
@@ -449,6 +517,9 @@ def cpu_baseline(args, w):
 def run_reference(args, rank, world):
     if rank != 0:
         return None
+    if args.workload == "batched_64":
+        return {"impl": "reference", "unavailable": "the oracle arm times samples of one snapshot; "
+                                                    "batched_64 is measured against map_batch with one worker"}
     w = load_workload(args)
     pseudo = WORKLOADS[args.workload][1]
     parts, cells, pairs = oracle_sample(w, args.theta, pseudo=pseudo)
@@ -488,6 +559,14 @@ def main():
     if world > 1:
         import torch
         torch.distributed.init_process_group("nccl")
+    if args.workload == "batched_64":
+        res = run_batched(args, rank, world)
+        if rank == 0:
+            print(json.dumps(res))
+        if world > 1:
+            import torch
+            torch.distributed.destroy_process_group()
+        return
     res = run_ours(args, rank, world)
     if rank == 0:
         if not args.no_cpu_baseline:

@@ -288,6 +288,42 @@ int map_exact_noalloc(em_ctx *ctx, const em_pairs *pr, const double *d_x, const 
 int map_back(em_ctx *ctx, const em_pairs *pr, const double *d_w, const double *d_f_cell, double *d_f_out,
              const em_pseudo *ps, const em_tree *t, double *d_f_particle_out);
 
+/* ---- map_batch ------------------------------------------------------------------
+ * Many independent snapshots through the whole path: build_tree,
+ * make_pseudo_particles (a node that keeps h_0 is not an error here),
+ * build_voronoi, find_pairs, map_exact, and map_back when a cell field is
+ * given.  Same results, bit for bit, as those calls made one snapshot at a
+ * time with the same parameters.  Snapshots go to nworkers host threads
+ * (1..64), each with its own context on its own non-blocking stream on
+ * `device`, largest first (by n + ngen).  Returns when every snapshot has
+ * finished.
+ * Per snapshot (caller-owned; device arrays on `device`):
+ *   in:  n particles d_x, d_y, d_z, d_m, d_h; ngen sites d_gx, d_gy, d_gz;
+ *        box (as h_box of build_tree); nsrc sources h_src (host, xyz);
+ *        d_f_cell[ngen] or NULL
+ *   out: d_rho[ngen] cell densities; d_f[n] (original order, set iff
+ *        d_f_cell is) the cell field mapped back onto the particles;
+ *        npseudo, npairs, nfp64 (pairs recomputed in FP64); status (em_status,
+ *        -1 if the snapshot did not run)
+ * Returns EM_OK, or the first failing snapshot's status with its index in
+ * em_last_error().  *h_launches (may be NULL): kernels launched in all. */
+typedef struct {
+    int64_t n;
+    const double *d_x, *d_y, *d_z, *d_m, *d_h;
+    int64_t ngen;
+    const double *d_gx, *d_gy, *d_gz;
+    double box[6];
+    int nsrc;
+    const double *h_src;
+    const double *d_f_cell;
+    double *d_rho;
+    double *d_f;
+    int64_t npseudo, npairs, nfp64;
+    int status;
+} em_snapshot;
+
+int map_batch(int device, int nsnap, em_snapshot *snaps, const em_params *p, int nworkers, int64_t *h_launches);
+
 #ifdef __cplusplus
 }
 #endif

@@ -24,6 +24,14 @@ class EmParams(C.Structure):
                 ("reserved", C.c_int * 4)]
 
 
+class EmSnapshot(C.Structure):
+    _fields_ = [("n", C.c_int64), ("d_x", C.c_void_p), ("d_y", C.c_void_p), ("d_z", C.c_void_p),
+                ("d_m", C.c_void_p), ("d_h", C.c_void_p), ("ngen", C.c_int64), ("d_gx", C.c_void_p),
+                ("d_gy", C.c_void_p), ("d_gz", C.c_void_p), ("box", C.c_double * 6), ("nsrc", C.c_int),
+                ("h_src", C.c_void_p), ("d_f_cell", C.c_void_p), ("d_rho", C.c_void_p), ("d_f", C.c_void_p),
+                ("npseudo", C.c_int64), ("npairs", C.c_int64), ("nfp64", C.c_int64), ("status", C.c_int)]
+
+
 P = C.c_void_p
 PP = C.POINTER(C.c_void_p)
 I64 = C.c_int64
@@ -58,6 +66,7 @@ SIGNATURES = {
     "voronoi_info": (I32, [P, PI64, PI64, PI64]),
     "voronoi_centroids": (I32, [P, P, P, P, P]),
     "lloyd": (I32, [P, I64, P, P, P, P, I32, PPAR]),
+    "map_batch": (I32, [I32, I32, C.POINTER(EmSnapshot), PPAR, I32, PI64]),
     "voronoi_get": (I32, [P, P] + [P] * 6),
     "voronoi_destroy": (I32, [P]),
     "find_pairs": (I32, [P, I64, P, P, P, P, P, PP, PI64]),

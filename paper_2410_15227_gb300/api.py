@@ -305,6 +305,51 @@ def lloyd(ctx: Context, gx, gy, gz, box, iters: int = 5, params: Params | None =
     return gx, gy, gz
 
 
+def map_batch(device: int, snapshots, params: Params, nworkers: int = 4):
+    """Independent snapshots through the whole path (build_tree ... map_exact,
+    map_back when a cell field is given) on nworkers host threads with a
+    stream each.  snapshots: dicts with device tensors x, y, z, m, h, gx, gy,
+    gz, box (6 numbers), sources ((k, 3) numbers) and optionally f_cell.
+    Returns one dict per snapshot: rho, f (or None), npseudo, npairs, nfp64,
+    status, and the total kernel launches."""
+    n = len(snapshots)
+    arr = (N.EmSnapshot * max(n, 1))()
+    keep, outs = [], []
+    for k, sn in enumerate(snapshots):
+        x = sn["x"]
+        np_, ng = x.numel(), sn["gx"].numel()
+        dev = x.device
+        rho = torch.empty(ng, dtype=f64, device=dev)
+        f = torch.empty(np_, dtype=f64, device=dev) if sn.get("f_cell") is not None else None
+        src = [float(v) for v in torch.as_tensor(sn["sources"], dtype=f64).reshape(-1).tolist()]
+        hsrc = (C.c_double * len(src))(*src)
+        e = arr[k]
+        e.n, e.ngen = np_, ng
+        for name in ("x", "y", "z", "m", "h"):
+            setattr(e, "d_" + name, _ptr(sn[name], f64, np_, name))
+        for name in ("gx", "gy", "gz"):
+            setattr(e, "d_" + name, _ptr(sn[name], f64, ng, name))
+        for i, b in enumerate(sn["box"]):
+            e.box[i] = float(b)
+        e.nsrc = len(src) // 3
+        e.h_src = C.cast(hsrc, C.c_void_p)
+        e.d_f_cell = _ptr(sn.get("f_cell"), f64, ng, "f_cell")
+        e.d_rho = _ptr(rho, f64, ng)
+        e.d_f = _ptr(f, f64, np_) if f is not None else None
+        keep.append(hsrc)
+        outs.append((rho, f))
+    p = params.native()
+    launches = C.c_int64()
+    rc = N.lib().map_batch(int(device), n, arr, C.byref(p), int(nworkers), C.byref(launches))
+    res = [dict(rho=outs[k][0], f=outs[k][1], npseudo=arr[k].npseudo, npairs=arr[k].npairs,
+                nfp64=arr[k].nfp64, status=arr[k].status) for k in range(n)]
+    if rc != N.EM_OK:
+        err = N.NativeError("map_batch", rc, N.lib().em_last_error().decode(errors="replace"))
+        err.results = res   # the snapshots that did finish keep their outputs
+        raise err
+    return res, launches.value
+
+
 def voronoi_from_cells(ctx: Context, gen, cell_face_off, face_vert_off, verts, normals, nbr,
                        volume) -> Voronoi:
     nc = cell_face_off.numel() - 1
