@@ -30,7 +30,11 @@ WORKLOADS = {
     "pseudo_1e6": ("pseudo_1M_particles_262k_cells", True),
     "sphere_1e5": ("sphere_100k_particles_25k_cells", False),
     "batched_64": ("batched_64_snapshots", True),
+    "full_8m": ("full_8M_particles_2M_cells", True),
 }
+# workloads whose FP64 reference pass over every pair would take longer than
+# the timed steps: accuracy on a random sample of pairs instead
+ACCURACY_SAMPLE = {"full_8m": 2_000_000}
 # pseudo-particle selection: r_part, r_leaf from the paper's Table 1 runs; theta
 # chosen so that the cloud yields about 1e5 pseudo-particles (102,908)
 THETA = 0.065
@@ -46,7 +50,8 @@ def parse():
     ap.add_argument("--workload", choices=tuple(WORKLOADS), default="pseudo_1e6",
                     help="pseudo_1e6: 1e6-particle cloud through the tree and pseudo-particles (the "
                          "benchmark); sphere_1e5: 1e5 particles mapped directly (smaller case); "
-                         "batched_64: 64 independent snapshots of 1e3-1e5 particles through map_batch")
+                         "batched_64: 64 independent snapshots of 1e3-1e5 particles through map_batch; "
+                         "full_8m: 8e6 particles and 2e6 cells (accuracy on a pair sample)")
     ap.add_argument("--workers", type=int, default=8, help="batched_64: host threads (streams) of map_batch")
     ap.add_argument("--precision", choices=("mixed", "fp64"), default="mixed")
     ap.add_argument("--theta", type=float, default=THETA)
@@ -63,6 +68,9 @@ def load_workload(args):
     from paper_2410_15227_gb300 import inputs
     if args.workload == "pseudo_1e6":
         w = inputs.cached(inputs.workload_pseudo_1e6, cache_dir=args.cache)
+        w.params["theta"] = args.theta
+    elif args.workload == "full_8m":
+        w = inputs.cached(inputs.workload_full_8m, cache_dir=args.cache)
         w.params["theta"] = args.theta
     else:
         w = inputs.cached(inputs.workload_sphere_100k, cache_dir=args.cache)
@@ -183,7 +191,9 @@ def run_ours(args, rank, world):
 
     # accuracy of the mixed path against the FP64 path on the same pairs
     acc = {}
-    if args.precision == "mixed":
+    if args.precision == "mixed" and args.workload in ACCURACY_SAMPLE:
+        acc = sampled_accuracy(api, ctx, out, ACCURACY_SAMPLE[args.workload], device, [float(b) for b in w.box])
+    elif args.precision == "mixed":
         P64 = api.Params(precision=0)
         g = out["g"]
         w64, rho64, u64, _ = api.map_exact(ctx, out["pr"], g["x"], g["y"], g["z"], g["h"], g["m"],
@@ -326,6 +336,38 @@ def run_batched(args, rank, world):
                 gpu_launches=launches, clocks=ck, roofline=None, e2e=None, cpu_baseline=None)
 
 
+def sampled_accuracy(api, ctx, out, nsample, device, box, seed=11):
+    """Mixed against FP64 weights on a random sample of the pairs (a subset
+    of the (j, i)-sorted list stays sorted), and the partition of unity
+    sum_j w_ij = 1 over the pseudo-particles whose kernel lies inside the
+    box, for which it holds exactly."""
+    import torch
+    pr, g, vor = out["pr"], out["g"], out["vor"]
+    npairs, npseudo, _ = pr.info()
+    pp = pr.get()
+    gen = torch.Generator(device=device)
+    gen.manual_seed(seed)
+    k = min(nsample, npairs)
+    idx = torch.randperm(npairs, device=device, generator=gen)[:k].sort().values
+    sub = api.pairs_from_list(ctx, pp["pair_i"][idx].contiguous(), pp["pair_j"][idx].contiguous(), npseudo, vor)
+    del pp
+    w64, _, _, _ = api.map_exact(ctx, sub, g["x"], g["y"], g["z"], g["h"], g["m"], vor, api.Params(precision=0),
+                                 want_wsum=False)
+    wm = out["w"][idx]
+    inside = ((g["x"] - box[0]).minimum(box[1] - g["x"]).minimum(g["y"] - box[2]).minimum(box[3] - g["y"])
+              .minimum(g["z"] - box[4]).minimum(box[5] - g["z"])) >= 2 * g["h"]
+    dw = (wm - w64).abs()
+    big = w64.abs() >= 1e-9
+    rel = dw[big] / w64[big].abs()
+    over = dw > 1e-5 * w64.abs() + 1e-14
+    return {"max_rel_err_w_vs_fp64": float(rel.max()), "rms_rel_err_w_vs_fp64": float(rel.pow(2).mean().sqrt()),
+            "rel_err_over": "pairs with |w| >= 1e-9", "max_abs_err_w_vs_fp64": float(dw.max()),
+            "pairs_over_1e-5_rel_plus_1e-14_abs": int(over.sum()), "sampled_pairs": int(k),
+            "max_abs_unity_err": float((out["wsum"][inside] - 1).abs().max()),
+            "unity_over": "pseudo-particles whose 2h sphere lies inside the box",
+            "fp64_recomputed_frac": out["nfp64"] / max(npairs, 1)}
+
+
 def reduce_over_ranks(t_ms, units, world, device):
     """Whole-job figures across ranks: the slowest rank's timed milliseconds
     and the units (pairs) all ranks processed.  One process per GPU; on one
@@ -383,7 +425,9 @@ def roofline(npairs, ms, precision, workload):
     it.  FP64 mode: the closed form k_map_fp64 against the FP64 rate, with the
     same geometry count over all faces and edges (its transcendental calls are
     not counted)."""
-    wk = WORK[workload]
+    wk = WORK.get(workload)
+    if wk is None:   # per-pair work not counted for this workload
+        return None
     t = ms * 1e-3
     if precision == "mixed":
         nodes = 4 * wk["slots"]
