@@ -56,6 +56,8 @@ def parse():
     ap.add_argument("--precision", choices=("mixed", "fp64"), default="mixed")
     ap.add_argument("--theta", type=float, default=THETA)
     ap.add_argument("--fp64-threshold", type=float, default=1e-5)
+    ap.add_argument("--err-ulps", type=int, default=0,
+                    help="factor of the mixed pass's FP32 error estimate in units of 2^-24 (0: 8)")
     ap.add_argument("--h-tol", type=float, default=1e-13,
                     help="Newton tolerance |dh|/h_0 of the node h-solver; the paper runs 1e-2")
     ap.add_argument("--no-e2e", action="store_true")
@@ -154,7 +156,7 @@ def run_ours(args, rank, world):
     P = api.Params(r_part=w.params["r_part"], r_leaf=w.params["r_leaf"], theta=args.theta,
                    h_fact=w.params["h_fact"], h_tol=args.h_tol,
                    precision=1 if args.precision == "mixed" else 0,
-                   fp64_threshold=args.fp64_threshold)
+                   fp64_threshold=args.fp64_threshold, fp32_err_ulps=err_ulps(args))
     stream = torch.cuda.current_stream(device)
     map_ms = []
     kernel_ms = []   # (main pass, FP64 recompute) of each timed map_exact, from the library's events
@@ -259,7 +261,7 @@ def run_ours(args, rank, world):
                        "pseudo_particles": out["npseudo"] if pseudo else None, "pairs_per_step": out["npairs"],
                        "theta": args.theta, "r_part": w.params["r_part"], "r_leaf": w.params["r_leaf"],
                        "precision": args.precision, "fp64_threshold": args.fp64_threshold, "h_tol": args.h_tol,
-                       "l2": "flushed between steps (258 MiB write)", "parallelism": f"replicas x{world}"},
+                       "fp32_err_ulps": err_ulps(args), "l2": "flushed between steps (258 MiB write)", "parallelism": f"replicas x{world}"},
                map_exact_ms=statistics.mean(t_map), map_exact_pairs_per_s=out["npairs"] / (statistics.mean(t_map) * 1e-3),
                accuracy=acc, gpu_launches=launches, clocks=ck)
     k_main = statistics.mean(k[0] for k in kernel_ms)
@@ -269,6 +271,11 @@ def run_ours(args, rank, world):
     if not args.no_e2e:
         res["e2e"] = run_e2e(args, w, step, device)
     return res
+
+
+def err_ulps(args):
+    """Factor of the mixed pass's error estimate, 8 ulps unless given."""
+    return args.err_ulps if args.err_ulps > 0 else 8
 
 
 def run_batched(args, rank, world):

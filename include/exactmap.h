@@ -65,7 +65,9 @@ typedef struct {
     int block_pairs;        /* map_exact: threads per block of the FP64 kernels, one pair per warp (32..128, a multiple of 32; 0 = 128) */
     int h0_above;           /* make_pseudo_particles: with more pseudo-particles than this, every node takes h_0 (Eq. 11) and
                                the neighbour search and solver are skipped (Section 2.4.2; the paper uses 10^6); 0 = never */
-    int reserved[4];
+    int fp32_err_ulps;      /* map_exact mixed mode: a pair goes to FP64 when fp32_err_ulps 2^-24 times the sum of the
+                               magnitudes of its FP32 pieces exceeds max(fp64_threshold |w|, 1e-14); 0 = the default 8 */
+    int reserved[3];
 } em_params;
 
 void em_params_default(em_params *p);

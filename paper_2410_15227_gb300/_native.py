@@ -21,7 +21,7 @@ class EmParams(C.Structure):
                 ("h_fact", C.c_double), ("h_tol", C.c_double), ("max_newton", C.c_int),
                 ("precision", C.c_int), ("fp64_threshold", C.c_double), ("knn_k", C.c_int),
                 ("leaf_max", C.c_int), ("block_pairs", C.c_int), ("h0_above", C.c_int),
-                ("reserved", C.c_int * 4)]
+                ("fp32_err_ulps", C.c_int), ("reserved", C.c_int * 3)]
 
 
 class EmSnapshot(C.Structure):

@@ -30,6 +30,7 @@ class Params:
     leaf_max: int = 8
     block_pairs: int = 0
     h0_above: int = 0             # > 0: with more pseudo-particles than this, every node takes h_0 (Eq. 11)
+    fp32_err_ulps: int = 8        # mixed mode: factor of the FP32 error estimate, in units of 2^-24
 
     def native(self) -> N.EmParams:
         p = N.EmParams()

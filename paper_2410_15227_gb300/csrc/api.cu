@@ -63,6 +63,7 @@ EM_EXPORT void em_params_default(em_params *p)
     p->leaf_max = 8;
     p->block_pairs = 0;
     p->h0_above = 0;
+    p->fp32_err_ulps = 8;
 }
 
 EM_EXPORT int em_ctx_create(em_ctx **ctx, int device, void *stream)

@@ -539,6 +539,13 @@ __global__ void __launch_bounds__(32 * FW_WARPS) k_map_fp64(
 // above 1e-14 / tol, absolute 1e-14 below); so does a face plane through P.
 namespace {
 
+// factor of the FP32 pass's error estimate: fp32_err_ulps units of 2^-24
+// (0 stands for the default 8)
+double em_est_k(const em_params *p)
+{
+    return (double)(p->fp32_err_ulps > 0 ? p->fp32_err_ulps : 8) * 5.9604644775390625e-8;
+}
+
 // launch shape of the FP32 pass (build-time tuning knobs)
 #ifndef EM_MQ_SLOTS
 #define EM_MQ_SLOTS 6
@@ -762,7 +769,7 @@ __global__ void MQ_LAUNCH_BOUNDS k_map_fp32(int64_t npairs, const int32_t *__res
                                                         const PlaneF *__restrict__ plane_f,
                                                         const PlaneF *__restrict__ plane_fl,
                                                         const EdgeF *__restrict__ edge_f,
-                                                        const EdgeF *__restrict__ edge_fl, float tol,
+                                                        const EdgeF *__restrict__ edge_fl, float tol, double est_k,
                                                         double *__restrict__ w, int32_t *__restrict__ flagged,
                                                         int *__restrict__ nflag)
 {
@@ -908,11 +915,12 @@ __global__ void MQ_LAUNCH_BOUNDS k_map_fp32(int64_t npairs, const int32_t *__res
         const double wk = full ? sum : ((inside ? 1.0 : 0.0) - sum);
         const double magd = (double)mag + ((inside && !full) ? 1.0 : 0.0);
         w[k] = wk;
-        // error bound of the FP32 pass: 8 ulp of every non-negative piece it
-        // summed (pieces are relative-accurate to a few ulp; against FP64 the
-        // largest error/bound ratio seen was 0.81, and no pair of the test
-        // workloads exceeds the tolerance until the factor drops below 2)
-        const double est = 8.0 * 5.9604644775390625e-8 * magd;
+        // error bound of the FP32 pass: est_k = (ulps) 2^-24 times the sum of
+        // the non-negative pieces it summed.  With the default 8 ulps the
+        // largest error/bound ratio seen against FP64 on the 1e5 and 1e6
+        // clouds was 0.81; tiny cells deep inside large kernels (h / V^(1/3)
+        // above ~12, as in the 8e6 cloud) need more
+        const double est = est_k * magd;
         flag = force || !(est <= fmax((double)tol * fabs(wk), 1e-14));
     }
     // one append per warp: the flagged pairs of a warp (mostly of one cell)
@@ -985,7 +993,8 @@ EM_EXPORT int map_exact(em_ctx *ctx, const em_pairs *pr, const double *d_x, cons
             EM_CUDA(cudaMemsetAsync(nflag, 0, sizeof(int), ctx->stream));
             k_map_fp32<<<em_grid((n + 31) / 32, MQ_WARPS), 32 * MQ_WARPS, 0, ctx->stream>>>(
                 n, pr->pair_i, pr->pair_j, d_x, d_y, d_z, d_h, v->gen, v->radius, v->cell_face_off,
-                v->face_vert_off, v->plane_f, v->plane_fl, v->edge_f, v->edge_fl, (float)p->fp64_threshold, d_w_out, flagged, nflag);
+                v->face_vert_off, v->plane_f, v->plane_fl, v->edge_f, v->edge_fl, (float)p->fp64_threshold, em_est_k(p),
+                d_w_out, flagged, nflag);
             EM_LAUNCHED(ctx);
             if (ctx->timing) {
                 EM_CUDA(cudaEventRecord(ctx->ev[1], ctx->stream));
@@ -1103,7 +1112,8 @@ EM_EXPORT int map_exact_noalloc(em_ctx *ctx, const em_pairs *pr, const double *d
             EM_CUDA(cudaMemsetAsync(nflag, 0, sizeof(int), ctx->stream));
             k_map_fp32<<<em_grid((n + 31) / 32, MQ_WARPS), 32 * MQ_WARPS, 0, ctx->stream>>>(
                 n, pr->pair_i, pr->pair_j, d_x, d_y, d_z, d_h, v->gen, v->radius, v->cell_face_off,
-                v->face_vert_off, v->plane_f, v->plane_fl, v->edge_f, v->edge_fl, (float)p->fp64_threshold, d_w_out, flagged, nflag);
+                v->face_vert_off, v->plane_f, v->plane_fl, v->edge_f, v->edge_fl, (float)p->fp64_threshold, em_est_k(p),
+                d_w_out, flagged, nflag);
             EM_LAUNCHED(ctx);
             const int fgrid = (int)std::min<int64_t>((n + block / 32 - 1) / (block / 32), 152 * 64);
             k_map_fp64_flagged<<<fgrid, block, 0, ctx->stream>>>(nflag, pr->pair_i, pr->pair_j, d_x, d_y, d_z, d_h,
