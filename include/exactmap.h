@@ -7,7 +7,10 @@
  * overview): build the gravity tree, walk it to select pseudo-particles and
  * solve their smoothing lengths, build the Voronoi grid on the generation
  * sites, map the (pseudo-)particle density onto the grid with the Exact
- * mapping, and map per-cell results back onto the particles.
+ * mapping, and map per-cell results back onto the particles.  Around it:
+ * the adaptive refinement of the tree-walk (Section 2.4.1, Eq. 5), Lloyd's
+ * iteration on the sites (Section 2.3), and an executor that runs many
+ * independent snapshots through the pipeline at once (map_batch).
  *
  * Conventions (every entry point):
  *   - returns an int status (EM_OK = 0 on success, see em_status); no call
@@ -20,7 +23,10 @@
  *     allocates for them; release it with the matching *_destroy call.
  *   - all GPU work is enqueued on the context's stream.  Calls whose output
  *     size is data dependent (tree, pseudo-particles, cells, pairs) synchronise
- *     that stream once to read the size; the others do not synchronise.
+ *     that stream once to read the size, and so do the calls that return a
+ *     count to the host (refine_check); the others do not synchronise.
+ *     map_batch takes no context: it runs on streams of its own and returns
+ *     when every snapshot has finished.
  *   - results are deterministic: the same inputs give bit-identical outputs.
  *   - indices are 0-based.  Particle and cell counts must be < 2^31.
  */
