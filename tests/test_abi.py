@@ -34,3 +34,42 @@ def test_binding_loads_and_reports_errors():
     st = L.em_ctx_sync(None)
     assert st == _native.EM_EINVAL
     assert b"invalid argument" in L.em_last_error()
+
+
+def _c_layout(struct, fields):
+    """sizeof and offsetof of a header struct, from a C program gcc compiles
+    against include/exactmap.h."""
+    import subprocess
+    import tempfile
+    body = "\n".join(f'    printf("%s %zu\\n", "{f}", offsetof({struct}, {f}));' for f in fields)
+    src = ("#include <stddef.h>\n#include <stdio.h>\n#include \"exactmap.h\"\nint main(void) {\n"
+           f'    printf("sizeof %zu\\n", sizeof({struct}));\n{body}\n    return 0;\n}}\n')
+    with tempfile.TemporaryDirectory() as d:
+        c, exe = os.path.join(d, "layout.c"), os.path.join(d, "layout")
+        open(c, "w").write(src)
+        subprocess.run(["gcc", "-std=c11", "-I", os.path.join(ROOT, "include"), c, "-o", exe], check=True)
+        out = subprocess.run([exe], check=True, capture_output=True, text=True).stdout
+    return {k: int(v) for k, v in (line.split() for line in out.strip().splitlines())}
+
+
+def test_struct_layouts_match_header():
+    """The ctypes mirrors of em_params and em_snapshot have the header's
+    size and field offsets."""
+    from paper_2410_15227_gb300 import _native
+    for cls, name in ((_native.EmParams, "em_params"), (_native.EmSnapshot, "em_snapshot")):
+        fields = [f for f, _ in cls._fields_]
+        lay = _c_layout(name, fields)
+        assert lay["sizeof"] == ctypes.sizeof(cls), name
+        for f in fields:
+            assert lay[f] == getattr(cls, f).offset, (name, f)
+
+
+def test_python_defaults_match_library():
+    """api.Params() carries the values em_params_default() fills."""
+    from dataclasses import fields
+    from paper_2410_15227_gb300 import _native, api
+    c = _native.EmParams()
+    _native.lib().em_params_default(ctypes.byref(c))
+    p = api.Params()
+    for f in fields(p):
+        assert getattr(c, f.name) == getattr(p, f.name), f.name
