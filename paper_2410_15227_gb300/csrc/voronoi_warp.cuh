@@ -1,9 +1,8 @@
 // Warp-cooperative Voronoi cell construction (one warp per cell, the cell
-// in shared memory).  Same dual representation and the same clipping order
-// as the per-thread code in voronoi_cell.cuh: vertices beyond the bisector
-// are removed, kept vertices stay in order, and the new vertices are
-// appended in the order (removed vertex, edge) -- so both produce the same
-// cell.  Candidates: every generator within a radius R of the site (found by
+// in shared memory, in dual form: planes, and vertices as triangles of
+// planes).  A clip removes the vertices beyond the bisector, keeps the
+// others in order and appends the new vertices in the order (removed
+// vertex, edge), so the vertex order is fixed by the clips alone.  Candidates: every generator within a radius R of the site (found by
 // a warp walk of the generators' box hierarchy), sorted by distance; the
 // cell is exact once 2 R_max < R, otherwise the shell up to 2 R_max is
 // clipped in as well.
@@ -59,8 +58,6 @@ __device__ void wcell_box(WCell &c, const double *box, double gx, double gy, dou
 {
     const int lane = threadIdx.x & 31;
     if (lane == 0) {
-        emv::VCell *dummy = nullptr;
-        (void)dummy;
         const double lo[3] = {box[0] - gx, box[2] - gy, box[4] - gz};
         const double hi[3] = {box[1] - gx, box[3] - gy, box[5] - gz};
         c.np = 6;
