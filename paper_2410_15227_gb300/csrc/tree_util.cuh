@@ -40,26 +40,6 @@ __device__ __forceinline__ uint64_t morton_key(double x, double y, double z, dou
            spread3(quantise(z, zlo, zhi));
 }
 
-// M4 cubic spline in 3-D: W = w(q) / (pi h^3), truncated at q = 2.
-__device__ __forceinline__ double m4_w(double q)
-{
-    if (q < 1.0) return 1.0 - 1.5 * q * q + 0.75 * q * q * q;
-    if (q < 2.0) {
-        double t = 2.0 - q;
-        return 0.25 * t * t * t;
-    }
-    return 0.0;
-}
-__device__ __forceinline__ double m4_dw(double q)
-{
-    if (q < 1.0) return -3.0 * q + 2.25 * q * q;
-    if (q < 2.0) {
-        double t = 2.0 - q;
-        return -0.75 * t * t;
-    }
-    return 0.0;
-}
-
 constexpr int kMaxLevels = 8;
 
 // Level 0 = items (Morton order); level l >= 1 node k bounds the items
