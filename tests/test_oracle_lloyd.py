@@ -4,7 +4,6 @@ box's; a regular lattice of sites at the centres of equal boxes is a fixed
 point; one site's cell is the box; Monte Carlo centroids; Lloyd's iteration
 lowers the quantisation energy.  CPU only."""
 import numpy as np
-import pytest
 
 from paper_2410_15227_gb300 import inputs
 
