@@ -31,10 +31,11 @@ WORKLOADS = {
     "sphere_1e5": ("sphere_100k_particles_25k_cells", False),
     "batched_64": ("batched_64_snapshots", True),
     "full_8m": ("full_8M_particles_2M_cells", True),
+    "direct_8m": ("full_8M_particles_2M_cells_tree_off", False),
 }
 # workloads whose FP64 reference pass over every pair would take longer than
 # the timed steps: accuracy on a random sample of pairs instead
-ACCURACY_SAMPLE = {"full_8m": 2_000_000}
+ACCURACY_SAMPLE = {"full_8m": 2_000_000, "direct_8m": 2_000_000}
 # pseudo-particle selection: r_part, r_leaf from the paper's Table 1 runs; theta
 # chosen so that the cloud yields about 1e5 pseudo-particles (102,908)
 THETA = 0.065
@@ -51,7 +52,8 @@ def parse():
                     help="pseudo_1e6: 1e6-particle cloud through the tree and pseudo-particles (the "
                          "benchmark); sphere_1e5: 1e5 particles mapped directly (smaller case); "
                          "batched_64: 64 independent snapshots of 1e3-1e5 particles through map_batch; "
-                         "full_8m: 8e6 particles and 2e6 cells (accuracy on a pair sample)")
+                         "full_8m: 8e6 particles and 2e6 cells (accuracy on a pair sample); "
+                         "direct_8m: the same cloud with every particle mapped (tree off)")
     ap.add_argument("--workers", type=int, default=8, help="batched_64: host threads (streams) of map_batch")
     ap.add_argument("--precision", choices=("mixed", "fp64"), default="mixed")
     ap.add_argument("--theta", type=float, default=THETA)
@@ -71,7 +73,7 @@ def load_workload(args):
     if args.workload == "pseudo_1e6":
         w = inputs.cached(inputs.workload_pseudo_1e6, cache_dir=args.cache)
         w.params["theta"] = args.theta
-    elif args.workload == "full_8m":
+    elif args.workload in ("full_8m", "direct_8m"):
         w = inputs.cached(inputs.workload_full_8m, cache_dir=args.cache)
         w.params["theta"] = args.theta
     else:
