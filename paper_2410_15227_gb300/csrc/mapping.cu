@@ -553,6 +553,15 @@ double em_est_k(const em_params *p)
 #ifndef EM_MQ_WARPS
 #define EM_MQ_WARPS 2
 #endif
+#ifndef EM_G8_MAXLEN_FAR
+// longest 8-point sub-piece (in s) of the second kernel piece on a face
+// whose plane lies beyond h (R >= 1); elsewhere 2.  On that branch the
+// 8-point rule's truncation reaches ~5 ulp of the segment at length 2 and
+// ~0.3 ulp at 1.5 (an FP64 model of the integrand against adaptive
+// quadrature); the error estimate counts rounding only
+#define EM_G8_MAXLEN_FAR 2.0
+#endif
+static_assert(EM_G8_MAXLEN_FAR >= 0.5 && EM_G8_MAXLEN_FAR <= 2.0, "sub-pieces per segment must stay below 256");
 #ifndef EM_GL4_MAXLEN
 #define EM_GL4_MAXLEN 0.125   // longest segment (in s) integrated with 4 points
 #endif
@@ -718,7 +727,9 @@ __device__ __forceinline__ void mq_push_g(SegQueue &q, int lane, int &cnt, float
         const float len = s1 - s0;
         // 4 points for a short segment, else 8 on sub-pieces of length <= 2
         const bool gl4 = len <= (float)EM_GL4_MAXLEN;
-        const int m = len > 2.f ? (int)ceilf(0.5f * len) : 1;   // <= 36: A >= 1e-30, |tau| <= 2
+        const float g8 = (piece == 2 && fs.R >= 1.f) ? (float)EM_G8_MAXLEN_FAR : 2.f;
+        // m <= ceil(70.5 / g8) <= 141: A >= 1e-30, |tau| <= 2
+        const int m = len > g8 ? (int)ceilf(len * (1.f / g8)) : 1;
         const int sl = cnt++;
         q.sa[sl][lane] = s0;
         q.hl[sl][lane] = 0.5f * len / (float)m;
