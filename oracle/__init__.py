@@ -15,8 +15,8 @@ What it computes, by the paper's sections and equations:
   cell densities rho_j = sum_i m_i w_ij / V_j.
 * Morton octree, node mass / COM / size (Section 2.2.1), adaptive tree-walk
   (Section 2.4.1, Eq. 4), node h-solver (Section 2.4.2, Eqs. 6-11), inverse
-  mapping f_i = sum_j w_ij f_j / sum_j w_ij and constituent inheritance
-  (Section 2.3 and Section 2.5).
+  mapping f_i = sum_j w_ij f_j / sum_j w_ij (Section 2.3, ``map_back``) and
+  constituent inheritance (Section 2.5, ``inherit``).
 * Cell centroids and Lloyd's iteration on the sites (Section 2.3); the
   adaptive refinement of the tree-walk (Section 2.4.1, Eq. 5).
 
@@ -348,17 +348,44 @@ def particle_weight_sum(pairs: Pairs, w, n) -> np.ndarray:
 
 
 def map_back(pairs: Pairs, w, f_cell, n) -> np.ndarray:
-    """f_i = sum_j w_ij f_j / sum_j w_ij (kernel-weighted inverse mapping); NaN for
-    particles without any pair."""
+    """Inverse mapping (Section 2.3): f_i = sum_j w_ij f_j / sum_j w_ij, the
+    kernel-weighted average of the cell values over particle i's cells; NaN
+    for particles without any pair.  Both sums run over each particle's pairs
+    in ascending j, one rounded product and one rounded addition per term
+    (np.add.at applies the additions in index order)."""
+    order = np.lexsort((pairs.pair_j, pairs.pair_i))
+    pi = np.asarray(pairs.pair_i)[order]
+    pj = np.asarray(pairs.pair_j)[order]
+    wk = np.asarray(w, dtype=np.float64)[order]
+    fk = np.asarray(f_cell, dtype=np.float64)[pj]
     num = np.zeros(n)
     den = np.zeros(n)
-    order = np.lexsort((pairs.pair_j, pairs.pair_i))
-    for k in order:
-        i = pairs.pair_i[k]
-        num[i] += w[k] * f_cell[pairs.pair_j[k]]
-        den[i] += w[k]
+    np.add.at(num, pi, wk * fk)
+    np.add.at(den, pi, wk)
     with np.errstate(invalid="ignore", divide="ignore"):
         return num / den
+
+
+def inherit(ps: "Pseudo", tree: "Tree", f_pseudo) -> np.ndarray:
+    """Constituent inheritance (Section 2.5): the SPH particles a pseudo-particle
+    stands for share its value.  Pseudo-particle a covers the Morton positions
+    [first_a, first_a + count_a) of the tree's particle order, that is the
+    particles perm[first_a .. first_a + count_a - 1] (a node's constituents,
+    or the one extracted particle).  Returns one value per particle in the
+    input order; raises if a particle is covered twice or not at all (the
+    selection tiles the particles exactly once, Section 2.4.1)."""
+    n = tree.perm.shape[0]
+    f_pseudo = np.asarray(f_pseudo, dtype=np.float64)
+    out = np.zeros(n)
+    cover = np.zeros(n, np.int64)
+    for a in range(ps.n):
+        idx = tree.perm[int(ps.first[a]):int(ps.first[a]) + int(ps.count[a])]
+        out[idx] = f_pseudo[a]
+        cover[idx] += 1
+    if np.any(cover != 1):
+        raise ValueError(f"inherit: {int(np.sum(cover == 0))} particles uncovered, "
+                         f"{int(np.sum(cover > 1))} covered more than once")
+    return out
 
 
 # ---------------------------------------------------------------------------

@@ -73,8 +73,7 @@ def build(force: bool = False, verbose: bool = False, extra_flags=()) -> str:
                     print(out)
     if force or jobs or _stale(LIB_PATH, objs):
         tmp = LIB_PATH + f".{os.getpid()}.tmp"
-        run([nvcc, *ARCH, "-shared", "-o", tmp, *objs, "-lcuda"] if False else
-            [nvcc, *ARCH, "-shared", "-o", tmp, *objs])
+        run([nvcc, *ARCH, "-shared", "-o", tmp, *objs])
         os.replace(tmp, LIB_PATH)
     return LIB_PATH
 

@@ -74,8 +74,11 @@ EM_EXPORT int em_ctx_create(em_ctx **ctx, int device, void *stream)
     EM_CUDA(cudaGetDeviceCount(&ndev));
     EM_CHECK_ARG(device >= 0 && device < ndev);
     EM_CUDA(cudaSetDevice(device));
+    int nsm = 0;
+    EM_CUDA(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, device));
     em_ctx *c = new em_ctx;
     c->device = device;
+    c->nsm = nsm > 0 ? nsm : 1;
     c->stream = (cudaStream_t)stream;
     c->launches = 0;
     c->timing = false;

@@ -15,6 +15,7 @@
 
 struct em_ctx {
     int device;
+    int nsm;   // streaming multiprocessors of the device (grid sizes of the grid-stride kernels)
     cudaStream_t stream;
     int64_t launches;
     // optional timing of the map_exact kernels (em_ctx_set_timing):

@@ -987,7 +987,7 @@ EM_EXPORT int map_exact(em_ctx *ctx, const em_pairs *pr, const double *d_x, cons
     if (n) {
         if (ctx->timing) EM_CUDA(cudaEventRecord(ctx->ev[0], ctx->stream));
         if (p->precision == 0) {
-            k_map_fp64<<<(int)std::min<int64_t>((n + block / 32 - 1) / (block / 32), 152 * 64), block, 0,
+            k_map_fp64<<<(int)std::min<int64_t>((n + block / 32 - 1) / (block / 32), (int64_t)ctx->nsm * 64), block, 0,
                          ctx->stream>>>(n, pr->pair_i, pr->pair_j, d_x, d_y, d_z, d_h, v->gen, v->radius,
                                         v->cell_face_off, v->face_vert_off, v->plane, v->edge, d_w_out);
             EM_LAUNCHED(ctx);
@@ -1012,7 +1012,7 @@ EM_EXPORT int map_exact(em_ctx *ctx, const em_pairs *pr, const double *d_x, cons
                 EM_CUDA(cudaEventRecord(ctx->ev[2], ctx->stream));
             }
             // FP64 recompute of the flagged pairs; the count stays on the device
-            const int fgrid = (int)std::min<int64_t>((n + block / 32 - 1) / (block / 32), 152 * 64);
+            const int fgrid = (int)std::min<int64_t>((n + block / 32 - 1) / (block / 32), (int64_t)ctx->nsm * 64);
             k_map_fp64_flagged<<<fgrid, block, 0, ctx->stream>>>(nflag, pr->pair_i, pr->pair_j, d_x, d_y, d_z, d_h,
                                                                  v->gen, v->radius, v->cell_face_off,
                                                                  v->face_vert_off, v->plane, v->edge, flagged,
@@ -1112,7 +1112,7 @@ EM_EXPORT int map_exact_noalloc(em_ctx *ctx, const em_pairs *pr, const double *d
     if (h_nfp64) *h_nfp64 = 0;
     if (n) {
         if (p->precision == 0) {
-            k_map_fp64<<<(int)std::min<int64_t>((n + block / 32 - 1) / (block / 32), 152 * 64), block, 0,
+            k_map_fp64<<<(int)std::min<int64_t>((n + block / 32 - 1) / (block / 32), (int64_t)ctx->nsm * 64), block, 0,
                          ctx->stream>>>(n, pr->pair_i, pr->pair_j, d_x, d_y, d_z, d_h, v->gen, v->radius,
                                         v->cell_face_off, v->face_vert_off, v->plane, v->edge, d_w_out);
             EM_LAUNCHED(ctx);
@@ -1126,7 +1126,7 @@ EM_EXPORT int map_exact_noalloc(em_ctx *ctx, const em_pairs *pr, const double *d
                 v->face_vert_off, v->plane_f, v->plane_fl, v->edge_f, v->edge_fl, (float)p->fp64_threshold, em_est_k(p),
                 d_w_out, flagged, nflag);
             EM_LAUNCHED(ctx);
-            const int fgrid = (int)std::min<int64_t>((n + block / 32 - 1) / (block / 32), 152 * 64);
+            const int fgrid = (int)std::min<int64_t>((n + block / 32 - 1) / (block / 32), (int64_t)ctx->nsm * 64);
             k_map_fp64_flagged<<<fgrid, block, 0, ctx->stream>>>(nflag, pr->pair_i, pr->pair_j, d_x, d_y, d_z, d_h,
                                                                  v->gen, v->radius, v->cell_face_off,
                                                                  v->face_vert_off, v->plane, v->edge, flagged,
@@ -1163,11 +1163,15 @@ __global__ void k_map_back(int64_t np, const int64_t *__restrict__ off, const in
 {
     int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     if (i >= np) return;
+    // ascending j, each product and each sum rounded on its own (no fused
+    // multiply-add), so that equal weights give bit-identical results on any
+    // implementation that sums in the same order
     double num = 0.0, den = 0.0;
     for (int64_t k = off[i]; k < off[i + 1]; ++k) {
-        int32_t q = idx[k];
-        num += w[q] * f_cell[pj[q]];
-        den += w[q];
+        const int32_t q = idx[k];
+        const double wq = w[q];
+        num = __dadd_rn(num, __dmul_rn(wq, f_cell[pj[q]]));
+        den = __dadd_rn(den, wq);
     }
     f_out[i] = num / den;
 }

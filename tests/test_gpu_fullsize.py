@@ -10,8 +10,12 @@ cells and weights.  The candidate cells of a particle p come from a rigorous
 bound: a cell j reaches within 2h of p only if |g_j - p| <= 4h + d_p, with
 d_p the distance from p to its nearest generator (a point x of the cell with
 |x - p| < 2h is no farther from g_j than from the generator nearest p).
-Properties that hold at any size are checked over all particles: partition
-of unity, mass conservation, and the inverse mapping of a constant field."""
+The sampled weights are mapped on the GPU with the oracle's own h and pair
+list, so that FP64 mode is held to 1e-12.  Properties that hold at any size
+are checked over all particles: partition of unity, mass conservation, the
+inverse mapping of a constant field, and, for a random cell field, every
+particle's value equal to its pseudo-particle's through the oracle's own
+membership (Section 2.5)."""
 import numpy as np
 import pytest
 import torch
@@ -109,42 +113,47 @@ def test_sampled_node_h(full, sampled_h):
     assert np.array_equal(st == 2, sg == 2)
 
 
-def test_sampled_pairs_cells_and_weights(full, sampled_h, orc):
-    """Complete pair lists, cells and weights of sampled pseudo-particles."""
-    w, g, pg, vg = full["w"], full["g"], full["pg"], full["vg"]
+@pytest.fixture(scope="module")
+def sampled(full, oracle_pseudo, sampled_h, orc):
+    """The oracle's cells, pairs and weights of sampled pseudo-particles, each
+    with its own h (the oracle's h-solver for nodes, the input h for extracted
+    particles), from the candidate cells of the bound in the module docstring.
+    Positions are the oracle's own pseudo-particles'."""
+    w = full["w"]
+    ps_o = oracle_pseudo[0]
+    g = dict(x=ps_o.x, y=ps_o.y, z=ps_o.z, origin=ps_o.origin)
     tg_nodes, h_orc, st, tg_parts = sampled_h
     gen = np.stack([w.gx, w.gy, w.gz], 1)
-    # node pseudo-particles carry the oracle's h (equal to the GPU's to 1e-12,
-    # which weights near the support's edge, w ~ (2 - q)^4, amplify up to ~1e4);
-    # extracted particles carry the input h on both sides
-    targets = [(int(a), float(hh), 1e-8) for a, hh, s in zip(tg_nodes[:6], h_orc[:6], st[:6]) if s <= 1]
-    targets += [(int(a), float(w.h[a_part]), 1e-11)
-                for a, a_part in zip(tg_parts, -full["g"]["origin"][tg_parts] - 1)]
-    L = float(np.max(w.box[1::2] - w.box[0::2]))
-    cfo, fvo = vg["cell_face_off"], vg["face_vert_off"]
-    checked_pairs = 0
-    for a, ha, tol64 in targets:
+    targets = [(int(a), float(hh)) for a, hh, s in zip(tg_nodes[:6], h_orc[:6], st[:6]) if s <= 1]
+    targets += [(int(a), float(w.h[a_part])) for a, a_part in zip(tg_parts, -g["origin"][tg_parts] - 1)]
+    out = []
+    for a, ha in targets:
         p = np.array([g["x"][a], g["y"][a], g["z"][a]])
         d = np.linalg.norm(gen - p, axis=1)
         cand = np.flatnonzero(d <= 4.0 * ha + d.min() + 1e-12)
         cells = orc.voronoi(w.gx, w.gy, w.gz, w.box, cells=cand)
         one = lambda v: np.array([v], dtype=np.float64)
         po = orc.find_pairs(one(p[0]), one(p[1]), one(p[2]), one(ha), cells)
-        js_o = cells.cell_ids[po.pair_j]
+        wo = orc.map_exact_list(po.pair_i, po.pair_j, one(p[0]), one(p[1]), one(p[2]), one(ha), cells)
+        out.append(dict(a=a, h=ha, cells=cells, po=po, js=cells.cell_ids[po.pair_j], wo=wo))
+    return out
+
+
+def test_sampled_pairs_and_cells(full, sampled):
+    """Complete pair lists and cells of sampled pseudo-particles: the GPU's own
+    pairs (its own h) against the oracle's, up to pairs flagged near the
+    support's edge."""
+    w, pg, vg = full["w"], full["pg"], full["vg"]
+    L = float(np.max(w.box[1::2] - w.box[0::2]))
+    cfo, fvo = vg["cell_face_off"], vg["face_vert_off"]
+    checked = 0
+    for s in sampled:
+        a, cells, po, js_o = s["a"], s["cells"], s["po"], s["js"]
         mine = pg["pair_i"] == a
         js_g = pg["pair_j"][mine]
         near = set(js_g[pg["near"][mine] == 1].tolist())
         assert set(js_o.tolist()) - near == set(js_g.tolist()) - near, a
-        # weights: oracle on its own cells with its own h
-        wo = orc.map_exact_list(po.pair_i, po.pair_j, one(p[0]), one(p[1]), one(p[2]), one(ha), cells)
-        kg = np.flatnonzero(mine)
-        pos = {int(j): int(k) for j, k in zip(js_g, kg)}
-        for jloc, j, wref in zip(po.pair_j, js_o, wo):
-            if int(j) not in pos:   # only near pairs may be missing (checked above)
-                continue
-            k = pos[int(j)]
-            assert abs(full["w64"][k] - wref) <= tol64 * abs(wref) + 1e-14, (a, j, full["w64"][k], wref)
-            assert abs(full["wm"][k] - wref) <= 1e-5 * abs(wref) + 1e-14, (a, j, full["wm"][k], wref)
+        for jloc, j in zip(po.pair_j, js_o):
             # the cell itself: neighbours (faces above 1e-10 L^2) and volume
             fo = {int(n) for v, nrm, n in cells.faces(int(jloc)) if abs(_area(v, nrm)) >= 1e-10 * L * L}
             fg = set()
@@ -154,8 +163,36 @@ def test_sampled_pairs_cells_and_weights(full, sampled_h, orc):
                     fg.add(int(vg["nbr"][f]))
             assert fo == fg, j
             assert abs(vg["volume"][j] - cells.volume[jloc]) <= 1e-12 * cells.volume[jloc]
-            checked_pairs += 1
-    assert checked_pairs > 300
+            checked += 1
+    assert checked > 300
+
+
+@pytest.mark.parametrize("precision,tol", [(0, 1e-12), (1, 1e-5)])
+def test_sampled_weights(full, oracle_pseudo, sampled, precision, tol):
+    """Weights of the sampled pseudo-particles on the GPU's cells, mapped with
+    the oracle's h and the oracle's pair list (pairs_from_list), against the
+    oracle's weights: 1e-12 relative in FP64 mode, 1e-5 in mixed mode, above
+    the absolute floor 1e-14."""
+    ctx, vor = full["ctx"], full["vor"]
+    ps_o = oracle_pseudo[0]
+    h = ps_o.h.copy()
+    pi, pj, wref = [], [], []
+    for s in sampled:
+        h[s["a"]] = s["h"]
+        pi.append(np.full(s["js"].shape[0], s["a"]))
+        pj.append(s["js"])
+        wref.append(s["wo"])
+    pi, pj, wref = np.concatenate(pi), np.concatenate(pj), np.concatenate(wref)
+    order = np.lexsort((pi, pj))
+    pi, pj, wref = pi[order], pj[order], wref[order]
+    pr = api.pairs_from_list(ctx, dev(pi, torch.int32), dev(pj, torch.int32), ps_o.n, vor)
+    X = [dev(a) for a in (ps_o.x, ps_o.y, ps_o.z, h, ps_o.m)]
+    wg, _, _, _ = api.map_exact(ctx, pr, *X, vor, api.Params(precision=precision, fp64_threshold=1e-5),
+                                want_wsum=False)
+    wg = wg.cpu().numpy()
+    assert wg.shape[0] > 300
+    err = np.abs(wg - wref)
+    assert np.all(err <= tol * np.abs(wref) + 1e-14), float(np.max(err / (np.abs(wref) + 1e-300)))
 
 
 def test_partition_of_unity_and_mass(full):
@@ -176,6 +213,28 @@ def test_partition_of_unity_and_mass(full):
     assert np.all(err <= 1e-5 * np.abs(full["w64"]) + 1e-14)
     assert np.max(err[big] / np.abs(full["w64"][big])) < 1e-5
     assert 0 < full["nf"] < 0.05 * full["wm"].shape[0]
+
+
+def test_map_back_random_field(full, oracle_pseudo, sampled, orc):
+    """Inverse mapping of a random cell field (uniform [0, 1], seed 5) at full
+    size.  Every particle's value is its pseudo-particle's, through the
+    oracle's own membership of the 1e6 particles (tree and selection, Section
+    2.5); the sampled pseudo-particles' values equal the weighted means of the
+    oracle's own pairs and weights, within the weights' tolerance carried into
+    a mean of values in [0, 1] (twice the relative error)."""
+    ctx, pairs, ps, tree = full["ctx"], full["pairs"], full["ps"], full["tree"]
+    nc = full["vg"]["volume"].shape[0]
+    f_cell = np.random.default_rng([5, 5]).random(nc)
+    ps_o, t_o, _ = oracle_pseudo
+    owner = orc.inherit(ps_o, t_o, np.arange(ps_o.n, dtype=np.float64)).astype(np.int64)
+    for wk, tol in (("w64", 1e-8), ("wm", 2e-5)):
+        f, fp = api.map_back(ctx, pairs, torch.as_tensor(full[wk], device="cuda"), dev(f_cell), ps, tree)
+        f, fp = f.cpu().numpy(), fp.cpu().numpy()
+        assert np.all(np.isfinite(f)) and np.std(fp) > 0.02
+        assert np.array_equal(fp, f[owner])
+        for s in sampled:
+            fo = float(np.sum(s["wo"] * f_cell[s["js"]]) / np.sum(s["wo"]))
+            assert abs(f[s["a"]] - fo) < tol, (wk, s["a"], f[s["a"]], fo)
 
 
 def test_map_back_constant_field(full):

@@ -200,6 +200,111 @@ def test_map_back_constant_and_linear(orc):
     assert np.max(np.abs(a - b)) < 1e-13
 
 
+def _indicator_pin(map_back_fn, pairs, wts, n, ncell, cells_to_check):
+    """Inverse mapping of the indicator field of cell j (1 on j, 0 elsewhere):
+    f_i = w_ij / sum_j' w_ij' for exactly the particles paired with j, 0 for the
+    other particles that have pairs.  The numerator is the single term w_ij and
+    the denominator sums the same weights in the same order as u_i, so both
+    sides are equal to the bit.  Returns the first failure, or None."""
+    u = np.zeros(n)
+    order = np.lexsort((pairs.pair_j, pairs.pair_i))
+    for k in order:
+        u[pairs.pair_i[k]] += wts[k]
+    has = u > 0
+    for j in cells_to_check:
+        f_cell = np.zeros(ncell)
+        f_cell[j] = 1.0
+        f = map_back_fn(pairs, wts, f_cell, n)
+        want = np.zeros(n)
+        sel = np.flatnonzero(pairs.pair_j == j)
+        want[pairs.pair_i[sel]] = wts[sel] / u[pairs.pair_i[sel]]
+        if not np.array_equal(f[has], want[has]):
+            return j
+        if not np.all(np.isnan(f[~has])):
+            return j
+    return None
+
+
+def test_map_back_indicator_field(orc):
+    """An indicator field pins which cell value each pair reads: a constant or
+    linear field cannot (Section 2.3, inverse mapping)."""
+    w = inputs.uniform_cube(120, 100, seed=30, gen_seed=31)
+    cells = orc.voronoi(w.gx, w.gy, w.gz, w.box)
+    pairs = orc.find_pairs(w.x, w.y, w.z, w.h, cells)
+    wts = orc.map_exact(pairs, w.x, w.y, w.z, w.h, cells)
+    js = [0, 17, 42, cells.ncell - 1]
+    assert _indicator_pin(orc.map_back, pairs, wts, w.n, cells.ncell, js) is None
+
+    # planted mistakes, each a copy of the oracle's sum with one index wrong
+    def read_at_particle(pairs, wts, f_cell, n):   # f_cell[pair_i] instead of f_cell[pair_j]
+        num, den = np.zeros(n), np.zeros(n)
+        for k in np.lexsort((pairs.pair_j, pairs.pair_i)):
+            i = pairs.pair_i[k]
+            num[i] += wts[k] * f_cell[i % f_cell.shape[0]]
+            den[i] += wts[k]
+        with np.errstate(invalid="ignore", divide="ignore"):
+            return num / den
+
+    def weights_unsorted(pairs, wts, f_cell, n):   # weights read in the (i, j) order, cells in the (j, i) order
+        num, den = np.zeros(n), np.zeros(n)
+        order = np.lexsort((pairs.pair_j, pairs.pair_i))
+        for t, k in enumerate(order):
+            i = pairs.pair_i[k]
+            num[i] += wts[order[t]] * f_cell[pairs.pair_j[t]]
+            den[i] += wts[k]
+        with np.errstate(invalid="ignore", divide="ignore"):
+            return num / den
+
+    for bad in (read_at_particle, weights_unsorted):
+        assert _indicator_pin(bad, pairs, wts, w.n, cells.ncell, js) is not None, bad.__name__
+
+
+def _inherit_pin(inherit_fn, ps, t, w):
+    """Every particle takes the value of the pseudo-particle that stands for it
+    (Section 2.5).  With f_pseudo = a (distinct per pseudo-particle), particle p
+    must get the index of an extracted pseudo-particle whose origin is p
+    itself, or of a node whose label is a prefix of p's Morton key (an
+    independent restatement of membership: label = 1 followed by the node's
+    3L key bits).  Returns the number of wrong particles."""
+    f = inherit_fn(ps, t, np.arange(ps.n, dtype=np.float64))
+    if f.shape[0] != w.n or not np.all(np.isfinite(f)):
+        return w.n
+    a = f.astype(np.int64)
+    keys = morton_numpy(w.x, w.y, w.z, w.box)
+    bad = 0
+    org = ps.origin[a]
+    part = org < 0
+    bad += int(np.sum(-org[part] - 1 != np.flatnonzero(part)))
+    lab = org[~part].astype(np.uint64)
+    lev = np.array([(int(v).bit_length() - 1) // 3 for v in lab], np.uint64)
+    pre = lab - (np.uint64(1) << (np.uint64(3) * lev))
+    bad += int(np.sum((keys[~part] >> (np.uint64(3) * (np.uint64(21) - lev))) != pre))
+    return bad
+
+
+def test_inherit(orc, cloud):
+    w = cloud
+    ps, t, _ = orc.make_pseudo_particles(w.x, w.y, w.z, w.m, w.h, w.box, np.array([[0.05, -0.02, 0.0]]),
+                                         0.1, 0.2, 0.5, solve=False)
+    assert (ps.origin < 0).sum() > 20 and (ps.count[ps.origin > 0] > 1).sum() > 100
+    assert _inherit_pin(orc.inherit, ps, t, w) == 0
+    # a pseudo-particle of one particle hands back its own value
+    f = orc.inherit(ps, t, np.arange(ps.n, dtype=np.float64))
+    one = np.flatnonzero(ps.count == 1)
+    assert np.array_equal(f[t.perm[ps.first[one]]], one.astype(np.float64))
+    # a constant value is inherited unchanged by every particle
+    assert np.all(orc.inherit(ps, t, np.full(ps.n, 0.3)) == 0.3)
+    # planted mistake: the Morton positions taken as particle indices (perm dropped)
+    import dataclasses
+    no_perm = lambda ps_, t_, f_: orc.inherit(ps_, dataclasses.replace(t_, perm=np.arange(w.n)), f_)
+    assert _inherit_pin(no_perm, ps, t, w) > 0
+    # a double cover is rejected
+    ps2 = dataclasses.replace(ps, first=ps.first.copy())
+    ps2.first[1] = ps2.first[0]
+    with pytest.raises(ValueError):
+        orc.inherit(ps2, t, np.zeros(ps.n))
+
+
 def test_h0_bypass(orc, cloud):
     """Above h0_above pseudo-particles no node is solved: each keeps h_0 of
     Eq. 11, 2 h_fact s_node (a one-particle node its particle's h), with
