@@ -971,25 +971,36 @@ __global__ void k_particle_wsum(int64_t np, const int64_t *__restrict__ off, con
     u[i] = s;
 }
 
-EM_EXPORT int map_exact(em_ctx *ctx, const em_pairs *pr, const double *d_x, const double *d_y, const double *d_z,
-                        const double *d_h, const double *d_m, const em_voronoi *v, const em_params *p,
-                        double *d_w_out, double *d_rho_out, double *d_wsum_out, int64_t *h_nfp64)
+// map_exact and map_exact_noalloc: the mixed pass's flagged-pair list and
+// counter are stream-ordered scratch (fixed == false) or the library's fixed
+// device array (fixed == true, at most EM_NOALLOC_MAX_PAIRS pairs).
+static int noalloc_buffers(em_ctx *ctx, int32_t **flagged, int **count);
+
+static int map_exact_run(em_ctx *ctx, const em_pairs *pr, const double *d_x, const double *d_y, const double *d_z,
+                         const double *d_h, const double *d_m, const em_voronoi *v, const em_params *p,
+                         double *d_w_out, double *d_rho_out, double *d_wsum_out, int64_t *h_nfp64, bool fixed)
 {
     EM_CHECK_ARG(ctx && pr && v && p && pr->ncell == v->ncell);
     EM_CHECK_ARG(pr->npairs == 0 || (d_x && d_y && d_z && d_h && d_w_out));
     EM_CHECK_ARG(d_rho_out == nullptr || d_m != nullptr);
     EM_CHECK_ARG(p->precision == 0 || p->precision == 1);
-    int64_t n = pr->npairs;
-    int block = p->block_pairs > 0 ? p->block_pairs : 128;
+    const int64_t n = pr->npairs;
+    if (fixed && n > EM_NOALLOC_MAX_PAIRS) {
+        em_set_error("map_exact_noalloc: %lld pairs exceed the fixed capacity of %d pairs", (long long)n,
+                     EM_NOALLOC_MAX_PAIRS);
+        return EM_ECAPACITY;
+    }
+    const int block = p->block_pairs > 0 ? p->block_pairs : 128;
     EM_CHECK_ARG(block % 32 == 0 && block <= 128);
     if (h_nfp64) *h_nfp64 = 0;
     if (ctx->timing) ctx->recorded[0] = ctx->recorded[1] = false;
     if (n) {
+        const int fgrid = (int)std::min<int64_t>((n + block / 32 - 1) / (block / 32), (int64_t)ctx->nsm * 64);
         if (ctx->timing) EM_CUDA(cudaEventRecord(ctx->ev[0], ctx->stream));
         if (p->precision == 0) {
-            k_map_fp64<<<(int)std::min<int64_t>((n + block / 32 - 1) / (block / 32), (int64_t)ctx->nsm * 64), block, 0,
-                         ctx->stream>>>(n, pr->pair_i, pr->pair_j, d_x, d_y, d_z, d_h, v->gen, v->radius,
-                                        v->cell_face_off, v->face_vert_off, v->plane, v->edge, d_w_out);
+            k_map_fp64<<<fgrid, block, 0, ctx->stream>>>(n, pr->pair_i, pr->pair_j, d_x, d_y, d_z, d_h, v->gen,
+                                                         v->radius, v->cell_face_off, v->face_vert_off, v->plane,
+                                                         v->edge, d_w_out);
             EM_LAUNCHED(ctx);
             if (ctx->timing) {
                 EM_CUDA(cudaEventRecord(ctx->ev[1], ctx->stream));
@@ -999,8 +1010,12 @@ EM_EXPORT int map_exact(em_ctx *ctx, const em_pairs *pr, const double *d_x, cons
             DevArena tmp(ctx->stream, true);
             int32_t *flagged;
             int *nflag;
-            EM_TRY(tmp.alloc(&flagged, n));
-            EM_TRY(tmp.alloc(&nflag, 1));
+            if (fixed) {
+                EM_TRY(noalloc_buffers(ctx, &flagged, &nflag));
+            } else {
+                EM_TRY(tmp.alloc(&flagged, n));
+                EM_TRY(tmp.alloc(&nflag, 1));
+            }
             EM_CUDA(cudaMemsetAsync(nflag, 0, sizeof(int), ctx->stream));
             k_map_fp32<<<em_grid((n + 31) / 32, MQ_WARPS), 32 * MQ_WARPS, 0, ctx->stream>>>(
                 n, pr->pair_i, pr->pair_j, d_x, d_y, d_z, d_h, v->gen, v->radius, v->cell_face_off,
@@ -1012,7 +1027,6 @@ EM_EXPORT int map_exact(em_ctx *ctx, const em_pairs *pr, const double *d_x, cons
                 EM_CUDA(cudaEventRecord(ctx->ev[2], ctx->stream));
             }
             // FP64 recompute of the flagged pairs; the count stays on the device
-            const int fgrid = (int)std::min<int64_t>((n + block / 32 - 1) / (block / 32), (int64_t)ctx->nsm * 64);
             k_map_fp64_flagged<<<fgrid, block, 0, ctx->stream>>>(nflag, pr->pair_i, pr->pair_j, d_x, d_y, d_z, d_h,
                                                                  v->gen, v->radius, v->cell_face_off,
                                                                  v->face_vert_off, v->plane, v->edge, flagged,
@@ -1043,6 +1057,13 @@ EM_EXPORT int map_exact(em_ctx *ctx, const em_pairs *pr, const double *d_x, cons
     return EM_OK;
 }
 
+EM_EXPORT int map_exact(em_ctx *ctx, const em_pairs *pr, const double *d_x, const double *d_y, const double *d_z,
+                        const double *d_h, const double *d_m, const em_voronoi *v, const em_params *p,
+                        double *d_w_out, double *d_rho_out, double *d_wsum_out, int64_t *h_nfp64)
+{
+    return map_exact_run(ctx, pr, d_x, d_y, d_z, d_h, d_m, v, p, d_w_out, d_rho_out, d_wsum_out, h_nfp64, false);
+}
+
 // ---------------------------------------------------------------------------
 // map_exact without allocation, for callers that cannot allocate device
 // memory during the call (their own pool holds all free memory, or they cannot
@@ -1063,9 +1084,11 @@ std::mutex g_noalloc_mutex;
 int32_t *g_noalloc_flagged_addr[NOALLOC_MAX_DEVICES];
 int *g_noalloc_count_addr[NOALLOC_MAX_DEVICES];
 
+}  // namespace
+
 // Device addresses of the two arrays on ctx's device, looked up once per
 // device with that device current.
-int noalloc_buffers(em_ctx *ctx, int32_t **flagged, int **count)
+static int noalloc_buffers(em_ctx *ctx, int32_t **flagged, int **count)
 {
     EM_CHECK_ARG(ctx->device >= 0 && ctx->device < NOALLOC_MAX_DEVICES);
     std::lock_guard<std::mutex> lock(g_noalloc_mutex);
@@ -1090,67 +1113,12 @@ int noalloc_buffers(em_ctx *ctx, int32_t **flagged, int **count)
     return EM_OK;
 }
 
-}  // namespace
-
 EM_EXPORT int map_exact_noalloc(em_ctx *ctx, const em_pairs *pr, const double *d_x, const double *d_y,
                                 const double *d_z, const double *d_h, const double *d_m, const em_voronoi *v,
                                 const em_params *p, double *d_w_out, double *d_rho_out, double *d_wsum_out,
                                 int64_t *h_nfp64)
 {
-    EM_CHECK_ARG(ctx && pr && v && p && pr->ncell == v->ncell);
-    EM_CHECK_ARG(pr->npairs == 0 || (d_x && d_y && d_z && d_h && d_w_out));
-    EM_CHECK_ARG(d_rho_out == nullptr || d_m != nullptr);
-    EM_CHECK_ARG(p->precision == 0 || p->precision == 1);
-    const int64_t n = pr->npairs;
-    if (n > EM_NOALLOC_MAX_PAIRS) {
-        em_set_error("map_exact_noalloc: %lld pairs exceed the fixed capacity of %d pairs", (long long)n,
-                     EM_NOALLOC_MAX_PAIRS);
-        return EM_ECAPACITY;
-    }
-    const int block = p->block_pairs > 0 ? p->block_pairs : 128;
-    EM_CHECK_ARG(block % 32 == 0 && block <= 128);
-    if (h_nfp64) *h_nfp64 = 0;
-    if (n) {
-        if (p->precision == 0) {
-            k_map_fp64<<<(int)std::min<int64_t>((n + block / 32 - 1) / (block / 32), (int64_t)ctx->nsm * 64), block, 0,
-                         ctx->stream>>>(n, pr->pair_i, pr->pair_j, d_x, d_y, d_z, d_h, v->gen, v->radius,
-                                        v->cell_face_off, v->face_vert_off, v->plane, v->edge, d_w_out);
-            EM_LAUNCHED(ctx);
-        } else {
-            int32_t *flagged;
-            int *nflag;
-            EM_TRY(noalloc_buffers(ctx, &flagged, &nflag));
-            EM_CUDA(cudaMemsetAsync(nflag, 0, sizeof(int), ctx->stream));
-            k_map_fp32<<<em_grid((n + 31) / 32, MQ_WARPS), 32 * MQ_WARPS, 0, ctx->stream>>>(
-                n, pr->pair_i, pr->pair_j, d_x, d_y, d_z, d_h, v->gen, v->radius, v->cell_face_off,
-                v->face_vert_off, v->plane_f, v->plane_fl, v->edge_f, v->edge_fl, (float)p->fp64_threshold, em_est_k(p),
-                d_w_out, flagged, nflag);
-            EM_LAUNCHED(ctx);
-            const int fgrid = (int)std::min<int64_t>((n + block / 32 - 1) / (block / 32), (int64_t)ctx->nsm * 64);
-            k_map_fp64_flagged<<<fgrid, block, 0, ctx->stream>>>(nflag, pr->pair_i, pr->pair_j, d_x, d_y, d_z, d_h,
-                                                                 v->gen, v->radius, v->cell_face_off,
-                                                                 v->face_vert_off, v->plane, v->edge, flagged,
-                                                                 d_w_out);
-            EM_LAUNCHED(ctx);
-            if (h_nfp64) {
-                int hflag = 0;
-                EM_CUDA(cudaMemcpyAsync(&hflag, nflag, sizeof(int), cudaMemcpyDeviceToHost, ctx->stream));
-                EM_CUDA(cudaStreamSynchronize(ctx->stream));
-                *h_nfp64 = hflag;
-            }
-        }
-    }
-    if (d_rho_out && v->ncell) {
-        k_cell_density<<<em_grid(v->ncell * 32, 256), 256, 0, ctx->stream>>>(v->ncell, pr->cell_pair_off, pr->pair_i,
-                                                                               d_w_out, d_m, v->volume, d_rho_out);
-        EM_LAUNCHED(ctx);
-    }
-    if (d_wsum_out && pr->np) {
-        k_particle_wsum<<<em_grid(pr->np, 256), 256, 0, ctx->stream>>>(pr->np, pr->part_pair_off, pr->part_pair_idx,
-                                                                        d_w_out, d_wsum_out);
-        EM_LAUNCHED(ctx);
-    }
-    return EM_OK;
+    return map_exact_run(ctx, pr, d_x, d_y, d_z, d_h, d_m, v, p, d_w_out, d_rho_out, d_wsum_out, h_nfp64, true);
 }
 
 // ---------------------------------------------------------------------------
