@@ -62,6 +62,9 @@ def parse():
                     help="factor of the mixed pass's FP32 error estimate in units of 2^-24 (0: 8)")
     ap.add_argument("--h-tol", type=float, default=1e-13,
                     help="Newton tolerance |dh|/h_0 of the node h-solver; the paper runs 1e-2")
+    ap.add_argument("--accuracy-pairs", type=int, default=-1,
+                    help="pairs compared with the FP64 path in mixed mode: a random sample of this size, 0 for "
+                         "all pairs (default: the workload's sample size, all pairs where none is set)")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cache", default=os.path.join(ROOT, "_cache"))
@@ -195,8 +198,9 @@ def run_ours(args, rank, world):
 
     # accuracy of the mixed path against the FP64 path on the same pairs
     acc = {}
-    if args.precision == "mixed" and args.workload in ACCURACY_SAMPLE:
-        acc = sampled_accuracy(api, ctx, out, ACCURACY_SAMPLE[args.workload], device, [float(b) for b in w.box])
+    nsample = args.accuracy_pairs if args.accuracy_pairs >= 0 else ACCURACY_SAMPLE.get(args.workload, 0)
+    if args.precision == "mixed" and nsample > 0:
+        acc = sampled_accuracy(api, ctx, out, nsample, device, [float(b) for b in w.box])
     elif args.precision == "mixed":
         P64 = api.Params(precision=0)
         g = out["g"]

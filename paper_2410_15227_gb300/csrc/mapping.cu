@@ -576,8 +576,9 @@ static_assert(MQ_CHUNK % 32 == 0, "whole rounds of the warp");
 constexpr unsigned FULL_MASK = 0xffffffffu;
 
 struct SegQueue {
-    float sa[MQ_SLOTS][32], hl[MQ_SLOTS][32], A[MQ_SLOTS][32], B2[MQ_SLOTS][32], c4[MQ_SLOTS][32];
-    float dd[MQ_SLOTS][32], Rr[MQ_SLOTS][32], vv[MQ_SLOTS][32], add[MQ_SLOTS][32], scale[MQ_SLOTS][32];
+    float ts[MQ_SLOTS][32], Sa[MQ_SLOTS][32], Ca[MQ_SLOTS][32], hl[MQ_SLOTS][32], A[MQ_SLOTS][32];
+    float B2[MQ_SLOTS][32], c4s[MQ_SLOTS][32], es[MQ_SLOTS][32], Rr[MQ_SLOTS][32], vv[MQ_SLOTS][32];
+    float add[MQ_SLOTS][32], scale[MQ_SLOTS][32];
     int meta[MQ_SLOTS][32];
     int first[MQ_SLOTS][32];            // index of a segment's first 4-node slot among its lane's (INT_MAX if empty)
     float vhi[MQ_CHUNK], vlo[MQ_CHUNK];   // scale * integral of each evaluated slot (float-float)
@@ -637,9 +638,9 @@ __device__ __forceinline__ void mq_flush(SegQueue &q, int lane, int cnt, emq::ff
             const int p = gl4 ? rr : rr >> 1;           // the sub-piece
             const int half = gl4 ? 2 : (rr & 1);        // which 4 nodes of its rule
             const float hl = q.hl[sl][lo];
-            const float val = emq::slot_eval(fmaf(2.f * (float)p + 1.f, hl, q.sa[sl][lo]), hl, half, q.A[sl][lo],
-                                             q.B2[sl][lo], q.c4[sl][lo], q.dd[sl][lo], q.Rr[sl][lo], q.vv[sl][lo],
-                                             q.add[sl][lo], mt);
+            const float val = emq::slot_eval((2.f * (float)p + 1.f) * hl, hl, half, q.ts[sl][lo], q.Sa[sl][lo],
+                                             q.Ca[sl][lo], q.A[sl][lo], q.B2[sl][lo], q.c4s[sl][lo], q.es[sl][lo],
+                                             q.Rr[sl][lo], q.vv[sl][lo], q.add[sl][lo], mt);
             const emq::ff v = emq::ff_two_prod(q.scale[sl][lo], val);
             q.vhi[t - c0] = v.hi;
             q.vlo[t - c0] = v.lo;
@@ -713,31 +714,52 @@ __device__ __forceinline__ void face_consts(emq::ff R2x, bool tilde, FaceState &
     fs.KR = tilde ? kt2 : k3 - kt2;
 }
 
-// Queue the kernel pieces of (D/pi) int over |tau| in [ua, ub] (one g-integral
-// of an edge) with the signed factor sc; the part beyond 2h is added directly.
-__device__ __forceinline__ void mq_push_g(SegQueue &q, int lane, int &cnt, float ua, float ub, float A, float B2,
-                                          float c1, float c4, float cc, float sc, const FaceState &fs, bool tilde,
-                                          emq::ff &acc, float &mag)
+// Queue the kernel pieces of (D/pi) int over |tau| in [ua, ua + du] (one
+// g-integral of an edge) with the signed factor sc; the part beyond 2h is
+// added directly.  du is the range's length from an accurate difference (the
+// edge length L/h, or |T| for a range starting at the foot), and every
+// segment's length in s is formed from such a difference: with a = ua and
+// b = ua + o,
+//     asinh(b/A) - asinh(a/A) = asinh(o (a + b) / (b sqrt(A^2 + a^2) + a sqrt(A^2 + b^2))),
+// an identity whose right side keeps the relative precision of o.  The
+// difference of two asinh values, each rounded to FP32, would carry an
+// absolute error of about 2^-24 |s|, which on a short segment (a small face
+// seen from afar: |T| ~ 1, L/h ~ 0.05) is tens of ulps of the segment, and
+// the error estimate, which counts rounding relative to the segments' sizes,
+// would not see it.  Where a segment starts (sa) needs no such care: shifting
+// a short segment moves its integral only by the integrand's change across it.
+__device__ __forceinline__ void mq_push_g(SegQueue &q, int lane, int &cnt, float ua, float du, float A, float B2,
+                                          emq::ff c1x, emq::ff c4x, emq::ff ccx, float sc, const FaceState &fs,
+                                          bool tilde, emq::ff &acc, float &mag)
 {
+    const float c1 = c1x.hi + c1x.lo, c4 = c4x.hi + c4x.lo;
     const float t1 = c1 < 0.f ? sqrtf(-c1) : 0.f;
     const float t2 = c4 > 0.f ? sqrtf(c4) : 0.f;
     const float iA = 1.f / A;
     const int tflag = tilde ? emq::SEG_TILDE : 0;
-    auto push = [&](int piece, float s0, float s1) {
-        const float len = s1 - s0;
+    // a segment of kernel piece `piece` from tau = ts (s-length len)
+    auto push = [&](int piece, float ts, float len) {
         // 4 points for a short segment, else 8 on sub-pieces of length <= 2
         const bool gl4 = len <= (float)EM_GL4_MAXLEN;
         const float g8 = (piece == 2 && fs.R >= 1.f) ? (float)EM_G8_MAXLEN_FAR : 2.f;
         // m <= ceil(70.5 / g8) <= 141: A >= 1e-30, |tau| <= 2
         const int m = len > g8 ? (int)ceilf(len * (1.f / g8)) : 1;
         const int sl = cnt++;
-        q.sa[sl][lane] = s0;
+        const bool ref1 = piece == 2 && fs.R < 1.f;   // difference split at Q = 1
+        // Q^2 - Rr^2 and 4 - Q^2 at ts, from the edge's float-float
+        // differences and ts^2 as an exact product
+        const emq::ff ts2 = emq::ff_two_prod(ts, ts);
+        const emq::ff es = emq::ff_add(ref1 ? c1x : ccx, ts2);
+        const emq::ff c4s = emq::ff_add(c4x, emq::ff_neg(ts2));
+        const float Sa = ts * iA;
+        q.ts[sl][lane] = ts;
+        q.Sa[sl][lane] = Sa;
+        q.Ca[sl][lane] = sqrtf(fmaf(Sa, Sa, 1.f));
         q.hl[sl][lane] = 0.5f * len / (float)m;
         q.A[sl][lane] = A;
         q.B2[sl][lane] = B2;
-        q.c4[sl][lane] = c4;
-        const bool ref1 = piece == 2 && fs.R < 1.f;   // difference split at Q = 1
-        q.dd[sl][lane] = ref1 ? c1 : cc;
+        q.c4s[sl][lane] = c4s.hi + c4s.lo;
+        q.es[sl][lane] = es.hi + es.lo;
         q.Rr[sl][lane] = ref1 ? 1.f : fs.R;
         q.vv[sl][lane] = ref1 ? 1.f : fs.v;
         q.add[sl][lane] = ref1 ? fs.C1 : 0.f;
@@ -745,19 +767,29 @@ __device__ __forceinline__ void mq_push_g(SegQueue &q, int lane, int &cnt, float
         q.meta[sl][lane] = m | (piece == 1 ? emq::SEG_PIECE1 : 0) | tflag | (gl4 ? emq::SEG_GL4 : 0);
     };
     // piece 1 is |tau| in [ua, b1], piece 2 in [a2, b2]; when both are present
-    // they meet at t1, whose s is computed once
+    // they meet at t1
+    const float ub = ua + du;
     const float b1 = fminf(ub, t1), a2 = fmaxf(ua, t1), b2 = fminf(ub, t2);
     const bool has1 = b1 > ua, has2 = b2 > a2;
     if (has1 || has2) {
-        const float sA = asinhf((has1 ? ua : a2) * iA), sB = asinhf((has2 ? b2 : b1) * iA);
-        const float sM = (has1 && has2) ? asinhf(t1 * iA) : 0.f;
-        if (has1) push(1, sA, has2 ? sM : sB);
-        if (has2) push(2, has1 ? sM : sA, sB);
+        const float ra = sqrtf(fmaf(ua, ua, A * A));
+        // s at ua + o minus s at ua, from the offset o
+        auto ds = [&](float o) {
+            const float b = ua + o;
+            const float rb = sqrtf(fmaf(b, b, A * A));
+            return asinhf(__fdividef(o * (ua + b), fmaf(b, ra, ua * rb)));
+        };
+        // offset in s of the end of the quadrature (ub, or Q = 2), and of Q = 1
+        const float d_end = ds(has2 && ub > t2 ? t2 - ua : du);
+        const float d_mid = (has1 && has2) ? ds(t1 - ua) : 0.f;
+        if (has1) push(1, ua, has2 ? d_mid : d_end);
+        if (has2) push(2, a2, d_end - d_mid);
     }
     if (tilde) {   // beyond 2h: K~(Q) = 0, the integrand is -K~(R) >= 0
         const float a = fmaxf(ua, t2), b = ub;
         if (b > a) {
-            const emq::ff v = emq::ff_two_prod(sc, -fs.KR * atan2f((b - a) * A, A * A + a * b));
+            const float ba = ua >= t2 ? du : du - (t2 - ua);   // b - a from the offsets
+            const emq::ff v = emq::ff_two_prod(sc, -fs.KR * atan2f(ba * A, A * A + a * b));
             acc = emq::ff_add(acc, v);
             mag += fabsf(v.hi);
         }
@@ -886,15 +918,17 @@ __global__ void MQ_LAUNCH_BOUNDS k_map_fp32(int64_t npairs, const int32_t *__res
                 if (a.hi != 0.f) {
                     const emq::ff th = emq::ff_offset_dot(H.ce, Lo.ce, H.ex, Lo.ex, H.ey, Lo.ey, H.ez, Lo.ez, rxx, ryy, rzz);
                     const emq::ff t0 = emq::ff_mul(th, ihh);
-                    const emq::ff t1 = emq::ff_add(t0, emq::ff_mul(emq::ff{H.L, Lo.L}, ihh));
+                    const emq::ff lh = emq::ff_mul(emq::ff{H.L, Lo.L}, ihh);   // L/h
+                    const emq::ff t1 = emq::ff_add(t0, lh);
                     const emq::ff a2 = emq::ff_mul(a, a);
                     // A below 1e-30 h changes the integral by ~1e-30 relative and would
                     // make the s-range of the sinh substitution unbounded
                     const float A = fmaxf(fabsf(a.hi + a.lo), 1e-30f), T0 = t0.hi + t0.lo, T1 = t1.hi + t1.lo;
+                    const float dT = lh.hi + lh.lo;   // T1 - T0 = L/h, from the edge length itself
                     const float B2f = fs.Df * fs.Df + A * A;
                     const emq::ff c1x = emq::ff_add(fs.dm1, a2), c4x = emq::ff_add(fs.d4, emq::ff_neg(a2));
                     const emq::ff ccx = emq::ff_add(a2, emq::ff{-fs.rr2, 0.f});
-                    const float c1 = c1x.hi + c1x.lo, c4 = c4x.hi + c4x.lo, cc = ccx.hi + ccx.lo;
+
                     // signed factor: D/pi, face orientation, side of the edge line, direction along it
                     const float base = fs.sign * (a.hi > 0.f ? 1.f : -1.f) * fs.Df * 0.31830988618379067154f;
                     // the edge's |tau| ranges: one if T0 and T1 lie on one side of
@@ -904,9 +938,10 @@ __global__ void MQ_LAUNCH_BOUNDS k_map_fp32(int64_t npairs, const int32_t *__res
                     const float sc = (one_side ? T1 >= T0 : T1 > T0) ? base : -base;
 #pragma unroll 1
                     for (int part = 0; part < (one_side ? 1 : 2); ++part) {
+                        // one side: [min |T|, min |T| + L/h]; else [0, |T0|] and [0, |T1|]
                         const float ua = one_side ? fminf(u0, u1) : 0.f;
-                        const float ub = one_side ? fmaxf(u0, u1) : (part ? u1 : u0);
-                        mq_push_g(q, lane, cnt, ua, ub, A, B2f, c1, c4, cc, sc, fs, tilde, acc, mag);
+                        const float du = one_side ? dT : (part ? u1 : u0);
+                        mq_push_g(q, lane, cnt, ua, du, A, B2f, c1x, c4x, ccx, sc, fs, tilde, acc, mag);
                     }
                 }
             }

@@ -33,11 +33,13 @@
 //              K3(Q) - K3(R) = d/(4 Q R (Q + R));
 //   R < 1 <= Q: the difference is split at Q = 1 (the same formula with R
 //              replaced by 1), the constant K(1) - K(R) taken in FP64;
-// where d = Q^2 - R^2 = c + tau^2 with c = A^2 - rho^2 per edge in FP64
-// (rho the in-plane distance from the foot to the polygon),
+// where d = Q^2 - R^2 = c + tau^2 with c = A^2 - rho^2 per edge in float-float
+// (rho the in-plane distance from the foot to the polygon), evaluated at each
+// node relative to the segment's start (see the segment fields below),
 // S4(u, v) = u^3 + u^2 v + u v^2 + v^3, S5(Q, R) = Q^4 + Q^3 R + ... + R^4,
-// and u = 2 - Q = (4 - Q^2)/(2 + Q).  tau = A sinh(s) is formed from expm1
-// so that it keeps its relative precision near s = 0.
+// and u = 2 - Q = (4 - Q^2)/(2 + Q).  sinh and cosh of a node's offset from
+// its segment's start are formed from expm1, so that they keep their relative
+// precision for small offsets.
 //
 // The same quadrature integrates the full kernel (K instead of K~) for a
 // particle inside a cell that lies entirely within 2h of it.
@@ -70,13 +72,24 @@ __device__ __forceinline__ void rule_half(int r, float &x0, float &w0, float &x1
 }
 
 // Segment fields (see the header comment):
-//   sa, hl  start of the first sub-piece, half-length of every sub-piece
-//   A, B2   A and B^2 of the edge;  c4 = 4 - B^2 (piece 2)
-//   dd      Q^2 - Rr^2 - tau^2: A^2 - rho^2, or B^2 - 1 when Rr = 1
+//   ts      tau at the segment's start (>= 0); the segment runs from there to
+//           larger |tau|, s = asinh(tau / A) from s(ts)
+//   Sa, Ca  sinh and cosh of s(ts): ts / A and sqrt(1 + (ts/A)^2)
+//   hl      half-length in s of every sub-piece
+//   A, B2   A and B^2 of the edge
+//   es      Q^2 - Rr^2 at ts (float-float sum, rounded once; >= 0)
+//   c4s     4 - Q^2 at ts (piece 2)
 //   Rr      reference distance of the difference (R, or 1)
 //   v       2 - Rr, computed where it keeps its relative precision (piece 2)
 //   add     constant added to the difference: K(1) - K(R) when Rr = 1, else 0
 //   meta    m | piece1 << 8 | tilde << 9 | gl4 << 10, m the number of sub-pieces
+// Each node is placed by its offset delta in s from the segment's start, and
+// everything that cancels is formed from that offset: tau - ts =
+// A (Sa (cosh delta - 1) + Ca sinh delta), Q^2 - Rr^2 = es + (tau - ts)(tau + ts)
+// and 4 - Q^2 = c4s - (tau - ts)(tau + ts), sums whose terms do not cancel.
+// Forming tau^2 itself and subtracting a constant near it instead loses
+// about 2^-24 tau^2 absolutely, which for a small face seen from afar (Q ~ R
+// over the whole face) is many ulps of Q^2 - R^2.
 // The rule: within a piece the integrand is analytic in the strip
 // |Im s| < pi/2 (its singularities are the branch points of Q(s), where
 // B^2 + A^2 sinh^2 s = 0 with B >= A, and the poles of 1/cosh s; the kernel's
@@ -93,12 +106,13 @@ constexpr int SEG_PIECE1 = 1 << 8;
 constexpr int SEG_TILDE = 1 << 9;
 constexpr int SEG_GL4 = 1 << 10;
 
-// One slot: int over the 4 nodes mid +- hl x0, mid +- hl x1 of half r of the
-// rule (see rule_half) of [K(Q(s)) - K(R)] / cosh(s) ds.  Q and 1/Q come from
-// one reciprocal square root and a Newton step (about 1 ulp); the other
-// quotients are reciprocals of quantities bounded away from zero.
-__device__ __forceinline__ float slot_eval(float mid, float hl, int r, float A, float B2, float c4, float dd,
-                                           float Rr, float vr, float add, int meta)
+// One slot: int over the 4 nodes off +- hl x0, off +- hl x1 (offsets from the
+// segment's start) of half r of the rule (see rule_half) of
+// [K(Q(s)) - K(R)] / cosh(s) ds.  Q and 1/Q come from one reciprocal square
+// root and a Newton step (about 1 ulp); the other quotients are reciprocals of
+// quantities bounded away from zero.
+__device__ __forceinline__ float slot_eval(float off, float hl, int r, float ts, float Sa, float Ca, float A,
+                                           float B2, float c4s, float es, float Rr, float vr, float add, int meta)
 {
     const bool piece1 = (meta & SEG_PIECE1) != 0;
     const bool tilde = (meta & SEG_TILDE) != 0;
@@ -107,23 +121,27 @@ __device__ __forceinline__ float slot_eval(float mid, float hl, int r, float A, 
     const float v = piece1 ? Rr : vr;
     const float p2 = v * v, p3 = p2 * v, p4 = p2 * p2;
     const float iRr = __fdividef(1.f, Rr);   // Rr >= 1e-30 wherever it is used
-    float xk[2], wk[2];
-    rule_half(r, xk[0], wk[0], xk[1], wk[1]);
+    const float ts2 = 2.f * ts;
+    float x0, w0, x1, w1;
+    rule_half(r, x0, w0, x1, w1);
     float acc = 0.f;
 #pragma unroll kNodeUnroll
     for (int i = 0; i < 4; ++i) {
-        const float s = fmaf((i & 1) ? -hl : hl, xk[i >> 1], mid);
-        const float em = expm1f(s);
-        const float e = 1.f + em;
-        const float ei = __fdividef(1.f, e);
-        const float ch = 0.5f * (e + ei);
-        const float tau = 0.5f * A * (em * (1.f + ei));
-        const float t2 = tau * tau;
-        const float q2 = B2 + t2;
+        const float xi = (i >> 1) ? x1 : x0, wi = (i >> 1) ? w1 : w0;
+        const float dl = fmaf((i & 1) ? -hl : hl, xi, off);   // offset from the start, > 0
+        const float em = expm1f(dl);
+        const float ei = __fdividef(1.f, 1.f + em);
+        const float sh = 0.5f * em * (1.f + ei);    // sinh delta
+        const float cm = 0.5f * em * em * ei;       // cosh delta - 1
+        const float dt = A * fmaf(Sa, cm, Ca * sh);   // tau - ts
+        const float ch = fmaf(Ca, cm, fmaf(Sa, sh, Ca));   // cosh s
+        const float tau = ts + dt;
+        const float q2 = fmaf(tau, tau, B2);
         float iQ = rsqrtf(q2);
         iQ = iQ * fmaf(-0.5f * q2 * iQ, iQ, 1.5f);
         const float Q = q2 * iQ;
-        const float d = dd + t2;
+        const float dq = dt * (ts2 + dt);           // Q^2 - Q(ts)^2
+        const float d = es + dq;
         const float iq = __fdividef(1.f, Q + Rr);
         float f;
         if (piece1) {
@@ -131,13 +149,13 @@ __device__ __forceinline__ float slot_eval(float mid, float hl, int r, float A, 
             const float phf = (1.f / 6.f) - 0.075f * (Q * Q + R2) + 0.025f * s5 * iq;
             f = tilde ? d * ((0.25f * iq) * iQ * iRr - phf) : d * phf;
         } else {
-            const float u = __fdividef(c4 - t2, 2.f + Q);
+            const float u = __fdividef(c4s - dq, 2.f + Q);
             const float S4 = ((u + v) * u + p2) * u + p3;
             const float br = u * S4 * (1.f + iQ) + p4 * (1.f + 2.f * iQ * iRr);
             const float x = d * iq * (1.f / 120.f) * br;
             f = (tilde ? x : d * iQ * (0.25f * iRr) * iq - x) + add;
         }
-        acc += wk[i >> 1] * __fdividef(f, ch);
+        acc += wi * __fdividef(f, ch);
     }
     return acc * hl;
 }

@@ -142,6 +142,40 @@ def sphere_workload(n: int, ngen: int, sigma: float = 1.0, seed: int = 2,
                     g[:, 2].copy(), _sphere_box(p, h), sources=np.zeros((1, 3)))
 
 
+def dense_cluster(n_sites: int = 400, n_outer: int = 80, n_part: int = 96, radius: float = 0.05,
+                  seed: int = 41) -> Workload:
+    """Tiny cells deep inside large kernels: n_sites sites uniform in a ball of
+    the given radius at the origin, n_outer sites uniform in [-1, 1]^3 beyond
+    three radii, and n_part particles at distance q h from the origin with q
+    uniform in [1.1, 1.6] and h / V^(1/3) uniform in [12, 24], V the mean
+    volume of the ball's cells.  Domain [-1, 1]^3, equal masses summing to 1.
+    The configuration that stresses the mixed pass: the faces of the small
+    cells lie in the kernel's outer shell, where their pyramid terms cancel
+    by about h / V^(1/3)."""
+    rng = np.random.default_rng(seed)
+
+    def ball(n, r):
+        v = rng.normal(size=(n, 3))
+        v /= np.linalg.norm(v, axis=1, keepdims=True)
+        return v * (r * rng.random(n) ** (1.0 / 3.0))[:, None]
+
+    inner = ball(n_sites, radius)
+    outer = []
+    while len(outer) < n_outer:
+        q = rng.uniform(-1.0, 1.0, 3)
+        if np.linalg.norm(q) > 3.0 * radius:
+            outer.append(q)
+    g = np.concatenate([inner, np.array(outer)])
+    ell = (4.0 / 3.0 * np.pi * radius ** 3 / n_sites) ** (1.0 / 3.0)
+    h = ell * rng.uniform(12.0, 24.0, n_part)
+    d = rng.normal(size=(n_part, 3))
+    d /= np.linalg.norm(d, axis=1, keepdims=True)
+    p = d * (h * rng.uniform(1.1, 1.6, n_part))[:, None]
+    return Workload(f"dense_cluster_{n_sites}_{n_part}", p[:, 0].copy(), p[:, 1].copy(), p[:, 2].copy(),
+                    np.full(n_part, 1.0 / n_part), h, g[:, 0].copy(), g[:, 1].copy(), g[:, 2].copy(),
+                    np.array([-1.0, 1.0, -1.0, 1.0, -1.0, 1.0]))
+
+
 # ---------------------------------------------------------------------------
 # The five named workloads.  Pseudo-particle parameters (r_part, r_leaf) are the
 # paper's Table 1 values read as dimensionless radii; theta for the 1e6-particle
