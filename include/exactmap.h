@@ -100,6 +100,21 @@ int em_ctx_set_timing(em_ctx *ctx, int on);
  * recorded events.  Both are 0 if nothing was recorded. */
 int em_ctx_map_times(em_ctx *ctx, double *ms_main, double *ms_recompute);
 
+/* ---- em_measure_peaks ---------------------------------------------------------
+ * Measured arithmetic peaks of the context's device, the denominators of the
+ * roofline of the ALU-bound mapping kernels (map_exact's FP32 pass is bound
+ * by its FP32, integer and special-function work, its FP64 path by the FP64
+ * pipe).  The paper has no counterpart: it is a measurement aid of this
+ * library.  Three of the library's own kernels run independent dependency
+ * chains over a grid of (SMs x resident blocks per SM) for tens of
+ * milliseconds each, timed with CUDA events on the context's stream (median
+ * of three launches after a warm-up); the call synchronises the stream.
+ *   h_out[5] (host): [0] FP32 fused multiply-add rate, TFLOP/s (2 flops each);
+ *   [1] FP64 fused multiply-add rate, TFLOP/s; [2] special-function rate
+ *   (approximate reciprocal square root), Top/s; [3] the device's SM count;
+ *   [4] its maximum SM clock, MHz. */
+int em_measure_peaks(em_ctx *ctx, double *h_out);
+
 /* ---- build_tree ------------------------------------------------------------
  * Morton-ordered octree of n particles (the paper's gravity tree, Section
  * 2.2.1, with an octree in place of the k-d tree; the method is independent

@@ -31,9 +31,11 @@ from dataclasses import dataclass
 import numpy as np
 
 from .build import build as _build
+from .build import build_count as _build_count
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
 _lib = None
+_count_lib = None
 
 
 def lib():
@@ -327,6 +329,31 @@ def map_exact_list(pi, pj, x, y, z, h, cells: Cells, nthreads=None) -> np.ndarra
     pi, pj = _i64a(pi), _i64a(pj)
     return map_exact(Pairs(pi, pj, np.zeros_like(pi, dtype=np.uint8), np.zeros(1, np.int64)),
                      x, y, z, h, cells, nthreads)
+
+
+WORK_FIELDS = ("right_subtriangles", "add", "mul", "div", "sqrt", "transcendental")
+
+
+def count_map_exact(pairs: Pairs, x, y, z, h, cells: Cells, nthreads=None):
+    """map_exact with its algorithmic work counted per pair (count.cpp): the
+    weights (bit-identical to map_exact's) and an (npairs, 6) array of counts
+    in the order of WORK_FIELDS -- right sub-triangles evaluated, FP64
+    additions/subtractions, multiplications, divisions, square roots and
+    transcendental calls (atan2, asinh, pow) of the closed form."""
+    global _count_lib
+    if _count_lib is None:
+        _count_lib = C.CDLL(_build_count())
+        _count_lib.orc_count_map_exact.restype = None
+        _count_lib.orc_count_map_exact.argtypes = [_i64, _p, _p, _p, _p, _p, _p, _p, _p, _p, _p, _p, _p, _i32]
+    x, y, z, h = _f64(x), _f64(y), _f64(z), _f64(h)
+    pi, pj = _i64a(pairs.pair_i), _i64a(pairs.pair_j)
+    w = np.zeros(pi.shape[0])
+    counts = np.zeros((pi.shape[0], 6), np.uint64)
+    _count_lib.orc_count_map_exact(pi.shape[0], _ptr(pi), _ptr(pj), _ptr(x), _ptr(y), _ptr(z), _ptr(h),
+                                   _ptr(_i64a(cells.cell_face_off)), _ptr(_i64a(cells.face_vert_off)),
+                                   _ptr(_f64(cells.verts)), _ptr(_f64(cells.normals)), _ptr(w), _ptr(counts),
+                                   nthreads or nthreads_default())
+    return w, counts
 
 
 def cell_density(pairs: Pairs, w, m, volume) -> np.ndarray:
@@ -669,4 +696,47 @@ def refine(x, y, z, m, h_particle, box, sources, r_part, r_leaf, theta, cells: C
             r_part += leaf_step
             r_leaf += leaf_step
     return ps, t, sel, force, max_iter, fn, (r_part, r_leaf)
+
+
+# ---------------------------------------------------------------------------
+# Bounded samples of a workload (the CPU baseline and the work counts)
+# ---------------------------------------------------------------------------
+
+def workload_sample(w, theta, ntarget=64, seed=7, pseudo=True, complete=False, nthreads=None):
+    """A bounded sample of a workload built by the oracle alone: `ntarget`
+    random pseudo-particles of the oracle's own tree and selection on the cloud
+    (Sections 2.2, 2.4; nodes get h from the h-solver against the whole
+    population) -- or random particles when the workload maps particles
+    directly -- with the oracle's brute-force cells and pairs around them.
+    complete=False takes the cells whose generators lie within 2h of a sampled
+    particle (a subset of its pairs); complete=True takes every cell that can
+    reach within 2h, from the bound |g - p| <= 4h + d_p (d_p the distance to
+    the nearest generator), so the sampled particles' pair lists are whole.
+    Returns ((x, y, z, h) of the sampled particles, cells, pairs)."""
+    pr = w.params
+    rng = np.random.default_rng(seed)
+    if not pseudo:      # the particles themselves
+        tg = np.sort(rng.choice(w.n, ntarget, replace=False))
+        px, py, pz, h = w.x[tg], w.y[tg], w.z[tg], w.h[tg]
+    else:
+        ps, tree, sel = make_pseudo_particles(w.x, w.y, w.z, w.m, w.h, w.box, np.zeros((1, 3)), pr["r_part"],
+                                              pr["r_leaf"], theta, h_fact=pr["h_fact"], solve=False)
+        tg = np.sort(rng.choice(ps.n, ntarget, replace=False))
+        h = ps.h[tg].copy()
+        node = ps.origin[tg] > 0
+        if node.any():
+            ids = sel.ref[tg[node]]
+            h0 = h_initial(tree, ids, w.h, pr["h_fact"])
+            h[node] = h_solve(tree.com[sel.pop_node], tree.com[ids], h0, pr["h_fact"], 1e-13, 50,
+                              nthreads)[0]
+        px, py, pz = ps.x[tg], ps.y[tg], ps.z[tg]
+    gen = np.stack([w.gx, w.gy, w.gz], 1)
+    near = np.zeros(w.ngen, bool)
+    for a in range(px.shape[0]):
+        d2 = np.einsum("ij,ij->i", gen - (px[a], py[a], pz[a]), gen - (px[a], py[a], pz[a]))
+        reach = 4.0 * h[a] + np.sqrt(d2.min()) if complete else 2.0 * h[a]
+        near |= d2 < reach * reach + (1e-12 if complete else 0.0)
+    cells = voronoi(w.gx, w.gy, w.gz, w.box, cells=np.flatnonzero(near), nthreads=nthreads)
+    pairs = find_pairs(px, py, pz, h, cells, nthreads)
+    return (px, py, pz, h), cells, pairs
 

@@ -31,6 +31,12 @@
 
 #define ORC_PI 3.14159265358979323846
 
+/* Work counting (count.cpp builds this file a second time with a counting
+ * number type and defines this hook); a no-op in the oracle itself. */
+#ifndef ORC_COUNT_TRIANGLE
+#define ORC_COUNT_TRIANGLE()
+#endif
+
 /* ------------------------------------------------------------------------ */
 /* M4 cubic spline                                                          */
 /* ------------------------------------------------------------------------ */
@@ -136,6 +142,7 @@ static double dprim(int region, double A, double B, double D, double tau)
 double orc_right_triangle(double D, double A, double T)
 {
     if (D <= 0.0 || A <= 0.0 || T == 0.0) return 0.0;
+    ORC_COUNT_TRIANGLE();
     double sgn = T < 0.0 ? -1.0 : 1.0;
     T = fabs(T);
     double B = sqrt(D * D + A * A);

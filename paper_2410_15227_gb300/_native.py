@@ -51,6 +51,7 @@ SIGNATURES = {
     "em_ctx_launch_count": (I64, [P]),
     "em_ctx_set_timing": (I32, [P, I32]),
     "em_ctx_map_times": (I32, [P, P, P]),
+    "em_measure_peaks": (I32, [P, P]),
     "build_tree": (I32, [P, I64, P, P, P, P, P, I32, PP]),
     "tree_info": (I32, [P, PI64, PI64, PI32]),
     "tree_get": (I32, [P, P] + [P] * 11),

@@ -85,6 +85,14 @@ class Context:
         N.call("em_ctx_map_times", self.handle, C.byref(a), C.byref(b))
         return a.value, b.value
 
+    def measure_peaks(self) -> dict:
+        """Measured FP32 and FP64 FMA rates (TFLOP/s), special-function rate
+        (Top/s), SM count and maximum SM clock (MHz) of the device."""
+        out = (C.c_double * 5)()
+        N.call("em_measure_peaks", self.handle, C.cast(out, C.c_void_p))
+        return dict(fp32_tflops=out[0], fp64_tflops=out[1], xu_tops=out[2], sm_count=int(out[3]),
+                    sm_clock_mhz=out[4])
+
     def close(self):
         if getattr(self, "handle", None):
             N.lib().em_ctx_destroy(self.handle)

@@ -211,6 +211,16 @@ def workload_pseudo_1e6(theta: float | None = None) -> Workload:
     return w
 
 
+def workload_pseudo_2e5() -> Workload:
+    """A fifth of the benchmark cloud: 2e5 particles of the sphere profile (seed
+    6, m = 5e-6), 52,428 generators drawn from them; theta = 0.12 selects
+    19,241 pseudo-particles.  The profiling case of the pseudo-particle path."""
+    w = sphere_workload(200_000, 52_428, 1.0, seed=6, field_seed=2, gen_seed=6,
+                        name="pseudo_200k_particles_52k_cells")
+    w.params = dict(PSEUDO_PARAMS, theta=0.12)
+    return w
+
+
 def workload_batched(nsnap: int = 64):
     """64 independent sphere snapshots, N_s log-uniform in [1e3, 1e5] (seed 100+s),
     generators 0.25 N_s."""

@@ -36,3 +36,19 @@ def test_reference_arm_batched_is_unavailable():
                           "--workload", "batched_64"], capture_output=True, text=True, check=True, cwd=ROOT)
     line = json.loads(out.stdout.strip().splitlines()[-1])
     assert line["impl"] == "reference" and "unavailable" in line
+
+
+def test_roofline_follows_the_counted_work_and_measured_peaks():
+    """achieved = the oracle-counted work per pair x pairs / time, against the
+    measured peak of the executing pipe; nominal figures only beside it."""
+    peaks = dict(fp32_tflops=70.0, fp64_tflops=1.1, xu_tops=4.5, sm_count=152, sm_clock_mhz=2070.0)
+    r = bench.roofline(24_000_000, 120.0, "mixed", "pseudo_1e6", peaks, 2070.0)
+    aw = bench.ALGO_WORK["pseudo_1e6"]
+    assert abs(r["achieved"] - 24e6 * aw["flops"] / 0.12 / 1e12) < 1e-9
+    assert r["peak"] == 70.0 and abs(r["frac"] - r["achieved"] / 70.0) < 1e-12
+    assert r["pipe"] == "fp32" and r["nominal_peak"] > r["peak"]
+    assert abs(r["sfu"]["achieved"] - 24e6 * (aw["sqrt"] + aw["transcendental"]) / 0.12 / 1e12) < 1e-9
+    assert "implementation" in r
+    r64 = bench.roofline(24_000_000, 4000.0, "fp64", "pseudo_1e6", peaks, None)
+    assert r64["peak"] == 1.1 and r64["kernel"] == "k_map_fp64" and "implementation" not in r64
+    assert bench.roofline(1, 1.0, "mixed", "full_8m", peaks) is None
