@@ -69,6 +69,9 @@ def parse():
     ap.add_argument("--accuracy-pairs", type=int, default=-1,
                     help="pairs compared with the FP64 path in mixed mode: a random sample of this size, 0 for "
                          "all pairs (default: the workload's sample size, all pairs where none is set)")
+    ap.add_argument("--no-autotune", action="store_true",
+                    help="mixed mode: keep the FP32 pass's default launch shape instead of tuning it on the workload "
+                         "(map_autotune, cached by device and workload in --cache/autotune.json)")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cache", default=os.path.join(ROOT, "_cache"))
@@ -205,6 +208,16 @@ def run_ours(args, rank, world):
     for _ in range(max(args.warmup, 0)):
         out = step(*X, *G, f_cell)
     torch.cuda.synchronize()
+    tuned = None
+    if args.precision == "mixed" and not args.no_autotune:
+        # the FP32 pass's launch shape, tuned on this workload's pairs (each shape is
+        # deterministic; the shapes agree to the mixed mode's tolerance)
+        g = out["g"]
+        tune = lambda: api.map_autotune(ctx, out["pr"], g["x"], g["y"], g["z"], g["h"], out["vor"], P)
+        cache = os.path.join(args.cache, "autotune.json") if args.cache else None
+        variant, ms, hit = api.autotune_cached(ctx, f"{args.workload}_theta{args.theta}", cache, tune)
+        P.fp32_variant = variant
+        tuned = {"variant": variant, "ms_per_variant": ms, "cached": hit}
 
     # accuracy of the mixed path against the FP64 path on the same pairs
     acc = {}
@@ -277,9 +290,10 @@ def run_ours(args, rank, world):
                        "pseudo_particles": out["npseudo"] if pseudo else None, "pairs_per_step": out["npairs"],
                        "theta": args.theta, "r_part": w.params["r_part"], "r_leaf": w.params["r_leaf"],
                        "precision": args.precision, "fp64_threshold": args.fp64_threshold, "h_tol": args.h_tol,
-                       "fp32_err_ulps": err_ulps(args), "l2": "flushed between steps (258 MiB write)", "parallelism": f"replicas x{world}"},
+                       "fp32_err_ulps": err_ulps(args), "fp32_variant": P.fp32_variant,
+                       "l2": "flushed between steps (258 MiB write)", "parallelism": f"replicas x{world}"},
                map_exact_ms=statistics.mean(t_map), map_exact_pairs_per_s=out["npairs"] / (statistics.mean(t_map) * 1e-3),
-               accuracy=acc, gpu_launches=launches, clocks=ck)
+               accuracy=acc, gpu_launches=launches, clocks=ck, autotune=tuned)
     k_main = statistics.mean(k[0] for k in kernel_ms)
     k_re = statistics.mean(k[1] for k in kernel_ms)
     res["map_exact_kernels_ms"] = {"main": k_main, "fp64_recompute": k_re}
@@ -298,9 +312,14 @@ def err_ulps(args):
 
 def run_batched(args, rank, world):
     """64 independent snapshots (N_s log-uniform in [1e3, 1e5], a quarter as
-    many sites) through map_batch, the whole path per snapshot.  The work
-    spans several streams and map_batch returns when all have finished, so a
-    step is timed by the host clock between two device synchronisations."""
+    many sites) through map_batch: the front stages per snapshot on host
+    threads with a stream each, then one mapping of every pair of the batch.
+    The FP32 pass's launch shape is tuned once on the batch (map_autotune,
+    cached by device and workload in --cache/autotune.json).  The work spans
+    several streams and map_batch returns when all have finished, so a step is
+    timed by the host clock between two device synchronisations.  Beside it:
+    the one-worker step, and the batch mapped in FP64 (the mapping's device
+    time and the cell densities' difference)."""
     import numpy as np
     import torch
 
@@ -317,48 +336,82 @@ def run_batched(args, rank, world):
     pp = inputs.PSEUDO_PARAMS
     P = api.Params(r_part=pp["r_part"], r_leaf=pp["r_leaf"], theta=args.theta, h_fact=pp["h_fact"],
                    h_tol=args.h_tol, precision=1 if args.precision == "mixed" else 0,
-                   fp64_threshold=args.fp64_threshold)
+                   fp64_threshold=args.fp64_threshold, fp32_err_ulps=err_ulps(args))
     flush = torch.empty(2 * L2_BYTES // 8, dtype=torch.float64, device=device)
+    ctx = api.Context(dev_index)
+    peaks = ctx.measure_peaks()
 
-    def step(nworkers):
+    def step(nworkers, params, tune=False):
         flush.zero_()
         torch.cuda.synchronize()
+        info = {}
         t = time.perf_counter()
-        res, launches = api.map_batch(dev_index, snaps, P, nworkers=nworkers)
+        res, launches = api.map_batch(dev_index, snaps, params, nworkers=nworkers, tune=tune, info=info)
         torch.cuda.synchronize()
-        return (time.perf_counter() - t) * 1e3, sum(r["npairs"] for r in res), launches, res
+        return (time.perf_counter() - t) * 1e3, sum(r["npairs"] for r in res), launches, res, info
 
+    tuned = None
+    if args.precision == "mixed":
+        def tune():
+            _, _, _, _, info = step(args.workers, P, tune=True)
+            return info["variant"], None
+        cache = os.path.join(args.cache, "autotune.json") if args.cache else None
+        variant, _, hit = api.autotune_cached(ctx, f"batched_64_theta{args.theta}", cache, tune)
+        P.fp32_variant = variant
+        tuned = {"variant": variant, "cached": hit}
     for _ in range(args.warmup):
-        step(args.workers)
-    serial_ms = min(step(1)[0] for _ in range(2))
+        out = step(args.workers, P)
+    serial_ms = min(step(1, P)[0] for _ in range(2))
     if world > 1:
         torch.distributed.barrier()
     torch.cuda.synchronize()
     clocks = ClockSampler(dev_index)
     clocks.start()
-    t_ms, npairs, launches = 0.0, 0, 0
+    t_ms, npairs, launches, map_ms = 0.0, 0, 0, []
     for _ in range(args.steps):
-        ms, n, nl, res = step(args.workers)
+        ms, n, nl, res, info = step(args.workers, P)
         t_ms += ms
         npairs += n
         launches += nl
+        map_ms.append(info["map_ms"])
     if world > 1:
         torch.distributed.barrier()
     ck = clocks.stop()
     tmax, units = reduce_over_ranks(t_ms, npairs, world, device)
     per_step = npairs // args.steps
-    return dict(metric=METRIC, value=units / (tmax * 1e-3), unit="pairs/s", n_gpus=world, steps=args.steps,
-                warmup=args.warmup, ms_per_step=tmax / args.steps, higher_is_better=True, scaling="weak",
-                vs_baseline=None, dtype="f32+f64" if args.precision == "mixed" else "f64", data="synthetic",
-                config={"workload": WORKLOADS[args.workload][0], "snapshots": len(ws),
-                        "particles": int(sum(w.n for w in ws)), "cells": int(sum(w.ngen for w in ws)),
-                        "pseudo_particles": int(sum(r["npseudo"] for r in res)), "pairs_per_step": per_step,
-                        "theta": args.theta, "r_part": pp["r_part"], "r_leaf": pp["r_leaf"],
-                        "precision": args.precision, "fp64_threshold": args.fp64_threshold, "h_tol": args.h_tol,
-                        "workers": args.workers, "timing": "host clock between device syncs around map_batch",
-                        "l2": "flushed between steps (258 MiB write)", "parallelism": f"replicas x{world}"},
-                serial_ms_per_step=serial_ms, serial_pairs_per_s=per_step / (serial_ms * 1e-3),
-                gpu_launches=launches, clocks=ck, roofline=None, e2e=None, cpu_baseline=None)
+    k_main = statistics.mean(m[0] for m in map_ms)
+    k_re = statistics.mean(m[1] for m in map_ms)
+    out = dict(metric=METRIC, value=units / (tmax * 1e-3), unit="pairs/s", n_gpus=world, steps=args.steps,
+               warmup=args.warmup, ms_per_step=tmax / args.steps, higher_is_better=True, scaling="weak",
+               vs_baseline=None, dtype="f32+f64" if args.precision == "mixed" else "f64", data="synthetic",
+               config={"workload": WORKLOADS[args.workload][0], "snapshots": len(ws),
+                       "particles": int(sum(w.n for w in ws)), "cells": int(sum(w.ngen for w in ws)),
+                       "pseudo_particles": int(sum(r["npseudo"] for r in res)), "pairs_per_step": per_step,
+                       "theta": args.theta, "r_part": pp["r_part"], "r_leaf": pp["r_leaf"],
+                       "precision": args.precision, "fp64_threshold": args.fp64_threshold, "h_tol": args.h_tol,
+                       "workers": args.workers, "fp32_variant": P.fp32_variant,
+                       "timing": "host clock between device syncs around map_batch",
+                       "l2": "flushed between steps (258 MiB write)", "parallelism": f"replicas x{world}"},
+               map_exact_kernels_ms={"main": k_main, "fp64_recompute": k_re},
+               map_exact_pairs_per_s=per_step / ((k_main + k_re) * 1e-3), autotune=tuned,
+               serial_ms_per_step=serial_ms, serial_pairs_per_s=per_step / (serial_ms * 1e-3),
+               gpu_launches=launches, clocks=ck, measured_peaks=peaks, e2e=None, cpu_baseline=None)
+    out["roofline"] = roofline(per_step, k_main, args.precision, "pseudo_1e6", peaks, ck["sm_mhz"] if ck else None)
+    if out["roofline"]:
+        out["roofline"]["work"] += " (the 1e6 cloud's count, same profile)"
+    if args.precision == "mixed":
+        # the same batch with every pair in FP64: the mapping's time, and how far
+        # the mixed cell densities are from the FP64 ones
+        P64 = api.Params(r_part=pp["r_part"], r_leaf=pp["r_leaf"], theta=args.theta, h_fact=pp["h_fact"],
+                         h_tol=args.h_tol, precision=0)
+        _, _, _, res64, info64 = step(args.workers, P64)
+        rel = max(float(((a["rho"] - b["rho"]).abs() / b["rho"].abs().clamp_min(1e-300)).max())
+                  for a, b in zip(res, res64))
+        out["fp64"] = {"map_exact_ms": info64["map_ms"][0],
+                       "map_exact_pairs_per_s": per_step / (info64["map_ms"][0] * 1e-3),
+                       "max_rel_err_rho_mixed_vs_fp64": rel,
+                       "fp64_recomputed_frac_mixed": sum(r["nfp64"] for r in res) / max(per_step, 1)}
+    return out
 
 
 def sampled_accuracy(api, ctx, out, nsample, device, box, seed=11):

@@ -73,7 +73,9 @@ typedef struct {
                                the neighbour search and solver are skipped (Section 2.4.2; the paper uses 10^6); 0 = never */
     int fp32_err_ulps;      /* map_exact mixed mode: a pair goes to FP64 when fp32_err_ulps 2^-24 times the sum of the
                                magnitudes of its FP32 pieces exceeds max(fp64_threshold |w|, 1e-14); 0 = the default 8 */
-    int reserved[3];
+    int fp32_variant;       /* map_exact mixed mode: launch shape of the FP32 pass, 0..EM_FP32_VARIANTS-1 (0 = default;
+                               see map_autotune); results are deterministic per shape */
+    int reserved[2];
 } em_params;
 
 void em_params_default(em_params *p);
@@ -275,6 +277,25 @@ int map_exact(em_ctx *ctx, const em_pairs *pr, const double *d_x, const double *
               const double *d_h, const double *d_m, const em_voronoi *v, const em_params *p,
               double *d_w_out, double *d_rho_out, double *d_wsum_out, int64_t *h_nfp64);
 
+/* ---- map_autotune ------------------------------------------------------------
+ * Launch shape of map_exact's FP32 pass for a workload: times the pass in
+ * each of its EM_FP32_VARIANTS launch shapes (warps per block, minimum
+ * resident blocks per SM) on the given pairs and cells -- a warm-up launch,
+ * then the median of three launches timed with CUDA events on the context's
+ * stream -- and returns the fastest in *h_best, to be passed as
+ * em_params.fp32_variant.  The paper has no counterpart (a tuning aid of this
+ * library).  Each shape is deterministic; the shapes are compiled separately
+ * and agree to the mixed mode's tolerance, not bit for bit (the compiler may
+ * fuse a multiply and an add differently in each).  Writes nothing but its
+ * outputs; synchronises the stream.
+ *   arguments as for map_exact (masses are not needed); p supplies
+ *   fp64_threshold and fp32_err_ulps
+ *   h_best (host): the fastest variant; h_ms (host, may be NULL):
+ *   [EM_FP32_VARIANTS] milliseconds per launch of each variant. */
+#define EM_FP32_VARIANTS 4
+int map_autotune(em_ctx *ctx, const em_pairs *pr, const double *d_x, const double *d_y, const double *d_z,
+                 const double *d_h, const em_voronoi *v, const em_params *p, int *h_best, double *h_ms);
+
 /* ---- map_exact_noalloc -------------------------------------------------------
  * The same computation and results as map_exact (bit-identical w, rho, u and
  * FP64 count), for callers that cannot allocate device memory during the
@@ -312,14 +333,17 @@ int map_back(em_ctx *ctx, const em_pairs *pr, const double *d_w, const double *d
              const em_pseudo *ps, const em_tree *t, double *d_f_particle_out);
 
 /* ---- map_batch ------------------------------------------------------------------
- * Many independent snapshots through the whole path: build_tree,
- * make_pseudo_particles (a node that keeps h_0 is not an error here),
- * build_voronoi, find_pairs, map_exact, and map_back when a cell field is
- * given.  Same results, bit for bit, as those calls made one snapshot at a
- * time with the same parameters.  Snapshots go to nworkers host threads
- * (1..64), each with its own context on its own non-blocking stream on
- * `device`, largest first (by n + ngen).  Returns when every snapshot has
- * finished.
+ * Many independent snapshots through the whole path (the paper's runtime
+ * study runs many snapshots, Section 3): build_tree, make_pseudo_particles
+ * (a node that keeps h_0 is not an error here), build_voronoi and
+ * find_pairs per snapshot on nworkers host threads (1..64), each with its own
+ * context on its own non-blocking stream on `device`, largest snapshot first
+ * (by n + ngen); then every pair of every snapshot mapped by ONE map_exact
+ * over the concatenated pseudo-particles, cells and pair lists (one launch of
+ * the FP32 pass and one of the FP64 recompute in mixed mode, one FP64 launch
+ * in FP64 mode), and map_back per snapshot when a cell field is given.
+ * Same results, bit for bit, as those calls made one snapshot at a time with
+ * the same parameters.  Returns when every snapshot has finished.
  * Per snapshot (caller-owned; device arrays on `device`):
  *   in:  n particles d_x, d_y, d_z, d_m, d_h; ngen sites d_gx, d_gy, d_gz;
  *        box (as h_box of build_tree); nsrc sources h_src (host, xyz);
@@ -328,8 +352,17 @@ int map_back(em_ctx *ctx, const em_pairs *pr, const double *d_w, const double *d
  *        d_f_cell is) the cell field mapped back onto the particles;
  *        npseudo, npairs, nfp64 (pairs recomputed in FP64); status (em_status,
  *        -1 if the snapshot did not run)
+ * tune != 0 (mixed mode): the FP32 pass's launch shape is chosen by
+ * map_autotune on the batch's concatenated pairs before the mapping;
+ * otherwise p->fp32_variant.  *h_variant (may be NULL): the shape used; the
+ * results equal the per-snapshot calls made with that shape.
+ * h_map_ms (host, may be NULL): [2] device milliseconds of the batch's
+ * mapping: the main pass (FP32 pass, or FP64 kernel) and the FP64 recompute.
+ * The batch's totals must stay below 2^31 particles, cells and pairs
+ * (EM_ECAPACITY otherwise).
  * Returns EM_OK, or the first failing snapshot's status with its index in
- * em_last_error().  *h_launches (may be NULL): kernels launched in all. */
+ * em_last_error(); the snapshots whose front stages succeeded are still
+ * mapped.  *h_launches (may be NULL): kernels launched in all. */
 typedef struct {
     int64_t n;
     const double *d_x, *d_y, *d_z, *d_m, *d_h;
@@ -345,7 +378,8 @@ typedef struct {
     int status;
 } em_snapshot;
 
-int map_batch(int device, int nsnap, em_snapshot *snaps, const em_params *p, int nworkers, int64_t *h_launches);
+int map_batch(int device, int nsnap, em_snapshot *snaps, const em_params *p, int nworkers, int tune,
+              int *h_variant, double *h_map_ms, int64_t *h_launches);
 
 #ifdef __cplusplus
 }

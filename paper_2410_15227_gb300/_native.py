@@ -21,7 +21,7 @@ class EmParams(C.Structure):
                 ("h_fact", C.c_double), ("h_tol", C.c_double), ("max_newton", C.c_int),
                 ("precision", C.c_int), ("fp64_threshold", C.c_double), ("knn_k", C.c_int),
                 ("leaf_max", C.c_int), ("block_pairs", C.c_int), ("h0_above", C.c_int),
-                ("fp32_err_ulps", C.c_int), ("reserved", C.c_int * 3)]
+                ("fp32_err_ulps", C.c_int), ("fp32_variant", C.c_int), ("reserved", C.c_int * 2)]
 
 
 class EmSnapshot(C.Structure):
@@ -67,7 +67,7 @@ SIGNATURES = {
     "voronoi_info": (I32, [P, PI64, PI64, PI64]),
     "voronoi_centroids": (I32, [P, P, P, P, P]),
     "lloyd": (I32, [P, I64, P, P, P, P, I32, PPAR]),
-    "map_batch": (I32, [I32, I32, C.POINTER(EmSnapshot), PPAR, I32, PI64]),
+    "map_batch": (I32, [I32, I32, C.POINTER(EmSnapshot), PPAR, I32, I32, PI32, P, PI64]),
     "voronoi_get": (I32, [P, P] + [P] * 6),
     "voronoi_destroy": (I32, [P]),
     "find_pairs": (I32, [P, I64, P, P, P, P, P, PP, PI64]),
@@ -77,6 +77,7 @@ SIGNATURES = {
     "pairs_destroy": (I32, [P]),
     "map_exact": (I32, [P, P, P, P, P, P, P, P, PPAR, P, P, P, PI64]),
     "map_exact_noalloc": (I32, [P, P, P, P, P, P, P, P, PPAR, P, P, P, PI64]),
+    "map_autotune": (I32, [P, P, P, P, P, P, P, PPAR, PI32, P]),
     "map_back": (I32, [P, P, P, P, P, P, P, P]),
 }
 

@@ -31,6 +31,7 @@ class Params:
     block_pairs: int = 0
     h0_above: int = 0             # > 0: with more pseudo-particles than this, every node takes h_0 (Eq. 11)
     fp32_err_ulps: int = 8        # mixed mode: factor of the FP32 error estimate, in units of 2^-24
+    fp32_variant: int = 0         # mixed mode: launch shape of the FP32 pass (map_autotune)
 
     def native(self) -> N.EmParams:
         p = N.EmParams()
@@ -314,11 +315,15 @@ def lloyd(ctx: Context, gx, gy, gz, box, iters: int = 5, params: Params | None =
     return gx, gy, gz
 
 
-def map_batch(device: int, snapshots, params: Params, nworkers: int = 4):
-    """Independent snapshots through the whole path (build_tree ... map_exact,
-    map_back when a cell field is given) on nworkers host threads with a
-    stream each.  snapshots: dicts with device tensors x, y, z, m, h, gx, gy,
-    gz, box (6 numbers), sources ((k, 3) numbers) and optionally f_cell.
+def map_batch(device: int, snapshots, params: Params, nworkers: int = 4, tune: bool = False, info: dict | None = None):
+    """Independent snapshots through the whole path: build_tree ...
+    find_pairs per snapshot on nworkers host threads with a stream each, then
+    one map_exact over all snapshots' pairs, and map_back when a cell field is
+    given.  snapshots: dicts with device tensors x, y, z, m, h, gx, gy, gz, box
+    (6 numbers), sources ((k, 3) numbers) and optionally f_cell.  tune: pick
+    the FP32 pass's launch shape on the batch (map_autotune).  info (optional
+    dict) receives the launch shape used ("variant") and the mapping's device
+    milliseconds ("map_ms": main pass, FP64 recompute).
     Returns one dict per snapshot: rho, f (or None), npseudo, npairs, nfp64,
     status, and the total kernel launches."""
     n = len(snapshots)
@@ -349,7 +354,13 @@ def map_batch(device: int, snapshots, params: Params, nworkers: int = 4):
         outs.append((rho, f))
     p = params.native()
     launches = C.c_int64()
-    rc = N.lib().map_batch(int(device), n, arr, C.byref(p), int(nworkers), C.byref(launches))
+    variant = C.c_int32()
+    ms = (C.c_double * 2)()
+    rc = N.lib().map_batch(int(device), n, arr, C.byref(p), int(nworkers), int(bool(tune)), C.byref(variant),
+                           C.cast(ms, C.c_void_p), C.byref(launches))
+    if info is not None:
+        info["variant"] = variant.value
+        info["map_ms"] = (ms[0], ms[1])
     res = [dict(rho=outs[k][0], f=outs[k][1], npseudo=arr[k].npseudo, npairs=arr[k].npairs,
                 nfp64=arr[k].nfp64, status=arr[k].status) for k in range(n)]
     if rc != N.EM_OK:
@@ -406,6 +417,44 @@ def map_exact(ctx: Context, pairs: Pairs, x, y, z, h_, m, vor: Voronoi, params: 
            C.byref(p), _ptr(w, f64, npairs), _ptr(rho, f64, nc), _ptr(wsum),
            C.byref(nfp64) if want_count else None)
     return w, rho, wsum, nfp64.value if want_count else None
+
+
+FP32_VARIANTS = 4
+
+
+def map_autotune(ctx: Context, pairs: Pairs, x, y, z, h_, vor: Voronoi, params: Params):
+    """The fastest launch shape of map_exact's FP32 pass on these pairs:
+    (variant for Params.fp32_variant, milliseconds of each variant)."""
+    npairs, np_, _ = pairs.info()
+    best = C.c_int32()
+    ms = (C.c_double * FP32_VARIANTS)()
+    p = params.native()
+    N.call("map_autotune", ctx.handle, pairs.handle, _ptr(x, f64, np_, "x"), _ptr(y, f64, np_, "y"),
+           _ptr(z, f64, np_, "z"), _ptr(h_, f64, np_, "h"), vor.handle, C.byref(p), C.byref(best),
+           C.cast(ms, C.c_void_p))
+    return best.value, list(ms)
+
+
+def autotune_cached(ctx: Context, key: str, cache_path: str, tune):
+    """A tuned variant from a JSON cache keyed by device name and workload
+    key, or tune() (returning (variant, ms list)) and store its result."""
+    import json
+    import os
+    dev = torch.cuda.get_device_name(ctx.device)
+    cache = {}
+    if cache_path and os.path.exists(cache_path):
+        with open(cache_path) as f:
+            cache = json.load(f)
+    hit = cache.get(dev, {}).get(key)
+    if hit is not None:
+        return int(hit["variant"]), hit.get("ms"), True
+    variant, ms = tune()
+    if cache_path:
+        cache.setdefault(dev, {})[key] = {"variant": int(variant), "ms": ms}
+        os.makedirs(os.path.dirname(os.path.abspath(cache_path)), exist_ok=True)
+        with open(cache_path, "w") as f:
+            json.dump(cache, f, indent=1)
+    return int(variant), ms, False
 
 
 def map_exact_noalloc(ctx: Context, pairs: Pairs, x, y, z, h_, m, vor: Voronoi, params: Params,

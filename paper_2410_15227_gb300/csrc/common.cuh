@@ -200,6 +200,12 @@ struct em_pairs {
 
 int em_prepare_cells(em_ctx *ctx, em_voronoi *v);                 // derived geometry
 int em_build_pair_index(em_ctx *ctx, em_pairs *pr);               // CSR offsets + transpose
+// map_exact's body (mapping.cu); d_flag_buf / d_flag_count: optional scratch
+// for the mixed pass's flagged pairs (npairs entries), read back by map_batch
+int em_map_exact_impl(em_ctx *ctx, const em_pairs *pr, const double *d_x, const double *d_y, const double *d_z,
+                      const double *d_h, const double *d_m, const em_voronoi *v, const em_params *p, double *d_w_out,
+                      double *d_rho_out, double *d_wsum_out, int64_t *h_nfp64, bool fixed, int32_t *d_flag_buf,
+                      int *d_flag_count);
 int em_exclusive_scan_i64(em_ctx *ctx, const int64_t *in, int64_t *out, int64_t n);
 int em_exclusive_scan_i32(em_ctx *ctx, const int32_t *in, int32_t *out, int64_t n);
 int em_sort_pairs_u64(em_ctx *ctx, uint64_t *keys, int32_t *vals, int64_t n, int end_bit);

@@ -798,12 +798,15 @@ __device__ __forceinline__ void mq_push_g(SegQueue &q, int lane, int &cnt, float
 
 }  // namespace
 
-#if EM_MQ_MINB > 0
-#define MQ_LAUNCH_BOUNDS __launch_bounds__(32 * EM_MQ_WARPS, EM_MQ_MINB)
-#else
-#define MQ_LAUNCH_BOUNDS __launch_bounds__(32 * EM_MQ_WARPS)
-#endif
-__global__ void MQ_LAUNCH_BOUNDS k_map_fp32(int64_t npairs, const int32_t *__restrict__ pi,
+// Launch shapes of the FP32 pass (em_params.fp32_variant, map_autotune):
+// warps per block and the minimum resident blocks per SM asked of the
+// compiler (0: none).  Variant 0 is the default shape.
+constexpr int MQ_NVARIANT = 4;
+constexpr int MQ_VARIANT_WARPS[MQ_NVARIANT] = {MQ_WARPS, 1, 4, 2};
+constexpr int MQ_VARIANT_MINB[MQ_NVARIANT] = {EM_MQ_MINB, 0, 0, 12};
+
+template <int WARPS, int MINB>
+__global__ void __launch_bounds__(32 * WARPS, MINB) k_map_fp32(int64_t npairs, const int32_t *__restrict__ pi,
                                                         const int32_t *__restrict__ pj, const double *__restrict__ x,
                                                         const double *__restrict__ y, const double *__restrict__ z,
                                                         const double *__restrict__ h, const double *__restrict__ gen,
@@ -816,10 +819,10 @@ __global__ void MQ_LAUNCH_BOUNDS k_map_fp32(int64_t npairs, const int32_t *__res
                                                         double *__restrict__ w, int32_t *__restrict__ flagged,
                                                         int *__restrict__ nflag)
 {
-    __shared__ SegQueue queues[MQ_WARPS];
+    __shared__ SegQueue queues[WARPS];
     SegQueue &q = queues[threadIdx.x >> 5];
     const int lane = threadIdx.x & 31;
-    const int64_t k0 = (blockIdx.x * (int64_t)MQ_WARPS + (threadIdx.x >> 5)) * 32;
+    const int64_t k0 = (blockIdx.x * (int64_t)WARPS + (threadIdx.x >> 5)) * 32;
     if (k0 >= npairs) return;   // the whole warp
     const int64_t k = k0 + lane;
     const bool valid = k < npairs;
@@ -858,8 +861,12 @@ __global__ void MQ_LAUNCH_BOUNDS k_map_fp32(int64_t npairs, const int32_t *__res
     }
     const bool tilde = !full;
 
-    emq::ff acc{0.f, 0.f};
-    float mag = 0.f;
+    // the quadrature's results are added in the order of the lane's own
+    // segments (mq_flush), the angles beyond 2h in the order of its edges, each
+    // into its own sum: neither order depends on when the warp flushes, so a
+    // pair's weight does not depend on the other pairs of its warp
+    emq::ff acc{0.f, 0.f}, acc_far{0.f, 0.f};
+    float mag = 0.f, mag_far = 0.f;
     bool force = false;   // the FP32 form does not apply: recompute in FP64
     int cnt = 0;   // segments queued by this lane
     const int nface = valid ? (int)(f1 - f) : 0;
@@ -941,7 +948,7 @@ __global__ void MQ_LAUNCH_BOUNDS k_map_fp32(int64_t npairs, const int32_t *__res
                         // one side: [min |T|, min |T| + L/h]; else [0, |T0|] and [0, |T1|]
                         const float ua = one_side ? fminf(u0, u1) : 0.f;
                         const float du = one_side ? dT : (part ? u1 : u0);
-                        mq_push_g(q, lane, cnt, ua, du, A, B2f, c1x, c4x, ccx, sc, fs, tilde, acc, mag);
+                        mq_push_g(q, lane, cnt, ua, du, A, B2f, c1x, c4x, ccx, sc, fs, tilde, acc_far, mag_far);
                     }
                 }
             }
@@ -957,9 +964,10 @@ __global__ void MQ_LAUNCH_BOUNDS k_map_fp32(int64_t npairs, const int32_t *__res
     if (valid) {
         // the integrals were summed with their signs: w = sum (full kernel) or
         // [P inside] - sum (complement kernel)
-        const double sum = (double)acc.hi + (double)acc.lo;
+        const emq::ff tot = emq::ff_add(acc, acc_far);
+        const double sum = (double)tot.hi + (double)tot.lo;
         const double wk = full ? sum : ((inside ? 1.0 : 0.0) - sum);
-        const double magd = (double)mag + ((inside && !full) ? 1.0 : 0.0);
+        const double magd = (double)mag + (double)mag_far + ((inside && !full) ? 1.0 : 0.0);
         w[k] = wk;
         // error bound of the FP32 pass: est_k = (ulps) 2^-24 times the sum of
         // the non-negative pieces it summed.  With the default 8 ulps the
@@ -1006,14 +1014,43 @@ __global__ void k_particle_wsum(int64_t np, const int64_t *__restrict__ off, con
     u[i] = s;
 }
 
-// map_exact and map_exact_noalloc: the mixed pass's flagged-pair list and
-// counter are stream-ordered scratch (fixed == false) or the library's fixed
-// device array (fixed == true, at most EM_NOALLOC_MAX_PAIRS pairs).
+// The FP32 pass in launch shape `variant` (see MQ_VARIANT_*).
+template <int V>
+static void launch_variant(cudaStream_t st, int64_t n, const int32_t *pi, const int32_t *pj, const double *x,
+                           const double *y, const double *z, const double *h, const double *gen, const double *radius,
+                           const int64_t *cfo, const int64_t *fvo, const PlaneF *pf, const PlaneF *pfl,
+                           const EdgeF *ef, const EdgeF *efl, float tol, double est_k, double *w, int32_t *flagged,
+                           int *nflag)
+{
+    constexpr int W = MQ_VARIANT_WARPS[V], B = MQ_VARIANT_MINB[V];
+    k_map_fp32<W, B><<<em_grid((n + 31) / 32, W), 32 * W, 0, st>>>(n, pi, pj, x, y, z, h, gen, radius, cfo, fvo, pf,
+                                                                 pfl, ef, efl, tol, est_k, w, flagged, nflag);
+}
+
+static void launch_map_fp32(int variant, cudaStream_t st, int64_t n, const int32_t *pi, const int32_t *pj,
+                            const double *x, const double *y, const double *z, const double *h, const double *gen,
+                            const double *radius, const int64_t *cfo, const int64_t *fvo, const PlaneF *pf,
+                            const PlaneF *pfl, const EdgeF *ef, const EdgeF *efl, float tol, double est_k, double *w,
+                            int32_t *flagged, int *nflag)
+{
+    switch (variant) {
+    case 1: launch_variant<1>(st, n, pi, pj, x, y, z, h, gen, radius, cfo, fvo, pf, pfl, ef, efl, tol, est_k, w, flagged, nflag); break;
+    case 2: launch_variant<2>(st, n, pi, pj, x, y, z, h, gen, radius, cfo, fvo, pf, pfl, ef, efl, tol, est_k, w, flagged, nflag); break;
+    case 3: launch_variant<3>(st, n, pi, pj, x, y, z, h, gen, radius, cfo, fvo, pf, pfl, ef, efl, tol, est_k, w, flagged, nflag); break;
+    default: launch_variant<0>(st, n, pi, pj, x, y, z, h, gen, radius, cfo, fvo, pf, pfl, ef, efl, tol, est_k, w, flagged, nflag); break;
+    }
+}
+
+// map_exact, map_exact_noalloc and map_batch: the mixed pass's flagged-pair
+// list and counter are stream-ordered scratch, the caller's scratch
+// (d_flag_buf, d_flag_count: map_batch), or the library's fixed device array
+// (fixed == true, at most EM_NOALLOC_MAX_PAIRS pairs).
 static int noalloc_buffers(em_ctx *ctx, int32_t **flagged, int **count);
 
-static int map_exact_run(em_ctx *ctx, const em_pairs *pr, const double *d_x, const double *d_y, const double *d_z,
-                         const double *d_h, const double *d_m, const em_voronoi *v, const em_params *p,
-                         double *d_w_out, double *d_rho_out, double *d_wsum_out, int64_t *h_nfp64, bool fixed)
+int em_map_exact_impl(em_ctx *ctx, const em_pairs *pr, const double *d_x, const double *d_y, const double *d_z,
+                      const double *d_h, const double *d_m, const em_voronoi *v, const em_params *p, double *d_w_out,
+                      double *d_rho_out, double *d_wsum_out, int64_t *h_nfp64, bool fixed, int32_t *d_flag_buf,
+                      int *d_flag_count)
 {
     EM_CHECK_ARG(ctx && pr && v && p && pr->ncell == v->ncell);
     EM_CHECK_ARG(pr->npairs == 0 || (d_x && d_y && d_z && d_h && d_w_out));
@@ -1027,6 +1064,7 @@ static int map_exact_run(em_ctx *ctx, const em_pairs *pr, const double *d_x, con
     }
     const int block = p->block_pairs > 0 ? p->block_pairs : 128;
     EM_CHECK_ARG(block % 32 == 0 && block <= 128);
+    EM_CHECK_ARG(p->fp32_variant >= 0 && p->fp32_variant < MQ_NVARIANT);
     if (h_nfp64) *h_nfp64 = 0;
     if (ctx->timing) ctx->recorded[0] = ctx->recorded[1] = false;
     if (n) {
@@ -1047,15 +1085,17 @@ static int map_exact_run(em_ctx *ctx, const em_pairs *pr, const double *d_x, con
             int *nflag;
             if (fixed) {
                 EM_TRY(noalloc_buffers(ctx, &flagged, &nflag));
+            } else if (d_flag_buf && d_flag_count) {   // the caller's scratch (map_batch), n entries
+                flagged = d_flag_buf;
+                nflag = d_flag_count;
             } else {
                 EM_TRY(tmp.alloc(&flagged, n));
                 EM_TRY(tmp.alloc(&nflag, 1));
             }
             EM_CUDA(cudaMemsetAsync(nflag, 0, sizeof(int), ctx->stream));
-            k_map_fp32<<<em_grid((n + 31) / 32, MQ_WARPS), 32 * MQ_WARPS, 0, ctx->stream>>>(
-                n, pr->pair_i, pr->pair_j, d_x, d_y, d_z, d_h, v->gen, v->radius, v->cell_face_off,
-                v->face_vert_off, v->plane_f, v->plane_fl, v->edge_f, v->edge_fl, (float)p->fp64_threshold, em_est_k(p),
-                d_w_out, flagged, nflag);
+            launch_map_fp32(p->fp32_variant, ctx->stream, n, pr->pair_i, pr->pair_j, d_x, d_y, d_z, d_h, v->gen,
+                            v->radius, v->cell_face_off, v->face_vert_off, v->plane_f, v->plane_fl, v->edge_f,
+                            v->edge_fl, (float)p->fp64_threshold, em_est_k(p), d_w_out, flagged, nflag);
             EM_LAUNCHED(ctx);
             if (ctx->timing) {
                 EM_CUDA(cudaEventRecord(ctx->ev[1], ctx->stream));
@@ -1096,7 +1136,66 @@ EM_EXPORT int map_exact(em_ctx *ctx, const em_pairs *pr, const double *d_x, cons
                         const double *d_h, const double *d_m, const em_voronoi *v, const em_params *p,
                         double *d_w_out, double *d_rho_out, double *d_wsum_out, int64_t *h_nfp64)
 {
-    return map_exact_run(ctx, pr, d_x, d_y, d_z, d_h, d_m, v, p, d_w_out, d_rho_out, d_wsum_out, h_nfp64, false);
+    return em_map_exact_impl(ctx, pr, d_x, d_y, d_z, d_h, d_m, v, p, d_w_out, d_rho_out, d_wsum_out, h_nfp64, false,
+                             nullptr, nullptr);
+}
+
+// Time the FP32 pass in every launch shape on the given pairs (a warm-up
+// launch, then the median of three CUDA-event-timed launches each) and return
+// the fastest.  Scratch only; the caller's arrays are read, never written.
+EM_EXPORT int map_autotune(em_ctx *ctx, const em_pairs *pr, const double *d_x, const double *d_y, const double *d_z,
+                           const double *d_h, const em_voronoi *v, const em_params *p, int *h_best, double *h_ms)
+{
+    EM_CHECK_ARG(ctx && pr && v && p && h_best && pr->ncell == v->ncell);
+    EM_CHECK_ARG(pr->npairs == 0 || (d_x && d_y && d_z && d_h));
+    *h_best = 0;
+    const int64_t n = pr->npairs;
+    if (n == 0) {
+        if (h_ms)
+            for (int k = 0; k < MQ_NVARIANT; ++k) h_ms[k] = 0.0;
+        return EM_OK;
+    }
+    DevArena tmp(ctx->stream, true);
+    double *w;
+    int32_t *flagged;
+    int *nflag;
+    EM_TRY(tmp.alloc(&w, n));
+    EM_TRY(tmp.alloc(&flagged, n));
+    EM_TRY(tmp.alloc(&nflag, 1));
+    cudaEvent_t e0, e1;
+    EM_CUDA(cudaEventCreate(&e0));
+    EM_CUDA(cudaEventCreate(&e1));
+    int rc = EM_OK;
+    double best = 1e300;
+    for (int k = 0; k < MQ_NVARIANT && rc == EM_OK; ++k) {
+        float t[4] = {0.f, 0.f, 0.f, 0.f};
+        for (int r = 0; r < 4 && rc == EM_OK; ++r) {
+            cudaMemsetAsync(nflag, 0, sizeof(int), ctx->stream);
+            cudaEventRecord(e0, ctx->stream);
+            launch_map_fp32(k, ctx->stream, n, pr->pair_i, pr->pair_j, d_x, d_y, d_z, d_h, v->gen, v->radius,
+                            v->cell_face_off, v->face_vert_off, v->plane_f, v->plane_fl, v->edge_f, v->edge_fl,
+                            (float)p->fp64_threshold, em_est_k(p), w, flagged, nflag);
+            ctx->launches++;
+            cudaEventRecord(e1, ctx->stream);
+            cudaError_t e = cudaEventSynchronize(e1);
+            if (e == cudaSuccess) e = cudaEventElapsedTime(&t[r], e0, e1);
+            if (e == cudaSuccess) e = cudaGetLastError();
+            if (e != cudaSuccess) {
+                em_set_error("map_autotune: variant %d: %s", k, cudaGetErrorString(e));
+                rc = EM_ECUDA;
+            }
+        }
+        const float a = t[1], b = t[2], c = t[3];   // t[0] is the warm-up
+        const double med = fmax(fmin(a, b), fmin(fmax(a, b), c));
+        if (h_ms) h_ms[k] = med;
+        if (rc == EM_OK && med < best) {
+            best = med;
+            *h_best = k;
+        }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    return rc;
 }
 
 // ---------------------------------------------------------------------------
@@ -1153,7 +1252,8 @@ EM_EXPORT int map_exact_noalloc(em_ctx *ctx, const em_pairs *pr, const double *d
                                 const em_params *p, double *d_w_out, double *d_rho_out, double *d_wsum_out,
                                 int64_t *h_nfp64)
 {
-    return map_exact_run(ctx, pr, d_x, d_y, d_z, d_h, d_m, v, p, d_w_out, d_rho_out, d_wsum_out, h_nfp64, true);
+    return em_map_exact_impl(ctx, pr, d_x, d_y, d_z, d_h, d_m, v, p, d_w_out, d_rho_out, d_wsum_out, h_nfp64, true,
+                             nullptr, nullptr);
 }
 
 // ---------------------------------------------------------------------------

@@ -96,3 +96,47 @@ def test_batch_failing_snapshot():
     good, _ = api.map_batch(0, as_dicts(SNAPS[:5]), P, nworkers=3)
     for k in (0, 1, 3, 4):
         assert res[k]["status"] == 0 and torch.equal(res[k]["rho"], good[k]["rho"])
+
+
+def test_batch_tuned_equals_serial_with_its_variant():
+    """The batch with its launch shape picked by map_autotune on the batch's
+    pairs equals the snapshots mapped one at a time with that shape, bit for
+    bit; the mapping's device time is reported."""
+    P = api.Params(r_part=0.05, r_leaf=0.1, theta=0.3, precision=1)
+    info = {}
+    res_t, _ = api.map_batch(0, as_dicts(SNAPS[:6]), P, nworkers=3, tune=True, info=info)
+    assert 0 <= info["variant"] < api.FP32_VARIANTS and info["map_ms"][0] > 0
+    Pv = api.Params(r_part=0.05, r_leaf=0.1, theta=0.3, precision=1, fp32_variant=info["variant"])
+    ctx = api.Context(0)
+    for (w, fc), r in zip(SNAPS[:6], res_t):
+        rho, f, npseudo, npairs, nf = serial(ctx, w, fc, Pv)
+        assert r["status"] == 0 and (r["npairs"], r["nfp64"]) == (npairs, nf)
+        assert torch.equal(r["rho"], rho)
+        assert torch.equal(torch.nan_to_num(r["f"], nan=-1.0), torch.nan_to_num(f, nan=-1.0))
+
+
+def test_autotune_variants():
+    """Every launch shape of the FP32 pass is deterministic (the same bits on
+    a second call) and within the mixed mode's tolerance of the default shape
+    (the shapes are compiled separately, and the compiler may fuse a multiply
+    and an add differently in each); map_autotune times them all and returns
+    one of them."""
+    w, _ = max(SNAPS, key=lambda s: s[0].n)
+    ctx = api.Context(0)
+    P = api.Params(r_part=0.05, r_leaf=0.1, theta=0.3, precision=1)
+    t = api.build_tree(ctx, dev(w.x), dev(w.y), dev(w.z), dev(w.m), w.box, 8)
+    g = api.make_pseudo_particles(ctx, t, dev(w.h), SRC, P).get()
+    vor = api.build_voronoi(ctx, dev(w.gx), dev(w.gy), dev(w.gz), w.box, P)
+    pr = api.find_pairs(ctx, g["x"], g["y"], g["z"], g["h"], vor)
+    best, ms = api.map_autotune(ctx, pr, g["x"], g["y"], g["z"], g["h"], vor, P)
+    assert 0 <= best < api.FP32_VARIANTS and len(ms) == api.FP32_VARIANTS and min(ms) > 0
+    w64, _, _, _ = api.map_exact(ctx, pr, g["x"], g["y"], g["z"], g["h"], g["m"], vor, api.Params(precision=0))
+    for v in range(api.FP32_VARIANTS):
+        Pv = api.Params(r_part=0.05, r_leaf=0.1, theta=0.3, precision=1, fp32_variant=v)
+        a, _, _, _ = api.map_exact(ctx, pr, g["x"], g["y"], g["z"], g["h"], g["m"], vor, Pv)
+        b, _, _, _ = api.map_exact(ctx, pr, g["x"], g["y"], g["z"], g["h"], g["m"], vor, Pv)
+        assert torch.equal(a, b), v
+        assert bool(((a - w64).abs() <= 1e-5 * w64.abs() + 1e-14).all()), v
+    with pytest.raises(Exception):
+        api.map_exact(ctx, pr, g["x"], g["y"], g["z"], g["h"], g["m"], vor,
+                      api.Params(precision=1, fp32_variant=api.FP32_VARIANTS))

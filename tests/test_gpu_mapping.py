@@ -194,3 +194,18 @@ def test_mixed_particle_on_a_face(ctx, orc):
     assert np.all(np.abs(wg - wo) <= 1e-5 * np.abs(wo) + TOL_ABS)
     mine = pairs.pair_i == 0
     assert abs(wo[mine].sum() - 1.0) < 1e-12 and abs(wg[mine].sum() - 1.0) < 1e-6
+
+
+def test_mixed_weight_independent_of_warp_neighbours(ctx, case):
+    """A pair's mixed weight does not depend on which pairs share its warp:
+    every third pair mapped on its own list (so in other warps, with other
+    neighbours) gives the same bits as in the whole list."""
+    w, c = case["w"], case
+    vor, pr, (wg, _, _, _) = run_gpu(ctx, c, 1, 1e-5)
+    sel = np.arange(0, c["pairs"].n, 3)
+    sub = api.pairs_from_list(ctx, dev(c["pairs"].pair_i[sel], torch.int32), dev(c["pairs"].pair_j[sel], torch.int32),
+                              w.n, vor)
+    ws, _, _, _ = api.map_exact(ctx, sub, dev(w.x), dev(w.y), dev(w.z), dev(w.h), dev(w.m), vor,
+                                api.Params(precision=1, fp64_threshold=1e-5))
+    torch.cuda.synchronize()
+    assert torch.equal(ws, wg[torch.as_tensor(sel, device="cuda")])
