@@ -379,14 +379,25 @@ __device__ __forceinline__ T pair_weight(T rx, T ry, T rz, T h, T radius, int64_
 }
 
 // FP64 closed form, one warp per pair (both the FP64 mode and the recompute
-// of the pairs the mixed pass flagged).  The lanes take the cell's faces
-// (inside test, skip test, K(D)), then the edges of the faces kept, each
-// edge's closed-form term (edge_full / edge_tilde, the same as pair_weight's)
-// times its orientation signs; a fixed-order warp sum adds them up.  Against a
-// thread per pair this keeps the lanes on one pair's edges instead of walking
-// different cells' faces, and a short list still fills the GPU.  A cell with
-// more than FW_MAXF faces (possible only for imported cells) is done by one
-// lane with pair_weight.
+// of the pairs the mixed pass flagged).
+//
+// An edge's term Phi(T1) - Phi(T0) (edge_full / edge_tilde) is linear in a
+// few evaluations: the basis b(tau) at an endpoint in region 1 or 2 (a
+// combination of region coefficient vectors and b0), the region-3 part at an
+// endpoint beyond 2h (the two angles b0, b1 alone), and the region
+// differences d1 = (c1 - c2).b(t1), d2 = (c2 - c3).b(t2), whose integer
+// coefficient sums the endpoints past t1 or t2 with their signs.  So each
+// lane takes an edge, lists these evaluations with their signed weights
+// (face orientation, edge orientation and endpoint sign folded in; a d1 or
+// d2 whose coefficient vanishes, as for both endpoints beyond t2 on one
+// side, is not listed), and appends them to one of two per-warp queues, one
+// of basis evaluations and one of angle evaluations.  Whenever a queue holds
+// 32 entries the warp evaluates them together, one per lane, so that the
+// transcendental code runs with the warp converged whatever the edges'
+// regions.  Each lane adds what it evaluated; a fixed-order warp sum ends the
+// pair.  The order of the evaluations depends on the pair alone, so the
+// result is reproducible.  A cell with more than FW_MAXF faces (possible only
+// for imported cells) is done by one lane with pair_weight.
 //
 // Entry t of list is k >= 0: pair k in the complement form (faces beyond 2h
 // skipped; its rounding, about 1e-13, is far inside the mixed mode's
@@ -395,6 +406,73 @@ __device__ __forceinline__ T pair_weight(T rx, T ry, T rz, T h, T radius, int64_
 // in the full form (the FP64 mode).
 constexpr int FW_WARPS = 4;
 constexpr int FW_MAXF = 64;
+constexpr int FQ = 64;   // ring capacity of each evaluation queue (a power of two, >= 63)
+
+// Evaluations waiting for a full warp: the basis at t (code: regions rA, rB
+// in bits 0-1, 2-3) weighted w0 (c_rA - c_rB).b - w1 b0, or the angles
+// w0 D atan(u/A) - w1 atan(D u / (A Q)).
+struct FwQueue {
+    double A[FQ], B2[FQ], D[FQ], t[FQ], w0[FQ], w1[FQ];
+    int code[FQ];
+};
+
+__device__ __noinline__ double fw_eval_basis(const FwQueue &q, int i)
+{
+    double b[6];
+    basis<double>(q.A[i], q.B2[i], q.D[i], q.t[i], b);
+    const int rA = q.code[i] & 3, rB = q.code[i] >> 2;
+    const double p1 = dot_c1(b), p2 = dot_c2(b), p3 = dot_c3(b);
+    const double dA = rA == 1 ? p1 : (rA == 2 ? p2 : p3);
+    const double dB = rB == 0 ? 0.0 : (rB == 1 ? p1 : (rB == 2 ? p2 : p3));
+    return q.w0[i] * (dA - dB) - q.w1[i] * b[0];
+}
+
+__device__ __noinline__ double fw_eval_angle(const FwQueue &q, int i, bool both)
+{
+    const double A = q.A[i], D = q.D[i], u = q.t[i];
+    double v = q.w0[i] * (D * atan2(u, A));
+    if (both) v -= q.w1[i] * atan2(D * u, A * sqrt(q.B2[i] + u * u));
+    return v;
+}
+
+// Append this lane's entry (if has) to ring q of n entries from head.
+__device__ __forceinline__ void fw_push(FwQueue &q, int head, int &n, bool has, double A, double B2, double D,
+                                        double t, double w0, double w1, int code)
+{
+    const unsigned m = __ballot_sync(0xffffffffu, has);
+    if (has) {
+        const int pos = (head + n + __popc(m & ((1u << (threadIdx.x & 31)) - 1u))) & (FQ - 1);
+        q.A[pos] = A;
+        q.B2[pos] = B2;
+        q.D[pos] = D;
+        q.t[pos] = t;
+        q.w0[pos] = w0;
+        q.w1[pos] = w1;
+        q.code[pos] = code;
+    }
+    n += __popc(m);
+}
+
+// Evaluate the queues' full warps (every entry when last), lane by entry.
+__device__ __forceinline__ void fw_drain(FwQueue &qb, FwQueue &qa, int &hb, int &nb, int &ha, int &na, bool both,
+                                         bool last, double &acc)
+{
+    const int lane = threadIdx.x & 31;
+    __syncwarp();
+    while (nb >= 32 || (last && nb > 0)) {
+        if (lane < nb) acc += fw_eval_basis(qb, (hb + lane) & (FQ - 1));
+        const int d = min(nb, 32);
+        hb = (hb + d) & (FQ - 1);
+        nb -= d;
+    }
+    while (na >= 32 || (last && na > 0)) {
+        if (lane < na) acc += fw_eval_angle(qa, (ha + lane) & (FQ - 1), both);
+        const int d = min(na, 32);
+        ha = (ha + d) & (FQ - 1);
+        na -= d;
+    }
+    __syncwarp();
+}
 
 __device__ __forceinline__ void fp64_pairs_warp(int64_t n, const int32_t *__restrict__ list,
                                                 const int32_t *__restrict__ pi, const int32_t *__restrict__ pj,
@@ -409,7 +487,9 @@ __device__ __forceinline__ void fp64_pairs_warp(int64_t n, const int32_t *__rest
     __shared__ int64_t fE0[FW_WARPS][FW_MAXF];
     __shared__ int fPre[FW_WARPS][FW_MAXF + 1];
     __shared__ float fSg[FW_WARPS][FW_MAXF];
+    __shared__ FwQueue fq[FW_WARPS][2];
     const int wi = threadIdx.x >> 5, lane = threadIdx.x & 31, wpb = blockDim.x >> 5;   // wpb <= FW_WARPS
+    FwQueue &qb = fq[wi][0], &qa = fq[wi][1];
     for (int64_t t = blockIdx.x * (int64_t)wpb + wi; t < n; t += (int64_t)gridDim.x * wpb) {
         const int32_t code = list ? list[t] : ~(int32_t)t;
         const int64_t k = code >= 0 ? code : ~code;
@@ -465,24 +545,107 @@ __device__ __forceinline__ void fp64_pairs_warp(int64_t n, const int32_t *__rest
             __syncwarp();
         }
         const int ne = fPre[wi][nface];
-        double acc = 0.0, terr = 0.0;
-        for (int e = lane; e < ne; e += 32) {
-            int lo = 0, hi = nface;   // fPre[lo] <= e < fPre[hi]
-            while (hi - lo > 1) {
-                const int mid = (lo + hi) >> 1;
-                if (fPre[wi][mid] <= e) lo = mid;
-                else hi = mid;
+        double acc = 0.0;
+        int hb = 0, nb = 0, ha = 0, na = 0;
+        for (int base = 0; base < ne; base += 32) {
+            const int e = base + lane;
+            // this lane's edge: its evaluations (has*), weights and split points
+            double A = 0.0, D = 0.0, B2 = 0.0, u0 = 0.0, u1 = 0.0, ts1 = 0.0, ts2 = 0.0;
+            double bw0[2] = {0.0, 0.0}, bw1[2] = {0.0, 0.0}, aw0[2] = {0.0, 0.0}, aw1[2] = {0.0, 0.0};
+            int bcode[2] = {0, 0};
+            bool hasb[2] = {false, false}, hasa[2] = {false, false};
+            double coef1 = 0.0, coef2 = 0.0;
+            if (e < ne) {
+                int lo = 0, hi = nface;   // fPre[lo] <= e < fPre[hi]
+                while (hi - lo > 1) {
+                    const int mid = (lo + hi) >> 1;
+                    if (fPre[wi][mid] <= e) lo = mid;
+                    else hi = mid;
+                }
+                const EdgeD E = edge[fE0[wi][lo] + (e - fPre[wi][lo])];
+                const double a = E.cm - (E.mx * rx + E.my * ry + E.mz * rz);
+                if (a != 0.0) {
+                    A = fabs(a) * ih;
+                    const double T0 = (E.ce - (E.ex * rx + E.ey * ry + E.ez * rz)) * ih;
+                    const double T1 = T0 + E.L * ih;
+                    D = fD[wi][lo];
+                    const double kd = fK[wi][lo];
+                    const double sg = (double)fSg[wi][lo] * (a > 0.0 ? 1.0 : -1.0);
+                    B2 = D * D + A * A;
+                    u0 = fabs(T0);
+                    u1 = fabs(T1);
+                    // endpoint signs: Phi(T1) - Phi(T0), Phi odd in T
+                    const double cs[2] = {T0 < 0.0 ? sg : -sg, T1 < 0.0 ? -sg : sg};
+                    const double uu[2] = {u0, u1};
+                    const bool near = B2 < 4.0;
+                    if (near) {
+                        ts2 = sqrt(4.0 - B2);
+                        if (B2 < 1.0) ts1 = sqrt(1.0 - B2);
+                    }
+#pragma unroll
+                    for (int s = 0; s < 2; ++s) {
+                        const double u = uu[s], c = cs[s];
+                        if (u == 0.0) continue;
+                        if (full) {
+                            if (!near || u > ts2) {   // region 3: the angles alone
+                                hasa[s] = true;
+                                aw0[s] = c * ((near || D < 2.0) ? 7.0 / 20.0 - kd : 0.25 / D);
+                                aw1[s] = c * 0.25;
+                                if (near) {
+                                    coef1 += c;
+                                    coef2 += c;
+                                }
+                            } else {
+                                hasb[s] = true;
+                                const int r = u <= ts1 ? 1 : 2;
+                                bcode[s] = r;
+                                bw0[s] = c;
+                                bw1[s] = c * kd;
+                                if (r == 2) coef1 += c;
+                            }
+                        } else {
+                            if (!near || u >= ts2) {   // beyond 2h: -(d1 + d2) - K~(D) b0
+                                hasa[s] = true;
+                                aw0[s] = -c * kd;
+                                if (near) {
+                                    coef1 -= c;
+                                    coef2 -= c;
+                                }
+                            } else {
+                                hasb[s] = true;
+                                const bool r2 = u > ts1;
+                                bcode[s] = r2 ? (3 | (2 << 2)) : (3 | (1 << 2));
+                                bw0[s] = c;
+                                bw1[s] = c * kd;
+                                if (r2) coef1 -= c;
+                            }
+                        }
+                    }
+                    if (!(B2 < 1.0)) coef1 = 0.0;   // no region 1: d1 = 0
+                }
             }
-            const EdgeD E = edge[fE0[wi][lo] + (e - fPre[wi][lo])];
-            const double a = E.cm - (E.mx * rx + E.my * ry + E.mz * rz);
-            if (a == 0.0) continue;
-            const double A = fabs(a) * ih;
-            const double t0 = (E.ce - (E.ex * rx + E.ey * ry + E.ez * rz)) * ih;
-            const double t1 = t0 + E.L * ih;
-            const double c = full ? edge_full<double>(fD[wi][lo], A, t0, t1, fK[wi][lo], terr)
-                                  : edge_tilde<double>(fD[wi][lo], A, t0, t1, fK[wi][lo], terr);
-            acc += (double)fSg[wi][lo] * ((a > 0.0) ? c : -c);
+            const bool has_t1 = coef1 != 0.0, has_t2 = coef2 != 0.0;
+            // six collective appends in a fixed order, draining full warps as they fill
+#pragma unroll 1
+            for (int step = 0; step < 6; ++step) {
+                // (selects rather than indexing, so that the arrays stay in registers)
+                const bool s = (step & 1) != 0;
+                if (step < 4) {
+                    const bool split = step >= 2;
+                    const bool has = split ? (s ? has_t2 : has_t1) : (s ? hasb[1] : hasb[0]);
+                    const double tt = split ? (s ? ts2 : ts1) : (s ? u1 : u0);
+                    const double w0 = split ? (s ? coef2 : coef1) : (s ? bw0[1] : bw0[0]);
+                    const double w1 = split ? 0.0 : (s ? bw1[1] : bw1[0]);
+                    const int cd = split ? (s ? (2 | (3 << 2)) : (1 | (2 << 2))) : (s ? bcode[1] : bcode[0]);
+                    fw_push(qb, hb, nb, has, A, B2, D, tt, w0, w1, cd);
+                } else {
+                    fw_push(qa, ha, na, s ? hasa[1] : hasa[0], A, B2, D, s ? u1 : u0, s ? aw0[1] : aw0[0],
+                            s ? aw1[1] : aw1[0], 0);
+                }
+                if (nb >= 32 || na >= 32) fw_drain(qb, qa, hb, nb, ha, na, full, false, acc);
+            }
         }
+        fw_drain(qb, qa, hb, nb, ha, na, full, true, acc);
 #pragma unroll
         for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
         if (lane == 0) {

@@ -17,6 +17,7 @@
 // finished cell's faces into a scratch slot of fixed capacity (64 faces, 384
 // face-vertices: every vertex belongs to three faces) and its counts; after
 // the scan of the counts, a copy pass moves the slots to the cells' offsets.
+#include <algorithm>
 #include <cmath>
 
 #include "common.cuh"
@@ -25,37 +26,42 @@
 #include "voronoi_cell.cuh"
 #include "voronoi_warp.cuh"
 
-constexpr int WMAXV_LOOP = emv::MAXV;
-
 namespace {
 
 using namespace emv;
 using emw::WCell;
 
 constexpr int VW = 2;   // warps (cells) per block
+#ifndef EM_VOR_MINB
+#define EM_VOR_MINB 12   // resident blocks per SM asked of the compiler in the first pass
+#endif
 
 // Capacity of a cell's scratch slot: faces (planes) and face-vertices (every
 // vertex belongs to three faces).
 constexpr int SLOT_F = emw::WMAXP;
-constexpr int SLOT_FV = 3 * emw::WMAXV;
+constexpr int SLOT_FV = 3 * MAXV;
 
-// Write the faces of the finished cell c: per face its unit normal, the
-// neighbour id and the offset of its vertex loop, the loop's vertices (CCW
-// seen from outside, absolute coordinates) from fvbase on; returns the counts
-// and the volume (divergence theorem).  Faces beyond fcap or vertices beyond
-// fvcap set bad.
-__device__ void emit_faces(const WCell &c, double gx, double gy, double gz, int fcap, int fvcap,
-                           int32_t *__restrict__ fvo, double *__restrict__ verts, double *__restrict__ normals,
-                           int64_t *__restrict__ nbr, int &nf, int &nfv, double &vol, bool &bad)
+// Write the faces of the finished cell c of sorted site s: per face its unit
+// normal, the neighbour id and the offset of its vertex loop, the loop's
+// vertices (CCW seen from outside, absolute coordinates) from fvbase on;
+// returns the counts and the volume (divergence theorem).  The planes are
+// formed again from their generators (emw::bisector, the builder's
+// arithmetic).  Faces beyond fcap or vertices beyond fvcap set bad.
+template <class C>
+__device__ void emit_faces(const C &c, const double *__restrict__ xs, const double *__restrict__ ys,
+                           const double *__restrict__ zs, const int32_t *__restrict__ perm, const double *box,
+                           double gx, double gy, double gz, int fcap, int fvcap, int32_t *__restrict__ fvo,
+                           double *__restrict__ verts, double *__restrict__ normals, int64_t *__restrict__ nbr, int &nf,
+                           int &nfv, double &vol, bool &bad)
 {
     const int lane = threadIdx.x & 31;
     int fbase = 0, fvbase = 0;
     double v = 0.0;
-    uint8_t loop[WMAXV_LOOP];
+    uint8_t loop[C::MAXV];
     bool err = false;
     for (int r = 0; r < c.np; r += 32) {
         int q = r + lane;
-        int n = q < c.np ? emw::wface_loop(c, q, loop, WMAXV_LOOP) : 0;
+        int n = q < c.np ? emw::wface_loop(c, q, loop, C::MAXV) : 0;
         if (n < 0) err = true;
         bool face = n >= 3;
         unsigned m = __ballot_sync(0xffffffffu, face);
@@ -72,7 +78,10 @@ __device__ void emit_faces(const WCell &c, double gx, double gy, double gz, int 
                 err = true;
             } else {
                 const int cur = c.cur;
-                double nx = c.pl[q][0], ny = c.pl[q][1], nz = c.pl[q][2];
+                const int sid = c.sid[q];
+                double nx, ny, nz, d;
+                if (sid >= 0) emw::bisector(xs, ys, zs, sid, gx, gy, gz, nx, ny, nz, d);
+                else emw::wall_plane(box, -1 - sid, gx, gy, gz, nx, ny, nz, d);
                 const double ln = sqrt(nx * nx + ny * ny + nz * nz), il = 1.0 / ln;
                 nx *= il;
                 ny *= il;
@@ -80,7 +89,7 @@ __device__ void emit_faces(const WCell &c, double gx, double gy, double gz, int 
                 normals[3 * fi] = nx;
                 normals[3 * fi + 1] = ny;
                 normals[3 * fi + 2] = nz;
-                nbr[fi] = c.pid[q];
+                nbr[fi] = sid >= 0 ? (int64_t)perm[sid] : (int64_t)sid;
                 fvo[fi] = fvi;
                 double ax = 0.0, ay = 0.0, az = 0.0;   // twice the vector area
                 for (int i = 0; i < n; ++i) {
@@ -93,7 +102,7 @@ __device__ void emit_faces(const WCell &c, double gx, double gy, double gz, int 
                     verts[3 * (fvi + i) + 2] = pa[2] + gz;
                 }
                 double area = 0.5 * (ax * nx + ay * ny + az * nz);
-                v += area * (c.pl[q][3] * il) * (1.0 / 3.0);
+                v += area * (d * il) * (1.0 / 3.0);
             }
         }
         fbase += __popc(m);
@@ -107,51 +116,85 @@ __device__ void emit_faces(const WCell &c, double gx, double gy, double gz, int 
     vol = v;
 }
 
-// One warp per cell (sorted index s): build the cell, write its faces into
-// the cell's scratch slot, its counts, generator and volume.
-__global__ void __launch_bounds__(32 * VW) k_voronoi_build(int64_t ngen, em::ChunkTree T, const double *__restrict__ xs,
-                                                           const double *__restrict__ ys, const double *__restrict__ zs,
-                                                           const int32_t *__restrict__ perm, double xlo, double xhi,
-                                                           double ylo, double yhi, double zlo, double zhi, int K,
-                                                           float margin, int64_t *__restrict__ nface,
-                                                           int64_t *__restrict__ nfv, int32_t *__restrict__ s_fvo,
-                                                           double *__restrict__ s_verts, double *__restrict__ s_normals,
-                                                           int64_t *__restrict__ s_nbr, double *__restrict__ volume,
-                                                           double *__restrict__ gen, int *__restrict__ status_or)
+struct BuildArgs {
+    int64_t ngen;
+    em::ChunkTree T;
+    const double *xs, *ys, *zs;
+    const int32_t *perm;
+    double box[6];
+    int K;
+    float margin;
+    int64_t *nface, *nfv;
+    int32_t *s_fvo;
+    double *s_verts, *s_normals;
+    int64_t *s_nbr;
+    double *volume, *gen;
+    int *status_or;      // [0] OR of the failing cells' status bits, [1] the first failing cell
+    int *retry_n;        // cells the first pass left for the second
+    int32_t *retry_list;
+};
+
+// Build the cell of sorted site s in c and write its faces into the cell's
+// scratch slot, its counts, generator and volume.  In the first pass a cell
+// that outgrows c's vertex capacity is listed for the second pass instead.
+template <class C>
+__device__ void build_one(C &c, const BuildArgs &a, int64_t s, bool first_pass)
 {
-    __shared__ WCell cells[VW];
-    const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int64_t s = blockIdx.x * (int64_t)VW + w;
-    if (s >= ngen) return;
-    WCell &c = cells[w];
-    const int64_t j = perm[s];
-    if (j < 0 || j >= ngen) {
-        if (lane == 0) atomicOr(status_or, VS_BOUNDS);
+    const int lane = threadIdx.x & 31;
+    const int64_t j = a.perm[s];
+    if (j < 0 || j >= a.ngen) {
+        if (lane == 0) atomicOr(a.status_or, VS_BOUNDS);
         return;
     }
-    const double box[6] = {xlo, xhi, ylo, yhi, zlo, zhi};
-    int nclip = 0;
-    int st = emw::wbuild_cell(c, T, xs, ys, zs, perm, s, box, K, margin, nullptr, nclip);
+    int st = emw::wbuild_cell(c, a.T, a.xs, a.ys, a.zs, s, a.box, a.K, a.margin);
+    if (first_pass && st == VS_CAPACITY) {
+        if (lane == 0) a.retry_list[atomicAdd(a.retry_n, 1)] = (int32_t)s;
+        return;
+    }
     int nf = 0, nv = 0;
     double vol = 0.0;
+    const double gx = a.xs[s], gy = a.ys[s], gz = a.zs[s];
     if (!st) {
         bool bad = false;
-        emit_faces(c, xs[s], ys[s], zs[s], SLOT_F, SLOT_FV, s_fvo + s * SLOT_F, s_verts + s * (3 * SLOT_FV),
-                   s_normals + s * (3 * SLOT_F), s_nbr + s * SLOT_F, nf, nv, vol, bad);
+        emit_faces(c, a.xs, a.ys, a.zs, a.perm, a.box, gx, gy, gz, SLOT_F, SLOT_FV, a.s_fvo + s * SLOT_F,
+                   a.s_verts + s * (3 * SLOT_FV), a.s_normals + s * (3 * SLOT_F), a.s_nbr + s * SLOT_F, nf, nv, vol,
+                   bad);
         if (bad) st |= VS_TOPOLOGY;
     }
     if (lane == 0) {
-        nface[j] = nf;
-        nfv[j] = nv;
-        volume[j] = vol;
-        gen[3 * j] = xs[s];
-        gen[3 * j + 1] = ys[s];
-        gen[3 * j + 2] = zs[s];
+        a.nface[j] = nf;
+        a.nfv[j] = nv;
+        a.volume[j] = vol;
+        a.gen[3 * j] = gx;
+        a.gen[3 * j + 1] = gy;
+        a.gen[3 * j + 2] = gz;
         if (st) {
-            atomicOr(status_or, st);
-            atomicMin(status_or + 1, (int)s);   // first failing cell (sorted index)
+            atomicOr(a.status_or, st);
+            atomicMin(a.status_or + 1, (int)s);   // first failing cell (sorted index)
         }
     }
+}
+
+// First pass: one warp per cell (sorted index s), the cell in a small
+// shared-memory footprint (MAXV_FIRST vertices) so that more warps fit an SM.
+__global__ void __launch_bounds__(32 * VW, EM_VOR_MINB) k_voronoi_build(BuildArgs a)
+{
+    __shared__ WCell<MAXV_FIRST> cells[VW];
+    const int w = threadIdx.x >> 5;
+    const int64_t s = blockIdx.x * (int64_t)VW + w;
+    if (s < a.ngen) build_one(cells[w], a, s, true);
+}
+
+// Second pass: the cells the first pass listed, at the full capacity (MAXV
+// vertices); the count is read on the device (grid-stride loop, one warp per
+// cell at a time).
+__global__ void __launch_bounds__(32 * VW) k_voronoi_build_large(BuildArgs a)
+{
+    __shared__ WCell<MAXV> cells[VW];
+    const int w = threadIdx.x >> 5;
+    const int64_t nr = *a.retry_n;
+    for (int64_t t = blockIdx.x * (int64_t)VW + w; t < nr; t += (int64_t)gridDim.x * VW)
+        build_one(cells[w], a, a.retry_list[t], false);
 }
 
 // One warp per cell: copy its scratch slot to the cell's scanned offsets.
@@ -261,21 +304,45 @@ static int voronoi_impl(em_ctx *ctx, int64_t ngen, const double *gx, const doubl
     EM_TRY(tmp.alloc(&s_nbr, ngen * SLOT_F));
     EM_TRY(tmp.alloc(&s_normals, ngen * 3 * SLOT_F));
     EM_TRY(tmp.alloc(&s_verts, ngen * 3 * SLOT_FV));
-    EM_TRY(tmp.alloc(&status, 2));
+    EM_TRY(tmp.alloc(&status, 3));
+    int32_t *retry;
+    EM_TRY(tmp.alloc(&retry, ngen));
     EM_TRY(v->mem.alloc(&cfo, ngen + 1));
     EM_TRY(v->mem.alloc(&v->gen, 3 * ngen));
     EM_TRY(v->mem.alloc(&v->volume, ngen));
     EM_CUDA(cudaMemsetAsync(status, 0, sizeof(int), st));
     EM_CUDA(cudaMemsetAsync(status + 1, 0x7f, sizeof(int), st));
+    EM_CUDA(cudaMemsetAsync(status + 2, 0, sizeof(int), st));
     EM_CUDA(cudaMemsetAsync(nface + ngen, 0, sizeof(int64_t), st));
     EM_CUDA(cudaMemsetAsync(nfv + ngen, 0, sizeof(int64_t), st));
     const double *b = v->box;
     double ext = 0.0;
     for (int k = 0; k < 6; ++k) ext = fmax(ext, fabs(b[k]));
     const float margin = (float)(4e-7 * (ext + 1.0));
-    k_voronoi_build<<<em_grid(ngen, VW), 32 * VW, 0, st>>>(ngen, T, xs, ys, zs, perm, b[0], b[1], b[2], b[3], b[4], b[5],
-                                                            K, margin, nface, nfv, s_fvo, s_verts, s_normals, s_nbr,
-                                                            v->volume, v->gen, status);
+    BuildArgs a;
+    a.ngen = ngen;
+    a.T = T;
+    a.xs = xs;
+    a.ys = ys;
+    a.zs = zs;
+    a.perm = perm;
+    for (int k = 0; k < 6; ++k) a.box[k] = b[k];
+    a.K = K;
+    a.margin = margin;
+    a.nface = nface;
+    a.nfv = nfv;
+    a.s_fvo = s_fvo;
+    a.s_verts = s_verts;
+    a.s_normals = s_normals;
+    a.s_nbr = s_nbr;
+    a.volume = v->volume;
+    a.gen = v->gen;
+    a.status_or = status;
+    a.retry_n = status + 2;
+    a.retry_list = retry;
+    k_voronoi_build<<<em_grid(ngen, VW), 32 * VW, 0, st>>>(a);
+    EM_LAUNCHED(ctx);
+    k_voronoi_build_large<<<(unsigned)std::min<int64_t>(em_grid(ngen, VW), 8 * (int64_t)ctx->nsm), 32 * VW, 0, st>>>(a);
     EM_LAUNCHED(ctx);
     EM_TRY(em_exclusive_scan_i64(ctx, nface, cfo, ngen + 1));
     EM_TRY(em_exclusive_scan_i64(ctx, nfv, cfvo, ngen + 1));

@@ -16,26 +16,57 @@
 namespace emw {
 
 constexpr int WMAXP = emv::MAXP;
-constexpr int WMAXV = emv::MAXV;
 constexpr int WCAND = 256;   // candidate list (power of two for the bitonic sort)
 
+// A cell under construction with room for NV vertices.  The planes are not
+// stored: plane q is the bisector of the site and generator sid[q] (its
+// sorted index), or box wall -1 - sid[q], formed again from the generator
+// positions wherever it is needed (bisector(), wall_plane()).
+template <int NV>
 struct WCell {
-    double pl[WMAXP][4];
-    double v[2][WMAXV][3];
-    float vf[WMAXV][4];      // the current vertices rounded to FP32, w = |x| + |y| + |z|
-    // clip in progress: 1 if the vertex lies beyond the plane, then its new
-    // index (0xff if removed)
-    uint8_t side[WMAXV];
+    static constexpr int MAXV = NV;
+    static_assert(NV <= 255, "vertex indices are bytes, 0xff marks a removed vertex");
+    double v[2][NV][3];
+    float vf[NV][4];         // the current vertices rounded to FP32, w = |x| + |y| + |z|
     float cd2[WCAND];        // sort keys of the candidates: squared distances rounded to FP32
     int cid[WCAND];
-    int pid[WMAXP];
-    uint8_t out_list[WMAXV];   // clip in progress: the removed vertices
-    uint8_t tri[2][WMAXV][4];
+    int sid[WMAXP];
+    // clip in progress: 1 if the vertex lies beyond the plane, then its new
+    // index (0xff if removed)
+    uint8_t side[NV];
+    uint8_t out_list[NV];    // clip in progress: the removed vertices
+    uint8_t tri[2][NV][4];
     // adj[t][e]: the vertex across edge e of vertex t, i.e. the one whose
     // triangle holds the reversed edge (tri[t][e + 1], tri[t][e])
-    uint8_t adj[2][WMAXV][4];
-    int np, nt, cur, ncand, err;
+    uint8_t adj[2][NV][4];
+    int np, nt, cur;
 };
+
+// Bisector plane n.x <= d of the site g (at the origin of the cell's frame)
+// and generator k: n = g_k - g, d = |n|^2 / 2, every rounding explicit so that
+// the builder and the face writer form the same bits.
+__device__ __forceinline__ void bisector(const double *__restrict__ xs, const double *__restrict__ ys,
+                                         const double *__restrict__ zs, int64_t k, double gx, double gy, double gz,
+                                         double &nx, double &ny, double &nz, double &d)
+{
+    nx = __dsub_rn(xs[k], gx);
+    ny = __dsub_rn(ys[k], gy);
+    nz = __dsub_rn(zs[k], gz);
+    d = __dmul_rn(0.5, __fma_rn(nz, nz, __fma_rn(ny, ny, __dmul_rn(nx, nx))));
+}
+
+// Box wall w (0..5: x-lo, x-hi, y-lo, y-hi, z-lo, z-hi) as n.x <= d in the
+// site's frame.
+__device__ __forceinline__ void wall_plane(const double *box, int w, double gx, double gy, double gz, double &nx,
+                                           double &ny, double &nz, double &d)
+{
+    const int ax = w >> 1;
+    const double g = ax == 0 ? gx : (ax == 1 ? gy : gz);
+    nx = ax == 0 ? ((w & 1) ? 1.0 : -1.0) : 0.0;
+    ny = ax == 1 ? ((w & 1) ? 1.0 : -1.0) : 0.0;
+    nz = ax == 2 ? ((w & 1) ? 1.0 : -1.0) : 0.0;
+    d = (w & 1) ? box[2 * ax + 1] - g : -(box[2 * ax] - g);
+}
 
 __device__ __forceinline__ unsigned lanemask_lt() { return (1u << (threadIdx.x & 31)) - 1u; }
 
@@ -54,23 +85,17 @@ __device__ __forceinline__ void set_vf(float *vf, double x, double y, double z)
     vf[3] = fabsf(xf) + fabsf(yf) + fabsf(zf);
 }
 
-__device__ void wcell_box(WCell &c, const double *box, double gx, double gy, double gz)
+template <class C>
+__device__ void wcell_box(C &c, const double *box, double gx, double gy, double gz)
 {
     const int lane = threadIdx.x & 31;
     if (lane == 0) {
         const double lo[3] = {box[0] - gx, box[2] - gy, box[4] - gz};
         const double hi[3] = {box[1] - gx, box[3] - gy, box[5] - gz};
         c.np = 6;
-        for (int w = 0; w < 6; ++w) {
-            int ax = w >> 1;
-            c.pl[w][0] = c.pl[w][1] = c.pl[w][2] = 0.0;
-            c.pl[w][ax] = (w & 1) ? 1.0 : -1.0;
-            c.pl[w][3] = (w & 1) ? hi[ax] : -lo[ax];
-            c.pid[w] = -1 - w;
-        }
+        for (int w = 0; w < 6; ++w) c.sid[w] = -1 - w;
         c.nt = 8;
         c.cur = 0;
-        c.err = 0;
         for (int i = 0; i < 8; ++i) {
             int sx = i & 1, sy = (i >> 1) & 1, sz = (i >> 2) & 1;
             uint8_t X = (uint8_t)sx, Y = (uint8_t)(2 + sy), Z = (uint8_t)(4 + sz);
@@ -94,7 +119,8 @@ __device__ void wcell_box(WCell &c, const double *box, double gx, double gy, dou
 }
 
 // Drop planes no vertex refers to (one lane; rare).
-__device__ int wcompact(WCell &c)
+template <class C>
+__device__ int wcompact(C &c)
 {
     const int lane = threadIdx.x & 31;
     if (lane == 0) {
@@ -107,10 +133,7 @@ __device__ int wcompact(WCell &c)
         for (int q = 0; q < c.np; ++q) {
             if (map[q] < 0) continue;
             map[q] = n;
-            if (n != q) {
-                for (int k = 0; k < 4; ++k) c.pl[n][k] = c.pl[q][k];
-                c.pid[n] = c.pid[q];
-            }
+            c.sid[n] = c.sid[q];
             ++n;
         }
         for (int t = 0; t < c.nt; ++t)
@@ -121,36 +144,39 @@ __device__ int wcompact(WCell &c)
     return c.np;
 }
 
-// Clip by n.x <= d.  Returns 1 changed, 0 unchanged, < 0 error (all lanes).
-__device__ int wclip(WCell &c, double nx, double ny, double nz, double d, int id)
+// Clip by the plane n.x <= d of generator sid.  Returns 1 changed, 0
+// unchanged, < 0 error (all lanes).
+template <class C>
+__device__ int wclip(C &c, double nx, double ny, double nz, double d, int sid)
 {
     const int lane = threadIdx.x & 31;
     const int cur = c.cur, nxt = cur ^ 1, nt = c.nt;
-    {
-        // FP32 side test: a bisector that every vertex clears by the band (far
-        // above the FP32 rounding of n, v, d and the products) cuts nothing
-        const float nxf = (float)nx, nyf = (float)ny, nzf = (float)nz, df = (float)d;
-        const float nmax = fmaxf(fmaxf(fabsf(nxf), fabsf(nyf)), fabsf(nzf));
-        bool maybe = false;
-        for (int t = lane; t < nt; t += 32) {
-            const float *vf = c.vf[t];
-            const float ff = nxf * vf[0] + nyf * vf[1] + nzf * vf[2] - df;
-            maybe = maybe || ff > -1e-5f * (nmax * vf[3] + fabsf(df));
-        }
-        if (!__any_sync(0xffffffffu, maybe)) return 0;
-    }
     // the side of each vertex: from its FP32 value where that clears the band
-    // (then the FP64 value has the same sign), else from the FP64 value
+    // (far above the FP32 rounding of n, v, d and the products; then the FP64
+    // value has the same sign), else from the FP64 value, which the warp
+    // evaluates only when some vertex lies in the band.  A vertex within
+    // 1e-13 of the plane's scale (above the rounding of the FP64 value and of
+    // the vertex) counts as on it and is kept, so that a plane through
+    // existing vertices, as in degenerate (lattice) site sets, cuts no sliver
+    // off; the new vertex on an edge from such a vertex is the vertex itself.
     const float nxf = (float)nx, nyf = (float)ny, nzf = (float)nz, df = (float)d;
     const float nmax = fmaxf(fmaxf(fabsf(nxf), fabsf(nyf)), fabsf(nzf));
     auto fval = [&](int t) { return nx * c.v[cur][t][0] + ny * c.v[cur][t][1] + nz * c.v[cur][t][2] - d; };
     bool any = false;
-    for (int t = lane; t < nt; t += 32) {
-        const float *vf = c.vf[t];
-        const float ff = nxf * vf[0] + nyf * vf[1] + nzf * vf[2] - df;
-        const float band = 1e-5f * (nmax * vf[3] + fabsf(df));
-        const bool out = ff > band ? true : (ff < -band ? false : fval(t) > 0.0);
-        c.side[t] = out ? 1 : 0;
+    for (int base = 0; base < nt; base += 32) {
+        const int t = base + lane;
+        bool out = false, unsure = false;
+        if (t < nt) {
+            const float *vf = c.vf[t];
+            const float ff = nxf * vf[0] + nyf * vf[1] + nzf * vf[2] - df;
+            const float band = 1e-5f * (nmax * vf[3] + fabsf(df));
+            out = ff > band;
+            unsure = !out && !(ff < -band);
+        }
+        if (__any_sync(0xffffffffu, unsure)) {
+            if (unsure) out = fval(t) > 1e-13 * (double)(nmax * c.vf[t][3] + fabsf(df));
+        }
+        if (t < nt) c.side[t] = out ? 1 : 0;
         any = any || out;
     }
     if (!__any_sync(0xffffffffu, any)) return 0;
@@ -217,8 +243,10 @@ __device__ int wclip(WCell &c, double nx, double ny, double nz, double d, int id
                 const uint8_t *tu = c.tri[cur][u];
                 ue = (tu[0] == b && tu[1] == a) ? 0 : ((tu[1] == b && tu[2] == a) ? 1 : 2);
                 bad = bad || !(tu[ue] == b && tu[(ue + 1) % 3] == a);
-                // the edge's end values in FP64 (fu <= 0 < ft, as their sides say)
-                const double fu = fval(u), ft = fval(t);
+                // the edge's end values in FP64: ft > 0 (beyond the band or the
+                // tolerance), fu taken as 0 where the kept vertex lies within the
+                // tolerance on the far side
+                const double fu = fmin(fval(u), 0.0), ft = fval(t);
                 double s = fu / (fu - ft);
                 px = c.v[cur][u][0] + s * (c.v[cur][t][0] - c.v[cur][u][0]);
                 py = c.v[cur][u][1] + s * (c.v[cur][t][1] - c.v[cur][u][1]);
@@ -228,7 +256,7 @@ __device__ int wclip(WCell &c, double nx, double ny, double nz, double d, int id
         unsigned m = __ballot_sync(0xffffffffu, newv);
         if (newv) {
             int pos = nn + __popc(m & lanemask_lt());
-            if (pos < WMAXV) {
+            if (pos < C::MAXV) {
                 c.tri[nxt][pos][0] = a;
                 c.tri[nxt][pos][1] = b;
                 c.tri[nxt][pos][2] = (uint8_t)q;
@@ -245,7 +273,7 @@ __device__ int wclip(WCell &c, double nx, double ny, double nz, double d, int id
     __syncwarp();
     // the new vertices around the new face q: (a, b, q) meets the one whose
     // a is this b across (b, q), and the one whose b is this a across (q, a)
-    if (nn <= WMAXV)
+    if (nn <= C::MAXV)
         for (int n = nk + lane; n < nn; n += 32) {
             const uint8_t an = c.tri[nxt][n][0], bn = c.tri[nxt][n][1];
             int m1 = -1, m2 = -1;
@@ -258,13 +286,9 @@ __device__ int wclip(WCell &c, double nx, double ny, double nz, double d, int id
             c.adj[nxt][n][2] = (uint8_t)(m2 < 0 ? 0 : m2);
         }
     if (__any_sync(0xffffffffu, bad)) return -emv::VS_TOPOLOGY;
-    if (nn > WMAXV) return -emv::VS_CAPACITY;
+    if (nn > C::MAXV) return -emv::VS_CAPACITY;
     if (lane == 0) {
-        c.pl[q][0] = nx;
-        c.pl[q][1] = ny;
-        c.pl[q][2] = nz;
-        c.pl[q][3] = d;
-        c.pid[q] = id;
+        c.sid[q] = sid;
         c.np = q + 1;
         c.nt = nn;
         c.cur = nxt;
@@ -273,31 +297,42 @@ __device__ int wclip(WCell &c, double nx, double ny, double nz, double d, int id
     return 1;
 }
 
-__device__ double wrmax2(const WCell &c)
+// An upper bound of the squared distance from the site to the cell's
+// farthest vertex: the largest squared norm of the FP32 vertex copies,
+// widened by 1e-5.  Each copy is within 2^-24 of its FP64 vertex per
+// coordinate and the FP32 sum of squares within 3 ulp, so the norm is
+// within 3e-7 of the exact one and the widened value lies above it.  A cell
+// whose squared norms fall below FP32's normal range takes the FP64 sum.
+template <class C>
+__device__ double wrmax2(const C &c)
 {
     const int lane = threadIdx.x & 31;
-    double r2 = 0.0;
+    float r2 = 0.f;
     for (int t = lane; t < c.nt; t += 32) {
-        const double *v = c.v[c.cur][t];
-        double q = v[0] * v[0] + v[1] * v[1] + v[2] * v[2];
-        r2 = q > r2 ? q : r2;
+        const float *v = c.vf[t];
+        r2 = fmaxf(r2, v[0] * v[0] + v[1] * v[1] + v[2] * v[2]);
     }
 #pragma unroll
-    for (int o = 16; o > 0; o >>= 1) {
-        double q = __shfl_xor_sync(0xffffffffu, r2, o);
-        r2 = q > r2 ? q : r2;
+    for (int o = 16; o > 0; o >>= 1) r2 = fmaxf(r2, __shfl_xor_sync(0xffffffffu, r2, o));
+    if (r2 >= 1e-30f) return (double)r2 * (1.0 + 1e-5);
+    double q2 = 0.0;
+    for (int t = lane; t < c.nt; t += 32) {
+        const double *v = c.v[c.cur][t];
+        q2 = fmax(q2, v[0] * v[0] + v[1] * v[1] + v[2] * v[2]);
     }
-    return r2;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) q2 = fmax(q2, __shfl_xor_sync(0xffffffffu, q2, o));
+    return q2 * (1.0 + 1e-12);
 }
 
 // Gather every generator k != s with lo2 <= d^2 < hi2 into the candidate
 // list (sorted by (d^2, k) afterwards).  Returns the count, or -1 if it
 // exceeds WCAND.
-__device__ int gather(WCell &c, const em::ChunkTree &T, const double *__restrict__ xs, const double *__restrict__ ys,
+template <class C>
+__device__ int gather(C &c, const em::ChunkTree &T, const double *__restrict__ xs, const double *__restrict__ ys,
                       const double *__restrict__ zs, int64_t s, double gx, double gy, double gz, double lo2,
                       double hi2, float margin, int &status)
 {
-    const int lane = threadIdx.x & 31;
     int n = 0;
     float R = (float)sqrt(hi2) + margin;
     // The window test runs in FP32 on the rounded positions and keeps every
@@ -342,7 +377,8 @@ __device__ int gather(WCell &c, const em::ChunkTree &T, const double *__restrict
 
 // Bitonic sort of the first n candidates by (d^2 in FP32, index), padded with
 // (inf, max) up to the next power of two (at most WCAND).
-__device__ void sort_cand(WCell &c, int n)
+template <class C>
+__device__ void sort_cand(C &c, int n)
 {
     const int lane = threadIdx.x & 31;
     int len = 2;
@@ -383,7 +419,8 @@ __device__ void sort_cand(WCell &c, int n)
 // kept one a little beyond p is only applied early (the half-spaces commute;
 // once applied it no longer cuts).  Returns the count with hi2 the window
 // actually covered, or -1 if the window cannot narrow (ties at the median).
-__device__ int gather_cutting(WCell &c, const em::ChunkTree &T, const double *__restrict__ xs,
+template <class C>
+__device__ int gather_cutting(C &c, const em::ChunkTree &T, const double *__restrict__ xs,
                               const double *__restrict__ ys, const double *__restrict__ zs, int64_t s, double gx,
                               double gy, double gz, double skip2, double &hi2)
 {
@@ -521,14 +558,14 @@ __device__ int gather_cutting(WCell &c, const em::ChunkTree &T, const double *__
     return n > WCAND ? -1 : n;
 }
 
-// Clip by the first nc (sorted) candidates; records the cutting ones.  A
-// candidate first meets an FP32 side test on the rounded positions (the same
-// band as in gather_cutting, above the rounding of the coordinates): one that
-// every vertex clears cuts nothing and costs no FP64 work.
-__device__ int clip_sorted(WCell &c, const em::ChunkTree &T, const double *__restrict__ xs,
-                           const double *__restrict__ ys, const double *__restrict__ zs,
-                           const int32_t *__restrict__ perm, int64_t n, double gx, double gy, double gz, int nc,
-                           int32_t *clip_ids, int &nclip)
+// Clip by the first nc (sorted) candidates.  A candidate first meets an FP32
+// side test on the rounded positions (the same band as in gather_cutting,
+// above the rounding of the coordinates): one that every vertex clears cuts
+// nothing and costs no FP64 work.
+template <class C>
+__device__ int clip_sorted(C &c, const em::ChunkTree &T, const double *__restrict__ xs,
+                           const double *__restrict__ ys, const double *__restrict__ zs, int64_t n, double gx,
+                           double gy, double gz, int nc)
 {
     const int lane = threadIdx.x & 31;
     const float gxf = (float)gx, gyf = (float)gy, gzf = (float)gz;
@@ -548,57 +585,55 @@ __device__ int clip_sorted(WCell &c, const em::ChunkTree &T, const double *__res
             }
             if (!__any_sync(0xffffffffu, maybe)) continue;
         }
-        double dx = xs[k] - gx, dy = ys[k] - gy, dz = zs[k] - gz;
-        int r = wclip(c, dx, dy, dz, 0.5 * (dx * dx + dy * dy + dz * dz), perm[k]);
+        double nx, ny, nz, d;
+        bisector(xs, ys, zs, k, gx, gy, gz, nx, ny, nz, d);
+        int r = wclip(c, nx, ny, nz, d, k);
         if (r < 0) return -r;
-        if (r > 0 && clip_ids) {   // record the cutting bisectors when asked
-            if (nclip >= emv::MAXCLIP) return emv::VS_CLIPS;
-            if (lane == 0) clip_ids[nclip] = k;
-            ++nclip;
-        }
     }
     return 0;
 }
 
-// Build the cell of sorted generator s; records the cutting bisectors.
+// Build the cell of sorted generator s.
 // Stage 1: every generator within a radius R chosen from the local spacing
 // (8th nearest of the site's 32-generator chunk), nearest first.  Stage 2
 // (exact completion): generators whose bisector still cuts the cell, in
 // distance windows [lo, hi) that shrink until they fit the candidate list,
 // nearest first, until the window passes 2 R_max.  Every generator nearer
 // than lo has been applied at each step.
-__device__ int wbuild_cell(WCell &c, const em::ChunkTree &T, const double *__restrict__ xs,
+template <class C>
+__device__ int wbuild_cell(C &c, const em::ChunkTree &T, const double *__restrict__ xs,
                            const double *__restrict__ ys, const double *__restrict__ zs,
-                           const int32_t *__restrict__ perm, int64_t s, const double *box, int K, float margin,
-                           int32_t *clip_ids, int &nclip)
+                           int64_t s, const double *box, int K, float margin)
 {
     const int lane = threadIdx.x & 31;
     int status = 0;
-    nclip = 0;
     const double gx = xs[s], gy = ys[s], gz = zs[s];
     if (!(gx > box[0] && gx < box[1] && gy > box[2] && gy < box[3] && gz > box[4] && gz < box[5]))
         return emv::VS_OUTSIDE;
     wcell_box(c, box, gx, gy, gz);
     const int64_t n = T.count[0];
-    // local spacing: the 8th smallest distance to the other members of the chunk
+    // local spacing: the 8th smallest distance to the other members of the
+    // chunk (a starting radius only, so FP32 on the rounded positions)
     double R2;
     {
         int64_t k = (s / 32) * 32 + lane;
-        double d2 = INFINITY;
+        float d2 = INFINITY;
         if (k < n && k != s) {
-            double dx = xs[k] - gx, dy = ys[k] - gy, dz = zs[k] - gz;
+            const float4 pk = T.pts[k], ps = T.pts[s];
+            const float dx = pk.x - ps.x, dy = pk.y - ps.y, dz = pk.z - ps.z;
             d2 = dx * dx + dy * dy + dz * dz;
         }
-        double kth = INFINITY;
+        float kthf = INFINITY;
         for (int r = 0; r < 8; ++r) {
-            double m = d2;
+            float m = d2;
 #pragma unroll
-            for (int o = 16; o > 0; o >>= 1) m = fmin(m, __shfl_xor_sync(0xffffffffu, m, o));
-            kth = m;
+            for (int o = 16; o > 0; o >>= 1) m = fminf(m, __shfl_xor_sync(0xffffffffu, m, o));
+            kthf = m;
             unsigned who = __ballot_sync(0xffffffffu, d2 == m);
             if (lane == __ffs(who) - 1) d2 = INFINITY;
         }
-        if (!(kth < INFINITY)) {
+        double kth = kthf;
+        if (!(kth > 0.0 && kth < INFINITY)) {
             const double bx = box[1] - box[0], by = box[3] - box[2], bz = box[5] - box[4];
             kth = 0.01 * (bx * bx + by * by + bz * bz);
         }
@@ -627,7 +662,7 @@ __device__ int wbuild_cell(WCell &c, const em::ChunkTree &T, const double *__res
     double skip2 = -1.0;
     if (nc > 0) {
         sort_cand(c, nc);
-        int st = clip_sorted(c, T, xs, ys, zs, perm, n, gx, gy, gz, nc, clip_ids, nclip);
+        int st = clip_sorted(c, T, xs, ys, zs, n, gx, gy, gz, nc);
         if (st) return status | st;
     }
     if (nc >= 0) skip2 = R2;   // every generator nearer than R was applied
@@ -645,7 +680,7 @@ __device__ int wbuild_cell(WCell &c, const em::ChunkTree &T, const double *__res
         if (m < 0) return status | emv::VS_CANDIDATES;
         if (m > 0) {
             sort_cand(c, m);
-            int st = clip_sorted(c, T, xs, ys, zs, perm, n, gx, gy, gz, m, clip_ids, nclip);
+            int st = clip_sorted(c, T, xs, ys, zs, n, gx, gy, gz, m);
             if (st) return status | st;
         }
         skip2 = hi2;
@@ -657,7 +692,8 @@ __device__ int wbuild_cell(WCell &c, const em::ChunkTree &T, const double *__res
 // outside; returns the length (0 if the plane holds no vertex, -1 on error).
 // From a vertex t holding q at position r, the next vertex around q is the
 // one across t's edge (tri[t][r + 2], q).
-__device__ int wface_loop(const WCell &c, int q, uint8_t *loop, int maxn)
+template <class C>
+__device__ int wface_loop(const C &c, int q, uint8_t *loop, int maxn)
 {
     const int cur = c.cur, nt = c.nt;
     int t0 = -1;
