@@ -374,11 +374,10 @@ def particle_weight_sum(pairs: Pairs, w, n) -> np.ndarray:
     return out
 
 
-def map_back(pairs: Pairs, w, f_cell, n) -> np.ndarray:
-    """Inverse mapping (Section 2.3): f_i = sum_j w_ij f_j / sum_j w_ij, the
-    kernel-weighted average of the cell values over particle i's cells; NaN
-    for particles without any pair.  Both sums run over each particle's pairs
-    in ascending j, one rounded product and one rounded addition per term
+def map_back_sums(pairs: Pairs, w, f_cell, n):
+    """The two sums of the inverse mapping (Section 2.3) per particle,
+    num_i = sum_j w_ij f_j and den_i = sum_j w_ij, over particle i's pairs in
+    ascending j, one rounded product and one rounded addition per term
     (np.add.at applies the additions in index order)."""
     order = np.lexsort((pairs.pair_j, pairs.pair_i))
     pi = np.asarray(pairs.pair_i)[order]
@@ -389,6 +388,14 @@ def map_back(pairs: Pairs, w, f_cell, n) -> np.ndarray:
     den = np.zeros(n)
     np.add.at(num, pi, wk * fk)
     np.add.at(den, pi, wk)
+    return num, den
+
+
+def map_back(pairs: Pairs, w, f_cell, n) -> np.ndarray:
+    """Inverse mapping (Section 2.3): f_i = sum_j w_ij f_j / sum_j w_ij, the
+    kernel-weighted average of the cell values over particle i's cells
+    (map_back_sums); NaN for particles without any pair."""
+    num, den = map_back_sums(pairs, w, f_cell, n)
     with np.errstate(invalid="ignore", divide="ignore"):
         return num / den
 
