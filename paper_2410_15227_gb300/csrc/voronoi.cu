@@ -43,10 +43,11 @@ constexpr int SLOT_FV = 3 * MAXV;
 
 // Write the faces of the finished cell c of sorted site s: per face its unit
 // normal, the neighbour id and the offset of its vertex loop, the loop's
-// vertices (CCW seen from outside, absolute coordinates) from fvbase on;
-// returns the counts and the volume (divergence theorem).  The planes are
-// formed again from their generators (emw::bisector, the builder's
-// arithmetic).  Faces beyond fcap or vertices beyond fvcap set bad.
+// vertices (CCW seen from outside, absolute coordinates, the FP64 meets of
+// emw::finish_vertices) from fvbase on; returns the counts and the volume
+// (divergence theorem).  The planes are formed again from their generators
+// (emw::bisector, the builder's arithmetic).  Faces beyond fcap or vertices
+// beyond fvcap set bad.
 template <class C>
 __device__ void emit_faces(const C &c, const double *__restrict__ xs, const double *__restrict__ ys,
                            const double *__restrict__ zs, const int32_t *__restrict__ perm, const double *box,
@@ -77,7 +78,6 @@ __device__ void emit_faces(const C &c, const double *__restrict__ xs, const doub
             if (fi >= fcap || fvi + n > fvcap) {
                 err = true;
             } else {
-                const int cur = c.cur;
                 const int sid = c.sid[q];
                 double nx, ny, nz, d;
                 if (sid >= 0) emw::bisector(xs, ys, zs, sid, gx, gy, gz, nx, ny, nz, d);
@@ -93,7 +93,7 @@ __device__ void emit_faces(const C &c, const double *__restrict__ xs, const doub
                 fvo[fi] = fvi;
                 double ax = 0.0, ay = 0.0, az = 0.0;   // twice the vector area
                 for (int i = 0; i < n; ++i) {
-                    const double *pa = c.v[cur][loop[i]], *pb = c.v[cur][loop[(i + 1) % n]];
+                    const double *pa = c.u.vx[loop[i]], *pb = c.u.vx[loop[(i + 1) % n]];
                     ax += pa[1] * pb[2] - pa[2] * pb[1];
                     ay += pa[2] * pb[0] - pa[0] * pb[2];
                     az += pa[0] * pb[1] - pa[1] * pb[0];
@@ -146,16 +146,18 @@ __device__ void build_one(C &c, const BuildArgs &a, int64_t s, bool first_pass)
         if (lane == 0) atomicOr(a.status_or, VS_BOUNDS);
         return;
     }
-    int st = emw::wbuild_cell(c, a.T, a.xs, a.ys, a.zs, s, a.box, a.K, a.margin);
+    const double gx = a.xs[s], gy = a.ys[s], gz = a.zs[s];
+    const emw::Frame F{a.xs, a.ys, a.zs, a.box, gx, gy, gz};
+    int st = emw::wbuild_cell(c, a.T, F, s, a.K, a.margin);
     if (first_pass && st == VS_CAPACITY) {
         if (lane == 0) a.retry_list[atomicAdd(a.retry_n, 1)] = (int32_t)s;
         return;
     }
     int nf = 0, nv = 0;
     double vol = 0.0;
-    const double gx = a.xs[s], gy = a.ys[s], gz = a.zs[s];
     if (!st) {
         bool bad = false;
+        emw::finish_vertices(c, F);
         emit_faces(c, a.xs, a.ys, a.zs, a.perm, a.box, gx, gy, gz, SLOT_F, SLOT_FV, a.s_fvo + s * SLOT_F,
                    a.s_verts + s * (3 * SLOT_FV), a.s_normals + s * (3 * SLOT_F), a.s_nbr + s * SLOT_F, nf, nv, vol,
                    bad);
