@@ -33,7 +33,7 @@ using emw::WCell;
 
 constexpr int VW = 2;   // warps (cells) per block
 #ifndef EM_VOR_MINB
-#define EM_VOR_MINB 12   // resident blocks per SM asked of the compiler in the first pass
+#define EM_VOR_MINB 14   // resident blocks per SM asked of the compiler in the first pass
 #endif
 
 // Capacity of a cell's scratch slot: faces (planes) and face-vertices (every
