@@ -747,43 +747,43 @@ __device__ int wbuild_cell(C &c, const em::ChunkTree &T, const Frame &F, int64_t
         // members lie mostly to one side), hence the factor 1/4
         R2 = 0.25 * kth * cbrt(1.5 * K / 8.0) * cbrt(1.5 * K / 8.0);
     }
-    // stage 1: shrink or grow R until the candidates fit and number at least K
-    double lo_ok = 0.0, hi_bad = INFINITY;
-    int nc = -1;
-    for (int it = 0; it < 48; ++it) {
-        nc = gather(c, T, xs, ys, zs, s, gx, gy, gz, -1.0, R2, margin, status);
-        if (status & emv::VS_COINCIDENT) return status;
-        if (nc < 0) {
-            hi_bad = R2;
-            R2 = lo_ok > 0.0 ? sqrt(lo_ok * hi_bad) : 0.3 * R2;
-            continue;
-        }
-        if (nc < K && nc < n - 1 && hi_bad == INFINITY && it < 40) {
-            lo_ok = R2;
-            R2 *= 2.0;
-            continue;
-        }
-        break;
-    }
+    // round -1 is stage 1, rounds 0.. stage 2; both clip through the one call
+    // site below (one inlined copy of the clip keeps the code small)
     double skip2 = -1.0;
-    if (nc > 0) {
-        sort_cand(c, nc);
-        int st = clip_sorted(c, T, F, n, nc);
-        if (st) return status | st;
-    }
-    if (nc >= 0) skip2 = R2;   // every generator nearer than R was applied
-    // stage 2: windows [skip2, hi2) of generators that still cut, nearest first
-    for (int round = 0; round < 256; ++round) {
-        const double lim2 = 4.0 * wrmax2(c, F) * (1.0 + 1e-12);   // no generator beyond 2 R_max can cut
-        if (skip2 >= lim2) return status;
-        double hi2 = lim2;
+    for (int round = -1; round < 256; ++round) {
         int m = -1;
-        for (int h = 0; h < 64; ++h) {
-            m = gather_cutting(c, T, xs, ys, zs, s, gx, gy, gz, skip2, hi2);
-            if (m >= 0) break;
-            hi2 = (skip2 > 0.0 ? skip2 : 0.0) + 0.5 * (hi2 - (skip2 > 0.0 ? skip2 : 0.0));
+        double hi2 = 0.0;
+        if (round < 0) {
+            // stage 1: shrink or grow R until the candidates fit and number at least K
+            double lo_ok = 0.0, hi_bad = INFINITY;
+            for (int it = 0; it < 48; ++it) {
+                m = gather(c, T, xs, ys, zs, s, gx, gy, gz, -1.0, R2, margin, status);
+                if (status & emv::VS_COINCIDENT) return status;
+                if (m < 0) {
+                    hi_bad = R2;
+                    R2 = lo_ok > 0.0 ? sqrt(lo_ok * hi_bad) : 0.3 * R2;
+                    continue;
+                }
+                if (m < K && m < n - 1 && hi_bad == INFINITY && it < 40) {
+                    lo_ok = R2;
+                    R2 *= 2.0;
+                    continue;
+                }
+                break;
+            }
+            hi2 = m >= 0 ? R2 : -1.0;   // every generator nearer than R gets applied
+        } else {
+            // stage 2: windows [skip2, hi2) of generators that still cut, nearest first
+            const double lim2 = 4.0 * wrmax2(c, F) * (1.0 + 1e-12);   // no generator beyond 2 R_max can cut
+            if (skip2 >= lim2) return status;
+            hi2 = lim2;
+            for (int h = 0; h < 64; ++h) {
+                m = gather_cutting(c, T, xs, ys, zs, s, gx, gy, gz, skip2, hi2);
+                if (m >= 0) break;
+                hi2 = (skip2 > 0.0 ? skip2 : 0.0) + 0.5 * (hi2 - (skip2 > 0.0 ? skip2 : 0.0));
+            }
+            if (m < 0) return status | emv::VS_CANDIDATES;
         }
-        if (m < 0) return status | emv::VS_CANDIDATES;
         if (m > 0) {
             sort_cand(c, m);
             int st = clip_sorted(c, T, F, n, m);
