@@ -107,7 +107,10 @@ __device__ __forceinline__ float cell_dist2_f32(float rx, float ry, float rz, in
 // (j << 32 | i) keys and near flags: unordered, the caller sorts them.  Hits
 // past the capacity are counted but not written; the caller then repeats the
 // pass with room for all of them.
-constexpr int PAIRS_WARPS = 4;
+#ifndef EM_PAIRS_WARPS
+#define EM_PAIRS_WARPS 4   // warps (cells) per block (build-time tuning knob)
+#endif
+constexpr int PAIRS_WARPS = EM_PAIRS_WARPS;
 constexpr int PAIRS_BUF = 128;   // hits a warp holds before writing them out
 
 __global__ void __launch_bounds__(32 * PAIRS_WARPS)
