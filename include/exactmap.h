@@ -247,6 +247,28 @@ int voronoi_destroy(em_voronoi *v);
  * read the count.  EM_ECAPACITY if the pairs reach 2^31. */
 int find_pairs(em_ctx *ctx, int64_t np, const double *d_x, const double *d_y, const double *d_z,
                const double *d_h, const em_voronoi *v, em_pairs **out, int64_t *npairs);
+/* Streamed pair finding, for pair lists one would rather not hold at once
+ * (a chunk capacity in pairs).
+ *   find_pairs_plan: counts every cell's pairs (find_pairs' pass without
+ *     output) and cuts the cells into consecutive ranges whose pairs number at
+ *     most chunk_capacity (a cell with more is a range of its own).
+ *     h_bounds (host, caller-allocated, ncell + 1 entries): the ranges are
+ *     [h_bounds[c], h_bounds[c + 1]) for c < *h_nchunks; *h_npairs (may be
+ *     NULL): the total.  Synchronises the stream.
+ *   find_pairs_cells: the pairs of the cells [cell_begin, cell_end) only, as
+ *     find_pairs returns them (sorted by (j, i); every cell of v indexed, the
+ *     others without pairs).  npairs_hint: the range's count from the plan
+ *     (sizes the buffer; <= 0 if unknown).
+ * The chunks' pair lists together are find_pairs' list.  map_exact on a
+ * chunk gives complete cell densities for its cells (0 for the others, so
+ * the chunks' densities add up) and per-particle weight sums that add over
+ * the chunks; map_back_sums adds the inverse mapping's sums over them. */
+int find_pairs_plan(em_ctx *ctx, int64_t np, const double *d_x, const double *d_y, const double *d_z,
+                    const double *d_h, const em_voronoi *v, int64_t chunk_capacity, int64_t *h_bounds,
+                    int64_t *h_nchunks, int64_t *h_npairs);
+int find_pairs_cells(em_ctx *ctx, int64_t np, const double *d_x, const double *d_y, const double *d_z,
+                     const double *d_h, const em_voronoi *v, int64_t cell_begin, int64_t cell_end,
+                     int64_t npairs_hint, em_pairs **out, int64_t *npairs);
 /* Import a pair list sorted by (j, i) (device int32 arrays). */
 int pairs_from_list(em_ctx *ctx, int64_t npairs, const int32_t *d_pair_i, const int32_t *d_pair_j,
                     int64_t np, const em_voronoi *v, em_pairs **out);
@@ -331,6 +353,17 @@ int map_exact_noalloc(em_ctx *ctx, const em_pairs *pr, const double *d_x, const 
  *   ps, t, d_f_particle_out[n particles, original order]: all NULL, or all set. */
 int map_back(em_ctx *ctx, const em_pairs *pr, const double *d_w, const double *d_f_cell, double *d_f_out,
              const em_pseudo *ps, const em_tree *t, double *d_f_particle_out);
+/* The inverse mapping in parts (chunks of pairs, or the ranks of a spatial
+ * split): map_back_sums ADDS sum_j w_ij f_j to d_num[i] and sum_j w_ij to
+ * d_den[i] over the pairs of pr (ascending j, as map_back sums), so that
+ * f_i = num_i / den_i once every part is in; inherit gives every SPH particle
+ * the value of the pseudo-particle it belongs to (Section 2.5), as map_back
+ * does with ps and t.
+ *   d_num, d_den[np] (device, caller-initialised); d_f_pseudo[ps n],
+ *   d_f_particle_out[n particles, original order] (device). */
+int map_back_sums(em_ctx *ctx, const em_pairs *pr, const double *d_w, const double *d_f_cell, double *d_num,
+                  double *d_den);
+int inherit(em_ctx *ctx, const em_pseudo *ps, const em_tree *t, const double *d_f_pseudo, double *d_f_particle_out);
 
 /* ---- map_batch ------------------------------------------------------------------
  * Many independent snapshots through the whole path (the paper's runtime
@@ -380,6 +413,26 @@ typedef struct {
 
 int map_batch(int device, int nsnap, em_snapshot *snaps, const em_params *p, int nworkers, int tune,
               int *h_variant, double *h_map_ms, int64_t *h_launches);
+
+/* The same batch as a handle (create, add, run), for callers that collect
+ * snapshots as they come.
+ *   map_batch_create: the device, parameters (copied) and host threads of
+ *     the runs (as map_batch's).
+ *   map_batch_add: copies the record; the arrays it points to stay the
+ *     caller's and must stay valid until a run that maps it returns.
+ *     *h_index (may be NULL): its index, in the order of the adds.
+ *   map_batch_run: map_batch over every snapshot added so far (the same
+ *     results, bit for bit); may be called again after more adds.
+ *   map_batch_get: copies record `index` out, with the outputs of the last
+ *     run (npseudo, npairs, nfp64, status; -1 before any run).
+ *   map_batch_destroy: frees the handle (NULL is accepted).
+ * EM_EINVAL for a NULL handle, a bad index or an invalid record. */
+typedef struct em_batch em_batch;
+int map_batch_create(int device, const em_params *p, int nworkers, em_batch **out);
+int map_batch_add(em_batch *b, const em_snapshot *s, int *h_index);
+int map_batch_run(em_batch *b, int tune, int *h_variant, double *h_map_ms, int64_t *h_launches);
+int map_batch_get(const em_batch *b, int index, em_snapshot *out);
+int map_batch_destroy(em_batch *b);
 
 #ifdef __cplusplus
 }

@@ -68,9 +68,18 @@ SIGNATURES = {
     "voronoi_centroids": (I32, [P, P, P, P, P]),
     "lloyd": (I32, [P, I64, P, P, P, P, I32, PPAR]),
     "map_batch": (I32, [I32, I32, C.POINTER(EmSnapshot), PPAR, I32, I32, PI32, P, PI64]),
+    "map_batch_create": (I32, [I32, PPAR, I32, PP]),
+    "map_batch_add": (I32, [P, C.POINTER(EmSnapshot), PI32]),
+    "map_batch_run": (I32, [P, I32, PI32, P, PI64]),
+    "map_batch_get": (I32, [P, I32, C.POINTER(EmSnapshot)]),
+    "map_batch_destroy": (I32, [P]),
     "voronoi_get": (I32, [P, P] + [P] * 6),
     "voronoi_destroy": (I32, [P]),
     "find_pairs": (I32, [P, I64, P, P, P, P, P, PP, PI64]),
+    "find_pairs_plan": (I32, [P, I64, P, P, P, P, P, I64, P, PI64, PI64]),
+    "find_pairs_cells": (I32, [P, I64, P, P, P, P, P, I64, I64, I64, PP, PI64]),
+    "map_back_sums": (I32, [P, P, P, P, P, P]),
+    "inherit": (I32, [P, P, P, P, P]),
     "pairs_from_list": (I32, [P, I64, P, P, I64, P, PP]),
     "pairs_info": (I32, [P, PI64, PI64, PI64]),
     "pairs_get": (I32, [P, P, P, P, P, P]),

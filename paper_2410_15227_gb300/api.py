@@ -315,6 +315,83 @@ def lloyd(ctx: Context, gx, gy, gz, box, iters: int = 5, params: Params | None =
     return gx, gy, gz
 
 
+def _snapshot_record(e, sn):
+    """Fill the em_snapshot record e from a snapshot dict (see map_batch);
+    returns the host source array to keep alive and the output tensors."""
+    x = sn["x"]
+    np_, ng = x.numel(), sn["gx"].numel()
+    dev = x.device
+    rho = torch.empty(ng, dtype=f64, device=dev)
+    f = torch.empty(np_, dtype=f64, device=dev) if sn.get("f_cell") is not None else None
+    src = [float(v) for v in torch.as_tensor(sn["sources"], dtype=f64).reshape(-1).tolist()]
+    hsrc = (C.c_double * len(src))(*src)
+    e.n, e.ngen = np_, ng
+    for name in ("x", "y", "z", "m", "h"):
+        setattr(e, "d_" + name, _ptr(sn[name], f64, np_, name))
+    for name in ("gx", "gy", "gz"):
+        setattr(e, "d_" + name, _ptr(sn[name], f64, ng, name))
+    for i, b in enumerate(sn["box"]):
+        e.box[i] = float(b)
+    e.nsrc = len(src) // 3
+    e.h_src = C.cast(hsrc, C.c_void_p)
+    e.d_f_cell = _ptr(sn.get("f_cell"), f64, ng, "f_cell")
+    e.d_rho = _ptr(rho, f64, ng)
+    e.d_f = _ptr(f, f64, np_) if f is not None else None
+    return hsrc, (rho, f)
+
+
+class Batch:
+    """The batch as a handle (map_batch_create / add / run / get): snapshots
+    added one at a time (dicts as for map_batch), mapped together by run().
+    The snapshots' tensors must stay alive until a run that maps them
+    returns; the handle keeps references to them."""
+
+    def __init__(self, device: int, params: Params, nworkers: int = 4):
+        self._p = params.native()
+        h = C.c_void_p()
+        N.call("map_batch_create", int(device), C.byref(self._p), int(nworkers), C.byref(h))
+        self.handle = h
+        self._keep, self._outs = [], []
+
+    def add(self, snapshot) -> int:
+        rec = N.EmSnapshot()
+        hsrc, out = _snapshot_record(rec, snapshot)
+        idx = C.c_int32()
+        N.call("map_batch_add", self.handle, C.byref(rec), C.byref(idx))
+        self._keep.append((hsrc, snapshot))
+        self._outs.append(out)
+        return idx.value
+
+    def run(self, tune: bool = False, info: dict | None = None):
+        """Map every snapshot added so far; returns the results as map_batch
+        does (one dict per snapshot, and the kernel launches)."""
+        launches = C.c_int64()
+        variant = C.c_int32()
+        ms = (C.c_double * 2)()
+        rc = N.lib().map_batch_run(self.handle, int(bool(tune)), C.byref(variant), C.cast(ms, C.c_void_p),
+                                   C.byref(launches))
+        if info is not None:
+            info["variant"] = variant.value
+            info["map_ms"] = (ms[0], ms[1])
+        res = [dict(rho=self._outs[k][0], f=self._outs[k][1], **self.get(k)) for k in range(len(self._outs))]
+        if rc != N.EM_OK:
+            err = N.NativeError("map_batch_run", rc, N.lib().em_last_error().decode(errors="replace"))
+            err.results = res
+            raise err
+        return res, launches.value
+
+    def get(self, index: int) -> dict:
+        rec = N.EmSnapshot()
+        N.call("map_batch_get", self.handle, int(index), C.byref(rec))
+        return dict(npseudo=rec.npseudo, npairs=rec.npairs, nfp64=rec.nfp64, status=rec.status)
+
+    def __del__(self):
+        h = getattr(self, "handle", None)
+        if h is not None and h.value:
+            N.lib().map_batch_destroy(h)
+            self.handle = None
+
+
 def map_batch(device: int, snapshots, params: Params, nworkers: int = 4, tune: bool = False, info: dict | None = None):
     """Independent snapshots through the whole path: build_tree ...
     find_pairs per snapshot on nworkers host threads with a stream each, then
@@ -330,28 +407,9 @@ def map_batch(device: int, snapshots, params: Params, nworkers: int = 4, tune: b
     arr = (N.EmSnapshot * max(n, 1))()
     keep, outs = [], []
     for k, sn in enumerate(snapshots):
-        x = sn["x"]
-        np_, ng = x.numel(), sn["gx"].numel()
-        dev = x.device
-        rho = torch.empty(ng, dtype=f64, device=dev)
-        f = torch.empty(np_, dtype=f64, device=dev) if sn.get("f_cell") is not None else None
-        src = [float(v) for v in torch.as_tensor(sn["sources"], dtype=f64).reshape(-1).tolist()]
-        hsrc = (C.c_double * len(src))(*src)
-        e = arr[k]
-        e.n, e.ngen = np_, ng
-        for name in ("x", "y", "z", "m", "h"):
-            setattr(e, "d_" + name, _ptr(sn[name], f64, np_, name))
-        for name in ("gx", "gy", "gz"):
-            setattr(e, "d_" + name, _ptr(sn[name], f64, ng, name))
-        for i, b in enumerate(sn["box"]):
-            e.box[i] = float(b)
-        e.nsrc = len(src) // 3
-        e.h_src = C.cast(hsrc, C.c_void_p)
-        e.d_f_cell = _ptr(sn.get("f_cell"), f64, ng, "f_cell")
-        e.d_rho = _ptr(rho, f64, ng)
-        e.d_f = _ptr(f, f64, np_) if f is not None else None
+        hsrc, out = _snapshot_record(arr[k], sn)
         keep.append(hsrc)
-        outs.append((rho, f))
+        outs.append(out)
     p = params.native()
     launches = C.c_int64()
     variant = C.c_int32()
@@ -390,6 +448,32 @@ def find_pairs(ctx: Context, x, y, z, h_, vor: Voronoi) -> Pairs:
     npairs = C.c_int64()
     N.call("find_pairs", ctx.handle, n, _ptr(x, f64, n, "x"), _ptr(y, f64, n, "y"),
            _ptr(z, f64, n, "z"), _ptr(h_, f64, n, "h"), vor.handle, C.byref(h), C.byref(npairs))
+    return Pairs(ctx, h)
+
+
+def find_pairs_plan(ctx: Context, x, y, z, h_, vor: Voronoi, chunk_capacity: int):
+    """Cell ranges whose pairs number at most chunk_capacity each: returns
+    (bounds as a list of ncell-range ends, starting with 0, total pairs)."""
+    n = x.numel()
+    nc = vor.info()[0]
+    bounds = (C.c_int64 * (nc + 1))()
+    nch = C.c_int64()
+    tot = C.c_int64()
+    N.call("find_pairs_plan", ctx.handle, n, _ptr(x, f64, n, "x"), _ptr(y, f64, n, "y"), _ptr(z, f64, n, "z"),
+           _ptr(h_, f64, n, "h"), vor.handle, int(chunk_capacity), C.cast(bounds, C.c_void_p), C.byref(nch),
+           C.byref(tot))
+    return [bounds[c] for c in range(nch.value + 1)], tot.value
+
+
+def find_pairs_cells(ctx: Context, x, y, z, h_, vor: Voronoi, cell_begin: int, cell_end: int,
+                     npairs_hint: int = 0) -> Pairs:
+    """The pairs of the cells [cell_begin, cell_end) only (the streamed form)."""
+    n = x.numel()
+    h = C.c_void_p()
+    npairs = C.c_int64()
+    N.call("find_pairs_cells", ctx.handle, n, _ptr(x, f64, n, "x"), _ptr(y, f64, n, "y"),
+           _ptr(z, f64, n, "z"), _ptr(h_, f64, n, "h"), vor.handle, int(cell_begin), int(cell_end),
+           int(npairs_hint), C.byref(h), C.byref(npairs))
     return Pairs(ctx, h)
 
 
@@ -477,6 +561,24 @@ def map_exact_noalloc(ctx: Context, pairs: Pairs, x, y, z, h_, m, vor: Voronoi, 
 
 
 NOALLOC_MAX_PAIRS = 1 << 20
+
+
+def map_back_sums(ctx: Context, pairs: Pairs, w, f_cell, num, den):
+    """Adds sum_j w_ij f_j to num and sum_j w_ij to den (device tensors, one
+    entry per (pseudo-)particle) over the pairs given."""
+    npairs, np_, nc = pairs.info()
+    N.call("map_back_sums", ctx.handle, pairs.handle, _ptr(w, f64, npairs), _ptr(f_cell, f64, nc),
+           _ptr(num, f64, np_, "num"), _ptr(den, f64, np_, "den"))
+    return num, den
+
+
+def inherit(ctx: Context, pseudo: Pseudo, tree: Tree, f_pseudo):
+    """Each SPH particle takes its pseudo-particle's value (Section 2.5)."""
+    n, _, _ = tree.info()
+    fp = ctx.empty(n)
+    N.call("inherit", ctx.handle, pseudo.handle, tree.handle, _ptr(f_pseudo, f64, pseudo.info()[0], "f_pseudo"),
+           _ptr(fp))
+    return fp
 
 
 def map_back(ctx: Context, pairs: Pairs, w, f_cell, pseudo: Pseudo | None = None,

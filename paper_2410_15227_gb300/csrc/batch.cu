@@ -447,3 +447,54 @@ EM_EXPORT int map_batch(int device, int nsnap, em_snapshot *snaps, const em_para
     if (h_launches) *h_launches = launches;
     return rc;
 }
+
+// The batch as a handle: the snapshots' records collected by map_batch_add,
+// mapped together by map_batch_run.
+struct em_batch {
+    int device;
+    em_params p;
+    int nworkers;
+    std::vector<em_snapshot> snaps;
+};
+
+EM_EXPORT int map_batch_create(int device, const em_params *p, int nworkers, em_batch **out)
+{
+    EM_CHECK_ARG(p && out && device >= 0 && nworkers >= 1 && nworkers <= 64);
+    EM_CHECK_ARG(p->precision == 0 || p->precision == 1);
+    *out = new em_batch{device, *p, nworkers, {}};
+    return EM_OK;
+}
+
+EM_EXPORT int map_batch_add(em_batch *b, const em_snapshot *s, int *h_index)
+{
+    EM_CHECK_ARG(b && s && b->snaps.size() < (size_t)INT32_MAX);
+    EM_CHECK_ARG(s->n >= 1 && s->ngen >= 1 && s->d_x && s->d_y && s->d_z && s->d_m && s->d_h && s->d_gx &&
+                 s->d_gy && s->d_gz && s->d_rho && s->h_src && s->nsrc >= 1);
+    EM_CHECK_ARG((s->d_f_cell == nullptr) == (s->d_f == nullptr));
+    b->snaps.push_back(*s);
+    em_snapshot &r = b->snaps.back();
+    r.status = -1;
+    r.npseudo = r.npairs = r.nfp64 = 0;
+    if (h_index) *h_index = (int)b->snaps.size() - 1;
+    return EM_OK;
+}
+
+EM_EXPORT int map_batch_run(em_batch *b, int tune, int *h_variant, double *h_map_ms, int64_t *h_launches)
+{
+    EM_CHECK_ARG(b);
+    return map_batch(b->device, (int)b->snaps.size(), b->snaps.data(), &b->p, b->nworkers, tune, h_variant,
+                     h_map_ms, h_launches);
+}
+
+EM_EXPORT int map_batch_get(const em_batch *b, int index, em_snapshot *out)
+{
+    EM_CHECK_ARG(b && out && index >= 0 && (size_t)index < b->snaps.size());
+    *out = b->snaps[index];
+    return EM_OK;
+}
+
+EM_EXPORT int map_batch_destroy(em_batch *b)
+{
+    delete b;
+    return EM_OK;
+}

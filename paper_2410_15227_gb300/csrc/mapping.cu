@@ -1453,6 +1453,50 @@ __global__ void k_inherit(int64_t npseudo, const int32_t *__restrict__ first, co
     for (int32_t k = first[a]; k < first[a] + count[a]; ++k) f_particle[perm[k]] = f;
 }
 
+// The two sums of map_back per particle, added into num and den (ascending
+// j, every product and sum rounded on its own, as k_map_back).
+__global__ void k_map_back_sums(int64_t np, const int64_t *__restrict__ off, const int32_t *__restrict__ idx,
+                                const int32_t *__restrict__ pj, const double *__restrict__ w,
+                                const double *__restrict__ f_cell, double *__restrict__ num, double *__restrict__ den)
+{
+    int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (i >= np) return;
+    double a = 0.0, b = 0.0;
+    for (int64_t k = off[i]; k < off[i + 1]; ++k) {
+        const int32_t q = idx[k];
+        const double wq = w[q];
+        a = __dadd_rn(a, __dmul_rn(wq, f_cell[pj[q]]));
+        b = __dadd_rn(b, wq);
+    }
+    num[i] = __dadd_rn(num[i], a);
+    den[i] = __dadd_rn(den[i], b);
+}
+
+EM_EXPORT int map_back_sums(em_ctx *ctx, const em_pairs *pr, const double *d_w, const double *d_f_cell,
+                            double *d_num, double *d_den)
+{
+    EM_CHECK_ARG(ctx && pr && d_num && d_den && (pr->npairs == 0 || d_w) && (pr->ncell == 0 || d_f_cell));
+    if (pr->np) {
+        k_map_back_sums<<<em_grid(pr->np, 256), 256, 0, ctx->stream>>>(pr->np, pr->part_pair_off,
+                                                                        pr->part_pair_idx, pr->pair_j, d_w,
+                                                                        d_f_cell, d_num, d_den);
+        EM_LAUNCHED(ctx);
+    }
+    return EM_OK;
+}
+
+EM_EXPORT int inherit(em_ctx *ctx, const em_pseudo *ps, const em_tree *t, const double *d_f_pseudo,
+                      double *d_f_particle_out)
+{
+    EM_CHECK_ARG(ctx && ps && t && d_f_particle_out && (ps->n == 0 || d_f_pseudo));
+    if (ps->n) {
+        k_inherit<<<em_grid(ps->n, 128), 128, 0, ctx->stream>>>(ps->n, ps->first, ps->count, t->perm, d_f_pseudo,
+                                                                 d_f_particle_out);
+        EM_LAUNCHED(ctx);
+    }
+    return EM_OK;
+}
+
 EM_EXPORT int map_back(em_ctx *ctx, const em_pairs *pr, const double *d_w, const double *d_f_cell, double *d_f_out,
                        const em_pseudo *ps, const em_tree *t, double *d_f_particle_out)
 {

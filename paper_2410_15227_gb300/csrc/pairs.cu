@@ -12,6 +12,8 @@
 // The pair set is therefore the FP64 predicate's.  Hits are compacted with a
 // warp ballot into a per-warp buffer and written, unordered, at positions
 // reserved with an atomic add; one radix sort by (j, i) puts them in order.
+#include <vector>
+
 #include "common.cuh"
 #include "tree_util.cuh"
 
@@ -114,31 +116,35 @@ constexpr int PAIRS_WARPS = EM_PAIRS_WARPS;
 constexpr int PAIRS_BUF = 128;   // hits a warp holds before writing them out
 
 __global__ void __launch_bounds__(32 * PAIRS_WARPS)
-    k_cell_pairs(int64_t ncell, em::ChunkTree T, const double *__restrict__ xs, const double *__restrict__ ys,
+    k_cell_pairs(int64_t cell0, int64_t cell1, em::ChunkTree T, const double *__restrict__ xs, const double *__restrict__ ys,
                  const double *__restrict__ zs, const double *__restrict__ hs, const int32_t *__restrict__ perm,
                  const double *__restrict__ gen, const double *__restrict__ radius, const int64_t *__restrict__ cfo,
                  const int64_t *__restrict__ fvo, const PlaneD *__restrict__ plane, const EdgeD *__restrict__ edge,
                  const PlaneF *__restrict__ plane_f, const EdgeF *__restrict__ edge_f, float margin,
                  unsigned long long *__restrict__ counter, int64_t capacity, uint64_t *__restrict__ keys,
-                 int32_t *__restrict__ nearf)
+                 int32_t *__restrict__ nearf, int64_t *__restrict__ cell_count)
 {
     __shared__ uint64_t buf_key[PAIRS_WARPS][PAIRS_BUF];
     __shared__ int32_t buf_near[PAIRS_WARPS][PAIRS_BUF];
     __shared__ int32_t cand_buf[PAIRS_WARPS][64];   // a chunk adds at most 32 to fewer than 32
     const int w = threadIdx.x >> 5;
-    int64_t j = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
-    if (j >= ncell) return;   // the whole warp
+    int64_t j = cell0 + ((blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5);
+    if (j >= cell1) return;   // the whole warp
     const int lane = threadIdx.x & 31;
     int nb = 0;   // hits in the warp's buffer (the same on every lane)
+    int64_t ncell_hits = 0;
+    // with capacity 0 the pass only counts (cell_count)
     auto write_out = [&]() {
-        unsigned long long at = 0;
-        if (lane == 0) at = atomicAdd(counter, (unsigned long long)nb);
-        at = __shfl_sync(0xffffffffu, at, 0);
-        for (int t = lane; t < nb; t += 32) {
-            const unsigned long long pos = at + (unsigned long long)t;
-            if (pos < (unsigned long long)capacity) {
-                keys[pos] = buf_key[w][t];
-                nearf[pos] = buf_near[w][t];
+        if (capacity > 0) {
+            unsigned long long at = 0;
+            if (lane == 0) at = atomicAdd(counter, (unsigned long long)nb);
+            at = __shfl_sync(0xffffffffu, at, 0);
+            for (int t = lane; t < nb; t += 32) {
+                const unsigned long long pos = at + (unsigned long long)t;
+                if (pos < (unsigned long long)capacity) {
+                    keys[pos] = buf_key[w][t];
+                    nearf[pos] = buf_near[w][t];
+                }
             }
         }
         __syncwarp();
@@ -183,6 +189,7 @@ __global__ void __launch_bounds__(32 * PAIRS_WARPS)
         }
         __syncwarp();
         nb += __popc(b);
+        ncell_hits += __popc(b);
     };
     // candidates within R_j + 2h (+ the band, which here also covers the FP32
     // rounding of the coordinates) collect in a per-warp buffer and are
@@ -214,6 +221,7 @@ __global__ void __launch_bounds__(32 * PAIRS_WARPS)
     });
     if (nc > 0) classify(lane < nc ? cb[lane] : 0, lane < nc);
     if (nb > 0) write_out();
+    if (cell_count && lane == 0) cell_count[j - cell0] = ncell_hits;
 }
 
 __global__ void k_split_keys(int64_t n, const uint64_t *__restrict__ keys, const int32_t *__restrict__ nearf,
@@ -279,35 +287,65 @@ int em_point_bbox(em_ctx *ctx, int64_t n, const double *x, const double *y, cons
     return EM_OK;
 }
 
-static int find_pairs_impl(em_ctx *ctx, int64_t np, const double *x, const double *y, const double *z,
-                           const double *h, const em_voronoi *v, em_pairs *pr)
+// The particles' side of pair finding: Morton order, sorted copies and the
+// sphere hierarchy (radius 2h), and the FP32 margin of the box.
+struct PairParticles {
+    int32_t *perm;
+    double *xs, *ys, *zs, *hs;
+    em::ChunkTree T;
+    float margin;
+};
+
+static int prepare_particles(em_ctx *ctx, DevArena &tmp, int64_t np, const double *x, const double *y,
+                             const double *z, const double *h, PairParticles &P)
 {
-    cudaStream_t st = ctx->stream;
-    DevArena tmp(st, true);
     double box[6];
     EM_TRY(em_point_bbox(ctx, np, x, y, z, box));
     uint64_t *mkey;
-    int32_t *perm;
-    double *xs, *ys, *zs, *hs;
     EM_TRY(tmp.alloc(&mkey, np));
-    EM_TRY(tmp.alloc(&perm, np));
-    EM_TRY(tmp.alloc(&xs, np));
-    EM_TRY(tmp.alloc(&ys, np));
-    EM_TRY(tmp.alloc(&zs, np));
-    EM_TRY(tmp.alloc(&hs, np));
-    EM_TRY(em_morton_sort(ctx, np, x, y, z, box, mkey, perm));
-    EM_TRY(em_gather_sorted(ctx, np, perm, x, y, z, h, xs, ys, zs, hs));
-    em::ChunkTree T;
-    EM_TRY(em_chunk_tree_build(ctx, tmp, np, xs, ys, zs, hs, 2.0, &T));
+    EM_TRY(tmp.alloc(&P.perm, np));
+    EM_TRY(tmp.alloc(&P.xs, np));
+    EM_TRY(tmp.alloc(&P.ys, np));
+    EM_TRY(tmp.alloc(&P.zs, np));
+    EM_TRY(tmp.alloc(&P.hs, np));
+    EM_TRY(em_morton_sort(ctx, np, x, y, z, box, mkey, P.perm));
+    EM_TRY(em_gather_sorted(ctx, np, P.perm, x, y, z, h, P.xs, P.ys, P.zs, P.hs));
+    EM_TRY(em_chunk_tree_build(ctx, tmp, np, P.xs, P.ys, P.zs, P.hs, 2.0, &P.T));
     double ext = 0.0;
     for (int c = 0; c < 6; ++c) ext = fmax(ext, fabs(box[c]));
-    const float margin = (float)(4e-7 * (ext + 1.0));
+    P.margin = (float)(4e-7 * (ext + 1.0));
+    return EM_OK;
+}
+
+static void launch_cell_pairs(em_ctx *ctx, const PairParticles &P, const em_voronoi *v, int64_t cell0, int64_t cell1,
+                              unsigned long long *counter, int64_t capacity, uint64_t *keys, int32_t *nearf,
+                              int64_t *cell_count)
+{
+    k_cell_pairs<<<em_grid((cell1 - cell0) * 32, 32 * PAIRS_WARPS), 32 * PAIRS_WARPS, 0, ctx->stream>>>(
+        cell0, cell1, P.T, P.xs, P.ys, P.zs, P.hs, P.perm, v->gen, v->radius, v->cell_face_off, v->face_vert_off,
+        v->plane, v->edge, v->plane_f, v->edge_f, P.margin, counter, capacity, keys, nearf, cell_count);
+}
+
+// The pairs of the cells [cell0, cell1) into pr (all of v's cells indexed,
+// the others without pairs).  capacity_hint > 0: the expected count (the
+// hit buffer's size; a pass that finds more repeats once with the exact
+// size); otherwise the context's hint from its last call, or a guess.
+static int find_pairs_impl(em_ctx *ctx, int64_t np, const double *x, const double *y, const double *z,
+                           const double *h, const em_voronoi *v, em_pairs *pr, int64_t cell0, int64_t cell1,
+                           int64_t capacity_hint)
+{
+    cudaStream_t st = ctx->stream;
+    DevArena tmp(st, true);
+    PairParticles P;
+    EM_TRY(prepare_particles(ctx, tmp, np, x, y, z, h, P));
     const int64_t nc = v->ncell;
-    // one pass into an unsorted buffer sized from the last call (or a guess
-    // on the first), repeated once with the exact size if it overflowed
+    // one pass into an unsorted buffer sized from the hint (or the last call,
+    // or a guess on the first), repeated once with the exact size if it
+    // overflowed
     unsigned long long *counter;
     EM_TRY(tmp.alloc(&counter, 1));
-    int64_t capacity = ctx->pairs_hint > 0 ? ctx->pairs_hint : 64 * np + (1 << 20);
+    int64_t capacity = capacity_hint > 0 ? capacity_hint
+                                         : (ctx->pairs_hint > 0 ? ctx->pairs_hint : 64 * np + (1 << 20));
     int64_t total = 0;
     uint64_t *keys = nullptr;
     int32_t *nearf = nullptr;
@@ -316,10 +354,10 @@ static int find_pairs_impl(em_ctx *ctx, int64_t np, const double *x, const doubl
         EM_TRY(buf.alloc(&keys, capacity));
         EM_TRY(buf.alloc(&nearf, capacity));
         EM_CUDA(cudaMemsetAsync(counter, 0, sizeof *counter, st));
-        k_cell_pairs<<<em_grid(nc * 32, 32 * PAIRS_WARPS), 32 * PAIRS_WARPS, 0, st>>>(
-            nc, T, xs, ys, zs, hs, perm, v->gen, v->radius, v->cell_face_off, v->face_vert_off, v->plane, v->edge,
-            v->plane_f, v->edge_f, margin, counter, capacity, keys, nearf);
-        EM_LAUNCHED(ctx);
+        if (cell1 > cell0) {
+            launch_cell_pairs(ctx, P, v, cell0, cell1, counter, capacity, keys, nearf, nullptr);
+            EM_LAUNCHED(ctx);
+        }
         unsigned long long hits = 0;
         EM_CUDA(cudaMemcpyAsync(&hits, counter, sizeof hits, cudaMemcpyDeviceToHost, st));
         EM_CUDA(cudaStreamSynchronize(st));
@@ -337,7 +375,7 @@ static int find_pairs_impl(em_ctx *ctx, int64_t np, const double *x, const doubl
         em_set_error("find_pairs: %lld pairs exceed the 2^31 limit of one pair list", (long long)total);
         return EM_ECAPACITY;
     }
-    ctx->pairs_hint = total + total / 8 + 1024;
+    if (capacity_hint <= 0) ctx->pairs_hint = total + total / 8 + 1024;
     pr->npairs = total;
     if (total) EM_TRY(em_sort_pairs_u64(ctx, keys, nearf, total, 32 + em_nbits((uint64_t)nc)));
     EM_TRY(pr->mem.alloc(&pr->pair_i, total));
@@ -350,16 +388,16 @@ static int find_pairs_impl(em_ctx *ctx, int64_t np, const double *x, const doubl
     return em_build_pair_index(ctx, pr);
 }
 
-EM_EXPORT int find_pairs(em_ctx *ctx, int64_t np, const double *d_x, const double *d_y, const double *d_z,
-                         const double *d_h, const em_voronoi *v, em_pairs **out, int64_t *npairs)
+static int new_pairs(em_ctx *ctx, int64_t np, const double *d_x, const double *d_y, const double *d_z,
+                     const double *d_h, const em_voronoi *v, int64_t cell0, int64_t cell1, int64_t hint,
+                     em_pairs **out, int64_t *npairs)
 {
-    EM_CHECK_ARG(ctx && v && out && np >= 1 && np < INT32_MAX && d_x && d_y && d_z && d_h);
     *out = nullptr;
     em_pairs *pr = new em_pairs(ctx->stream);
     pr->device = ctx->device;
     pr->np = np;
     pr->ncell = v->ncell;
-    int rc = find_pairs_impl(ctx, np, d_x, d_y, d_z, d_h, v, pr);
+    int rc = find_pairs_impl(ctx, np, d_x, d_y, d_z, d_h, v, pr, cell0, cell1, hint);
     if (rc) {
         pr->mem.release();
         delete pr;
@@ -368,4 +406,58 @@ EM_EXPORT int find_pairs(em_ctx *ctx, int64_t np, const double *d_x, const doubl
     if (npairs) *npairs = pr->npairs;
     *out = pr;
     return EM_OK;
+}
+
+EM_EXPORT int find_pairs_plan(em_ctx *ctx, int64_t np, const double *d_x, const double *d_y, const double *d_z,
+                              const double *d_h, const em_voronoi *v, int64_t chunk_capacity, int64_t *h_bounds,
+                              int64_t *h_nchunks, int64_t *h_npairs)
+{
+    EM_CHECK_ARG(ctx && v && np >= 1 && np < INT32_MAX && d_x && d_y && d_z && d_h && chunk_capacity >= 1 &&
+                 h_bounds && h_nchunks);
+    cudaStream_t st = ctx->stream;
+    DevArena tmp(st, true);
+    PairParticles P;
+    EM_TRY(prepare_particles(ctx, tmp, np, d_x, d_y, d_z, d_h, P));
+    const int64_t nc = v->ncell;
+    std::vector<int64_t> cnt(nc > 0 ? nc : 1);
+    if (nc > 0) {
+        int64_t *d_cnt;
+        EM_TRY(tmp.alloc(&d_cnt, nc));
+        launch_cell_pairs(ctx, P, v, 0, nc, nullptr, 0, nullptr, nullptr, d_cnt);
+        EM_LAUNCHED(ctx);
+        EM_CUDA(cudaMemcpyAsync(cnt.data(), d_cnt, nc * sizeof(int64_t), cudaMemcpyDeviceToHost, st));
+        EM_CUDA(cudaStreamSynchronize(st));
+    }
+    // consecutive cells while the count stays within the capacity; a cell
+    // above it is a chunk of its own
+    int64_t nch = 0, acc = 0, total = 0;
+    h_bounds[0] = 0;
+    for (int64_t j = 0; j < nc; ++j) {
+        if (acc > 0 && acc + cnt[j] > chunk_capacity) {
+            h_bounds[++nch] = j;
+            acc = 0;
+        }
+        acc += cnt[j];
+        total += cnt[j];
+    }
+    if (nc > 0) h_bounds[++nch] = nc;
+    *h_nchunks = nch;
+    if (h_npairs) *h_npairs = total;
+    return EM_OK;
+}
+
+EM_EXPORT int find_pairs_cells(em_ctx *ctx, int64_t np, const double *d_x, const double *d_y, const double *d_z,
+                               const double *d_h, const em_voronoi *v, int64_t cell_begin, int64_t cell_end,
+                               int64_t npairs_hint, em_pairs **out, int64_t *npairs)
+{
+    EM_CHECK_ARG(ctx && v && out && np >= 1 && np < INT32_MAX && d_x && d_y && d_z && d_h);
+    EM_CHECK_ARG(cell_begin >= 0 && cell_begin <= cell_end && cell_end <= v->ncell);
+    return new_pairs(ctx, np, d_x, d_y, d_z, d_h, v, cell_begin, cell_end, npairs_hint, out, npairs);
+}
+
+EM_EXPORT int find_pairs(em_ctx *ctx, int64_t np, const double *d_x, const double *d_y, const double *d_z,
+                         const double *d_h, const em_voronoi *v, em_pairs **out, int64_t *npairs)
+{
+    EM_CHECK_ARG(ctx && v && out && np >= 1 && np < INT32_MAX && d_x && d_y && d_z && d_h);
+    return new_pairs(ctx, np, d_x, d_y, d_z, d_h, v, 0, v->ncell, 0, out, npairs);
 }

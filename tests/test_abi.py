@@ -73,3 +73,24 @@ def test_python_defaults_match_library():
     p = api.Params()
     for f in fields(p):
         assert getattr(c, f.name) == getattr(p, f.name), f.name
+
+
+def test_batch_handle_argument_checks():
+    """map_batch_create / add / get / destroy reject bad arguments with
+    EM_EINVAL without touching a GPU."""
+    import ctypes as C
+    from paper_2410_15227_gb300 import _native
+    L = _native.lib()
+    p = _native.EmParams()
+    L.em_params_default(C.byref(p))
+    h = C.c_void_p()
+    assert L.map_batch_create(-1, C.byref(p), 4, C.byref(h)) == _native.EM_EINVAL
+    assert L.map_batch_create(0, C.byref(p), 0, C.byref(h)) == _native.EM_EINVAL
+    assert L.map_batch_create(0, None, 4, C.byref(h)) == _native.EM_EINVAL
+    assert L.map_batch_create(0, C.byref(p), 4, C.byref(h)) == _native.EM_OK
+    rec = _native.EmSnapshot()   # all NULL: an invalid record
+    assert L.map_batch_add(h, C.byref(rec), None) == _native.EM_EINVAL
+    assert L.map_batch_get(h, 0, C.byref(rec)) == _native.EM_EINVAL   # nothing added
+    assert L.map_batch_run(None, 0, None, None, None) == _native.EM_EINVAL
+    assert L.map_batch_destroy(h) == _native.EM_OK
+    assert L.map_batch_destroy(None) == _native.EM_OK

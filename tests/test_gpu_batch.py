@@ -140,3 +140,28 @@ def test_autotune_variants():
     with pytest.raises(Exception):
         api.map_exact(ctx, pr, g["x"], g["y"], g["z"], g["h"], g["m"], vor,
                       api.Params(precision=1, fp32_variant=api.FP32_VARIANTS))
+
+
+def test_batch_handle_equals_map_batch():
+    """The handle form (create, add, run, get) maps what map_batch maps, bit
+    for bit; a second run after more adds maps the enlarged batch; a bad
+    index is rejected."""
+    P = api.Params(r_part=0.05, r_leaf=0.1, theta=0.3, precision=1)
+    snaps = as_dicts(SNAPS[:6])
+    ref, _ = api.map_batch(0, snaps, P, nworkers=3)
+    b = api.Batch(0, P, nworkers=3)
+    assert [b.add(s) for s in snaps[:4]] == [0, 1, 2, 3]
+    assert b.get(2)["status"] == -1   # not run yet
+    res, launches = b.run()
+    assert len(res) == 4 and launches > 0
+    for r, q in zip(res, ref[:4]):
+        assert r["status"] == 0
+        assert (r["npseudo"], r["npairs"], r["nfp64"]) == (q["npseudo"], q["npairs"], q["nfp64"])
+        assert torch.equal(r["rho"], q["rho"])
+        assert torch.equal(torch.nan_to_num(r["f"], nan=-1.0), torch.nan_to_num(q["f"], nan=-1.0))
+    assert b.add(snaps[4]) == 4 and b.add(snaps[5]) == 5
+    res, _ = b.run()
+    for r, q in zip(res, ref):
+        assert torch.equal(r["rho"], q["rho"])
+    with pytest.raises(Exception):
+        b.get(6)
