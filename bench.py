@@ -69,6 +69,10 @@ def parse():
     ap.add_argument("--accuracy-pairs", type=int, default=-1,
                     help="pairs compared with the FP64 path in mixed mode: a random sample of this size, 0 for "
                          "all pairs (default: the workload's sample size, all pairs where none is set)")
+    ap.add_argument("--split", choices=("replicas", "spatial"), default="replicas",
+                    help="N > 1: an independent replica of the problem per rank (weak scaling), or one problem "
+                         "split over the ranks by Morton ranges of its cells with one all-reduce of the "
+                         "inverse mapping's sums (strong scaling)")
     ap.add_argument("--no-autotune", action="store_true",
                     help="mixed mode: keep the FP32 pass's default launch shape instead of tuning it on the workload "
                          "(map_autotune, cached by device and workload in --cache/autotune.json)")
@@ -167,8 +171,20 @@ def run_ours(args, rank, world):
     ctx = api.Context(dev_index)
     dv = lambda a: torch.as_tensor(np.ascontiguousarray(a), dtype=torch.float64, device=device)
     X = [dv(a) for a in (w.x, w.y, w.z, w.m, w.h)]
-    G = [dv(a) for a in (w.gx, w.gy, w.gz)]
-    f_cell = dv(np.random.default_rng([5, 3]).random(w.ngen))
+    f_np = np.random.default_rng([5, 3]).random(w.ngen)
+    spatial = args.split == "spatial"
+    if spatial:
+        # one problem over the ranks: generators in Morton order, this rank's
+        # contiguous range of cells
+        from paper_2410_15227_gb300 import partition
+        order = partition.morton_order(w.gx, w.gy, w.gz, w.box)
+        G = [dv(a[order]) for a in (w.gx, w.gy, w.gz)]
+        f_cell = dv(f_np[order])
+        cell_range = partition.contiguous_ranges(w.ngen, world)[rank]
+    else:
+        G = [dv(a) for a in (w.gx, w.gy, w.gz)]
+        f_cell = dv(f_np)
+        cell_range = None
     src = np.zeros((1, 3))
     P = api.Params(r_part=w.params["r_part"], r_leaf=w.params["r_leaf"], theta=args.theta,
                    h_fact=w.params["h_fact"], h_tol=args.h_tol,
@@ -189,8 +205,12 @@ def run_ours(args, rank, world):
         else:
             tree = ps = None
             g = dict(x=x, y=y, z=z, h=h, m=m)
-        vor = api.build_voronoi(ctx, gx, gy, gz, w.box, P)
-        pr = api.find_pairs(ctx, g["x"], g["y"], g["z"], g["h"], vor)
+        if spatial:
+            vor = api.build_voronoi_cells(ctx, gx, gy, gz, w.box, *cell_range, P)
+            pr = api.find_pairs_cells(ctx, g["x"], g["y"], g["z"], g["h"], vor, *cell_range)
+        else:
+            vor = api.build_voronoi(ctx, gx, gy, gz, w.box, P)
+            pr = api.find_pairs(ctx, g["x"], g["y"], g["z"], g["h"], vor)
         if record:
             e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
             e0.record(stream)
@@ -200,7 +220,19 @@ def run_ours(args, rank, world):
             e1.record(stream)
             map_ms.append((e0, e1))
             kernel_ms.append(ctx.map_times())
-        f, fp = api.map_back(ctx, pr, wts, fc, ps, tree)
+        if spatial:
+            # this rank's part of the inverse mapping's sums, added over the ranks
+            from paper_2410_15227_gb300 import partition
+            num = torch.zeros(g["x"].numel(), dtype=torch.float64, device=device)
+            den = torch.zeros_like(num)
+            api.map_back_sums(ctx, pr, wts, fc, num, den)
+            partition.reduce_sums(num, den)
+            if world > 1 and wsum is not None:   # each particle's weight sum, over every rank's cells
+                torch.distributed.all_reduce(wsum)
+            f = num / den
+            fp = api.inherit(ctx, ps, tree, f) if pseudo else None
+        else:
+            f, fp = api.map_back(ctx, pr, wts, fc, ps, tree)
         return dict(npairs=pr.info()[0], npseudo=ps.info()[0] if pseudo else w.n, nfp64=nf, rho=rho, fp=fp, wsum=wsum,
                     w=wts, pr=pr, g=g, vor=vor)
 
@@ -284,14 +316,16 @@ def run_ours(args, rank, world):
     value = units / (tmax * 1e-3)
     res = dict(metric=METRIC, value=value, unit="pairs/s", n_gpus=world, steps=args.steps,
                warmup=args.warmup, ms_per_step=tmax / args.steps, higher_is_better=True,
-               scaling="weak", vs_baseline=None,
+               scaling="strong" if spatial else "weak", vs_baseline=None,
                dtype="f32+f64" if args.precision == "mixed" else "f64", data="synthetic",
                config={"workload": WORKLOADS[args.workload][0], "particles": w.n, "cells": w.ngen,
                        "pseudo_particles": out["npseudo"] if pseudo else None, "pairs_per_step": out["npairs"],
                        "theta": args.theta, "r_part": w.params["r_part"], "r_leaf": w.params["r_leaf"],
                        "precision": args.precision, "fp64_threshold": args.fp64_threshold, "h_tol": args.h_tol,
                        "fp32_err_ulps": err_ulps(args), "fp32_variant": P.fp32_variant,
-                       "l2": "flushed between steps (258 MiB write)", "parallelism": f"replicas x{world}"},
+                       "l2": "flushed between steps (258 MiB write)",
+                       "parallelism": (f"spatial split x{world} (this rank's cells {cell_range[0]}..{cell_range[1]})"
+                                       if spatial else f"replicas x{world}")},
                map_exact_ms=statistics.mean(t_map), map_exact_pairs_per_s=out["npairs"] / (statistics.mean(t_map) * 1e-3),
                accuracy=acc, gpu_launches=launches, clocks=ck, autotune=tuned)
     k_main = statistics.mean(k[0] for k in kernel_ms)

@@ -206,6 +206,14 @@ int pseudo_destroy(em_pseudo *ps);
  * Coincident generators are rejected with EM_EINVAL. */
 int build_voronoi(em_ctx *ctx, int64_t ngen, const double *d_gx, const double *d_gy, const double *d_gz,
                   const double *h_box, const em_params *p, em_voronoi **out);
+/* The cells [cell_begin, cell_end) only (by generator index; every
+ * generator still bounds them), the others left without faces and with
+ * volume 0: one rank's cells in a spatial split whose ranks take contiguous
+ * ranges of generators sorted in Morton order.  The built cells are the
+ * same, bit for bit, as build_voronoi's. */
+int build_voronoi_cells(em_ctx *ctx, int64_t ngen, const double *d_gx, const double *d_gy, const double *d_gz,
+                        const double *h_box, const em_params *p, int64_t cell_begin, int64_t cell_end,
+                        em_voronoi **out);
 /* Import cells given as faces (e.g. from another grid code):
  *   d_gen: ncell generator positions (xyz interleaved)
  *   d_cell_face_off[ncell+1], d_face_vert_off[nface+1] (int64 CSR offsets)

@@ -63,6 +63,7 @@ SIGNATURES = {
     "pseudo_get": (I32, [P, P] + [P] * 9),
     "pseudo_destroy": (I32, [P]),
     "build_voronoi": (I32, [P, I64, P, P, P, P, PPAR, PP]),
+    "build_voronoi_cells": (I32, [P, I64, P, P, P, P, PPAR, I64, I64, PP]),
     "voronoi_from_cells": (I32, [P, I64, I64, I64, P, P, P, P, P, P, P, PP]),
     "voronoi_info": (I32, [P, PI64, PI64, PI64]),
     "voronoi_centroids": (I32, [P, P, P, P, P]),

@@ -295,6 +295,18 @@ def build_voronoi(ctx: Context, gx, gy, gz, box, params: Params | None = None) -
     return Voronoi(ctx, h)
 
 
+def build_voronoi_cells(ctx: Context, gx, gy, gz, box, cell_begin: int, cell_end: int,
+                        params: Params | None = None) -> Voronoi:
+    """The cells [cell_begin, cell_end) only (one rank of a spatial split)."""
+    n = gx.numel()
+    p = (params or Params()).native()
+    h = C.c_void_p()
+    bp, _keep = _box(box)
+    N.call("build_voronoi_cells", ctx.handle, n, _ptr(gx, f64, n, "gx"), _ptr(gy, f64, n, "gy"),
+           _ptr(gz, f64, n, "gz"), bp, C.byref(p), int(cell_begin), int(cell_end), C.byref(h))
+    return Voronoi(ctx, h)
+
+
 def voronoi_centroids(ctx: Context, vor: Voronoi):
     """Centroid of every cell (Section 2.3, the move of Lloyd's iteration),
     as three device tensors in generator order."""

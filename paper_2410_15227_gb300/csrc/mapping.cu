@@ -1163,7 +1163,8 @@ __global__ void k_cell_density(int64_t ncell, const int64_t *__restrict__ off, c
     for (int64_t k = off[warp] + lane; k < off[warp + 1]; k += 32) s += m[pi[k]] * w[k];
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
-    if (lane == 0) rho[warp] = s / volume[warp];
+    // a cell without pairs has density 0 (also one a range build left without volume)
+    if (lane == 0) rho[warp] = off[warp + 1] > off[warp] ? s / volume[warp] : 0.0;
 }
 
 // u_i = sum_j w_ij (ascending j), one thread per particle

@@ -132,6 +132,7 @@ struct BuildArgs {
     int *status_or;      // [0] OR of the failing cells' status bits, [1] the first failing cell
     int *retry_n;        // cells the first pass left for the second
     int32_t *retry_list;
+    int64_t cell0, cell1;   // the cells built (by generator index); the others are left without faces
 };
 
 // Build the cell of sorted site s in c and write its faces into the cell's
@@ -147,6 +148,17 @@ __device__ void build_one(C &c, const BuildArgs &a, int64_t s, bool first_pass)
         return;
     }
     const double gx = a.xs[s], gy = a.ys[s], gz = a.zs[s];
+    if (j < a.cell0 || j >= a.cell1) {   // outside the range: no faces, no volume
+        if (lane == 0) {
+            a.nface[j] = 0;
+            a.nfv[j] = 0;
+            a.volume[j] = 0.0;
+            a.gen[3 * j] = gx;
+            a.gen[3 * j + 1] = gy;
+            a.gen[3 * j + 2] = gz;
+        }
+        return;
+    }
     const emw::Frame F{a.xs, a.ys, a.zs, a.box, gx, gy, gz};
     int st = emw::wbuild_cell(c, a.T, F, s, a.K, a.margin);
     if (first_pass && st == VS_CAPACITY) {
@@ -275,7 +287,8 @@ __global__ void k_cell_centroid(int64_t ncell, const double *__restrict__ gen, c
 }  // namespace
 
 static int voronoi_impl(em_ctx *ctx, int64_t ngen, const double *gx, const double *gy, const double *gz,
-                        const em_params *p, em_voronoi *v, bool prepare = true)
+                        const em_params *p, em_voronoi *v, bool prepare = true, int64_t cell0 = 0,
+                        int64_t cell1 = -1)
 {
     cudaStream_t st = ctx->stream;
     DevArena tmp(st, true);
@@ -342,6 +355,8 @@ static int voronoi_impl(em_ctx *ctx, int64_t ngen, const double *gx, const doubl
     a.status_or = status;
     a.retry_n = status + 2;
     a.retry_list = retry;
+    a.cell0 = cell0;
+    a.cell1 = cell1 < 0 ? ngen : cell1;
     k_voronoi_build<<<em_grid(ngen, VW), 32 * VW, 0, st>>>(a);
     EM_LAUNCHED(ctx);
     k_voronoi_build_large<<<(unsigned)std::min<int64_t>(em_grid(ngen, VW), 8 * (int64_t)ctx->nsm), 32 * VW, 0, st>>>(a);
@@ -390,17 +405,18 @@ static int voronoi_impl(em_ctx *ctx, int64_t ngen, const double *gx, const doubl
     return prepare ? em_prepare_cells(ctx, v) : EM_OK;
 }
 
-EM_EXPORT int build_voronoi(em_ctx *ctx, int64_t ngen, const double *d_gx, const double *d_gy, const double *d_gz,
-                            const double *h_box, const em_params *p, em_voronoi **out)
+static int new_voronoi(em_ctx *ctx, int64_t ngen, const double *d_gx, const double *d_gy, const double *d_gz,
+                       const double *h_box, const em_params *p, int64_t cell0, int64_t cell1, em_voronoi **out)
 {
     EM_CHECK_ARG(ctx && out && h_box && p && d_gx && d_gy && d_gz);
     EM_CHECK_ARG(ngen >= 1 && ngen < INT32_MAX);
     EM_CHECK_ARG(h_box[1] > h_box[0] && h_box[3] > h_box[2] && h_box[5] > h_box[4]);
+    EM_CHECK_ARG(cell0 >= 0 && cell0 <= cell1 && cell1 <= ngen);
     *out = nullptr;
     em_voronoi *v = new em_voronoi(ctx->stream);
     v->device = ctx->device;
     for (int k = 0; k < 6; ++k) v->box[k] = h_box[k];
-    int rc = voronoi_impl(ctx, ngen, d_gx, d_gy, d_gz, p, v);
+    int rc = voronoi_impl(ctx, ngen, d_gx, d_gy, d_gz, p, v, true, cell0, cell1);
     if (rc) {
         v->mem.release();
         delete v;
@@ -408,6 +424,19 @@ EM_EXPORT int build_voronoi(em_ctx *ctx, int64_t ngen, const double *d_gx, const
     }
     *out = v;
     return EM_OK;
+}
+
+EM_EXPORT int build_voronoi(em_ctx *ctx, int64_t ngen, const double *d_gx, const double *d_gy, const double *d_gz,
+                            const double *h_box, const em_params *p, em_voronoi **out)
+{
+    return new_voronoi(ctx, ngen, d_gx, d_gy, d_gz, h_box, p, 0, ngen, out);
+}
+
+EM_EXPORT int build_voronoi_cells(em_ctx *ctx, int64_t ngen, const double *d_gx, const double *d_gy,
+                                  const double *d_gz, const double *h_box, const em_params *p, int64_t cell_begin,
+                                  int64_t cell_end, em_voronoi **out)
+{
+    return new_voronoi(ctx, ngen, d_gx, d_gy, d_gz, h_box, p, cell_begin, cell_end, out);
 }
 
 EM_EXPORT int voronoi_centroids(em_ctx *ctx, const em_voronoi *v, double *d_cx, double *d_cy, double *d_cz)

@@ -12,6 +12,10 @@ sum_j w_ij f_j and sum_j w_ij, are then added over the ranks with one
 all-reduce each, the only exchange.
 
 Host logic only: which cells and particles a rank takes, and the reduction.
+On the GPU a rank builds its cells with build_voronoi_cells, finds their
+pairs with find_pairs_cells (the tree walk from each cell reaches the
+particles near it, so every rank may pass all particles), maps them, and adds
+the inverse mapping's sums with map_back_sums before reduce_sums.
 """
 from __future__ import annotations
 
@@ -49,6 +53,22 @@ def cell_ranges(gx, gy, gz, box, world: int) -> list[np.ndarray]:
         raise ValueError("world must be at least 1")
     order = np.argsort(morton_keys(gx, gy, gz, box), kind="stable")
     return [np.sort(part) for part in np.array_split(order, world)]
+
+
+def morton_order(gx, gy, gz, box) -> np.ndarray:
+    """The permutation that sorts the generators into Morton order (ties by
+    index); with the generators stored in that order, rank r's cells are the
+    contiguous range contiguous_ranges(n, world)[r]."""
+    return np.argsort(morton_keys(gx, gy, gz, box), kind="stable")
+
+
+def contiguous_ranges(n: int, world: int) -> list[tuple[int, int]]:
+    """[begin, end) of each rank over n items, sizes differing by at most one
+    (the ranges cell_ranges cuts from the Morton order)."""
+    if world < 1:
+        raise ValueError("world must be at least 1")
+    edges = np.cumsum([0] + [len(p) for p in np.array_split(np.arange(n), world)])
+    return [(int(edges[r]), int(edges[r + 1])) for r in range(world)]
 
 
 def cell_boxes(cell_face_off, face_vert_off, verts) -> tuple[np.ndarray, np.ndarray]:

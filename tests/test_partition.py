@@ -153,3 +153,17 @@ def test_reaching_is_the_ball_box_test():
     # several boxes: the union
     lo2, hi2 = np.array([lo, [2.9, 0.0, 0.0]]), np.array([hi, [3.1, 1.0, 1.0]])
     assert list(partition.reaching(x, y, z, h, lo2, hi2)) == [0, 1, 4]
+
+
+def test_morton_order_and_contiguous_ranges():
+    w = _workload()
+    order = partition.morton_order(w.gx, w.gy, w.gz, w.box)
+    keys = partition.morton_keys(w.gx, w.gy, w.gz, w.box)
+    assert np.all(np.diff(keys[order].astype(np.float64)) >= 0)
+    for world in (1, 2, 5):
+        rng = partition.contiguous_ranges(w.ngen, world)
+        parts = partition.cell_ranges(w.gx, w.gy, w.gz, w.box, world)
+        assert rng[0][0] == 0 and rng[-1][1] == w.ngen
+        # rank r's Morton range, in the sorted order, is the generators cell_ranges gives it
+        for (a, b), p in zip(rng, parts):
+            assert np.array_equal(np.sort(order[a:b]), p)
