@@ -896,8 +896,8 @@ __device__ __forceinline__ void mq_push_g(SegQueue &q, int lane, int &cnt, float
                                           bool tilde, emq::ff &acc, float &mag)
 {
     const float c1 = c1x.hi + c1x.lo, c4 = c4x.hi + c4x.lo;
-    const float t1 = c1 < 0.f ? sqrtf(-c1) : 0.f;
-    const float t2 = c4 > 0.f ? sqrtf(c4) : 0.f;
+    const float t1 = c1 < 0.f ? emq::sqrt_nr(-c1) : 0.f;
+    const float t2 = c4 > 0.f ? emq::sqrt_nr(c4) : 0.f;
     const float iA = 1.f / A;
     const int tflag = tilde ? emq::SEG_TILDE : 0;
     // a segment of kernel piece `piece` from tau = ts (s-length len)
@@ -917,7 +917,7 @@ __device__ __forceinline__ void mq_push_g(SegQueue &q, int lane, int &cnt, float
         const float Sa = ts * iA;
         q.ts[sl][lane] = ts;
         q.Sa[sl][lane] = Sa;
-        q.Ca[sl][lane] = sqrtf(fmaf(Sa, Sa, 1.f));
+        q.Ca[sl][lane] = emq::sqrt_nr(fmaf(Sa, Sa, 1.f));
         q.hl[sl][lane] = 0.5f * len / (float)m;
         q.A[sl][lane] = A;
         q.B2[sl][lane] = B2;
@@ -935,11 +935,11 @@ __device__ __forceinline__ void mq_push_g(SegQueue &q, int lane, int &cnt, float
     const float b1 = fminf(ub, t1), a2 = fmaxf(ua, t1), b2 = fminf(ub, t2);
     const bool has1 = b1 > ua, has2 = b2 > a2;
     if (has1 || has2) {
-        const float ra = sqrtf(fmaf(ua, ua, A * A));
+        const float ra = emq::sqrt_nr(fmaf(ua, ua, A * A));
         // s at ua + o minus s at ua, from the offset o
         auto ds = [&](float o) {
             const float b = ua + o;
-            const float rb = sqrtf(fmaf(b, b, A * A));
+            const float rb = emq::sqrt_nr(fmaf(b, b, A * A));
             return asinhf(__fdividef(o * (ua + b), fmaf(b, ra, ua * rb)));
         };
         // offset in s of the end of the quadrature (ub, or Q = 2), and of Q = 1

@@ -60,6 +60,47 @@ namespace emq {
 
 constexpr int kNodeUnroll = EM_NODE_UNROLL;
 
+// e^x - 1 in FP32 for |x| <= 80, within about 1.5 ulp, at about half the
+// issue slots of the library call (the pass evaluates one per quadrature
+// node).  Cody and Waite's reduction x = k ln2 + r, |r| <= ln2/2, with ln2
+// split into a head of 12 significant bits (so k ln2_hi is exact for
+// |k| < 2^12) and the tail; e^r - 1 by its Taylor series to r^7/7!
+// (truncation r^8/8! <= 5.1e-9, a quarter ulp of e^r - 1 at |r| = ln2/2),
+// r + r^2 (1/2 + r (1/6 + ...)) so that the leading term stays exact; then
+// e^x - 1 = 2^k (e^r - 1) + (2^k - 1), one fused multiply-add, 2^k - 1
+// exact for |k| <= 24 and the sum rounded once.
+__device__ __forceinline__ float ex_m1(float x)
+{
+    const float ln2_hi = 0.693145751953125f;           // 2839 / 4096
+    const float ln2_lo = 1.4286068203094172e-06f;      // ln 2 - ln2_hi
+    const float k = rintf(x * 1.4426950408889634f);   // x / ln 2, nearest integer
+    float r = fmaf(-k, ln2_hi, x);
+    r = fmaf(-k, ln2_lo, r);
+    float p = fmaf(r, 1.f / 5040.f, 1.f / 720.f);
+    p = fmaf(r, p, 1.f / 120.f);
+    p = fmaf(r, p, 1.f / 24.f);
+    p = fmaf(r, p, 1.f / 6.f);
+    p = fmaf(r, p, 0.5f);
+    p = fmaf(r * r, p, r);                              // e^r - 1
+    const float s = __int_as_float(((int)k + 127) << 23);   // 2^k
+    return fmaf(s, p, s - 1.f);
+}
+
+// sqrt(x) for x >= 0 within 1 ulp, at about two thirds of the issue slots
+// of the correctly rounded call: x rsqrt(x) and one Newton step on y^2 = x
+// with 1/(2y) taken as rsqrt(x)/2.  A subnormal x is scaled by 2^48 first
+// (its root by 2^-24 after), since the reciprocal square root does not
+// resolve it; 0 gives 0.
+__device__ __forceinline__ float sqrt_nr(float x)
+{
+    const bool tiny = x < 1.17549435e-38f;                // below FP32's normal range
+    const float xs = tiny ? x * 281474976710656.f : x;    // 2^48
+    const float r = rsqrtf(xs);
+    const float y = xs * r;
+    const float s = fmaf(0.5f * r, fmaf(-y, y, xs), y);
+    return x > 0.f ? (tiny ? s * 5.9604644775390625e-8f : s) : 0.f;   // 2^-24
+}
+
 // Gauss-Legendre rules on [-1, 1], by their positive abscissae and weights
 // (the rules are symmetric), in two-node halves: half 0 and half 1 of the
 // 8-point rule, and the 4-point rule.  A "slot" is one half: 4 nodes.
@@ -129,7 +170,7 @@ __device__ __forceinline__ float slot_eval(float off, float hl, int r, float ts,
     for (int i = 0; i < 4; ++i) {
         const float xi = (i >> 1) ? x1 : x0, wi = (i >> 1) ? w1 : w0;
         const float dl = fmaf((i & 1) ? -hl : hl, xi, off);   // offset from the start, > 0
-        const float em = expm1f(dl);
+        const float em = ex_m1(dl);
         const float ei = __fdividef(1.f, 1.f + em);
         const float sh = 0.5f * em * (1.f + ei);    // sinh delta
         const float cm = 0.5f * em * em * ei;       // cosh delta - 1
