@@ -167,42 +167,39 @@ __device__ __forceinline__ void set_vf(float *vf, float &ev, double x, double y,
 
 __device__ __forceinline__ unsigned lanemask_lt() { return (1u << (threadIdx.x & 31)) - 1u; }
 
-__device__ __forceinline__ bool has_edge(const uint8_t *t, uint8_t a, uint8_t b)
-{
-    return (t[0] == a && t[1] == b) || (t[1] == a && t[2] == b) || (t[2] == a && t[0] == b);
-}
-
+// The box as the starting cell: walls 0..5 (x-lo, x-hi, y-lo, y-hi, z-lo,
+// z-hi), and corner i (bits x, y, z of i: 0 for lo, 1 for hi) the meet of
+// walls sx, 2 + sy, 4 + sz, ordered counter-clockwise seen from outside.  The
+// corner across the edge (tri[e], tri[e + 1]) shares those two walls and
+// differs in the axis of the third, tri[e + 2]: i with that axis' bit flipped.
+// Lane w sets wall w, lane i corner i.
 template <class C>
 __device__ void wcell_box(C &c, const Frame &F)
 {
     const int lane = threadIdx.x & 31;
-    if (lane == 0) {
-        const double lo[3] = {F.box[0] - F.gx, F.box[2] - F.gy, F.box[4] - F.gz};
-        const double hi[3] = {F.box[1] - F.gx, F.box[3] - F.gy, F.box[5] - F.gz};
-        c.np = 6;
-        for (int w = 0; w < 6; ++w) {
-            c.sid[w] = -1 - w;
-            double nx, ny, nz, d;
-            wall_plane(F.box, w, F.gx, F.gy, F.gz, nx, ny, nz, d);
-            c.pf[w] = make_float4((float)nx, (float)ny, (float)nz, (float)d);
+    if (lane < 6) {
+        c.sid[lane] = -1 - lane;
+        double nx, ny, nz, d;
+        wall_plane(F.box, lane, F.gx, F.gy, F.gz, nx, ny, nz, d);
+        c.pf[lane] = make_float4((float)nx, (float)ny, (float)nz, (float)d);
+    }
+    if (lane < 8) {
+        const int i = lane;
+        const int sx = i & 1, sy = (i >> 1) & 1, sz = (i >> 2) & 1;
+        const uint8_t X = (uint8_t)sx, Y = (uint8_t)(2 + sy), Z = (uint8_t)(4 + sz);
+        const bool pos = ((sx ? 1 : -1) * (sy ? 1 : -1) * (sz ? 1 : -1)) > 0;
+        const uint8_t t[3] = {X, pos ? Y : Z, pos ? Z : Y};
+        for (int e = 0; e < 3; ++e) {
+            c.tri[0][i][e] = t[e];
+            c.adj[0][i][e] = (uint8_t)(i ^ (1 << (t[(e + 2) % 3] >> 1)));
         }
+        set_vf(c.vf[i], c.ev[i], sx ? F.box[1] - F.gx : F.box[0] - F.gx, sy ? F.box[3] - F.gy : F.box[2] - F.gy,
+               sz ? F.box[5] - F.gz : F.box[4] - F.gz);
+    }
+    if (lane == 0) {
+        c.np = 6;
         c.nt = 8;
         c.cur = 0;
-        for (int i = 0; i < 8; ++i) {
-            int sx = i & 1, sy = (i >> 1) & 1, sz = (i >> 2) & 1;
-            uint8_t X = (uint8_t)sx, Y = (uint8_t)(2 + sy), Z = (uint8_t)(4 + sz);
-            bool pos = ((sx ? 1 : -1) * (sy ? 1 : -1) * (sz ? 1 : -1)) > 0;
-            c.tri[0][i][0] = X;
-            c.tri[0][i][1] = pos ? Y : Z;
-            c.tri[0][i][2] = pos ? Z : Y;
-            set_vf(c.vf[i], c.ev[i], sx ? hi[0] : lo[0], sy ? hi[1] : lo[1], sz ? hi[2] : lo[2]);
-        }
-        for (int i = 0; i < 8; ++i)
-            for (int e = 0; e < 3; ++e) {
-                const uint8_t a = c.tri[0][i][e], b = c.tri[0][i][(e + 1) % 3];
-                for (int s = 0; s < 8; ++s)
-                    if (has_edge(c.tri[0][s], b, a)) c.adj[0][i][e] = (uint8_t)s;
-            }
     }
     __syncwarp();
 }
