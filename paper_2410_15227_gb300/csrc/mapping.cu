@@ -8,6 +8,7 @@
 #include "common.cuh"
 #include "exact.cuh"
 #include "quad32.cuh"
+#include "split.cuh"
 
 using namespace em;
 
@@ -39,11 +40,14 @@ __global__ void k_prepare_faces(int64_t nface, int64_t ncell, const double *__re
     const int64_t v0 = fvo[f], v1 = fvo[f + 1];
     const double c = nx * (verts[3 * v0] - gx) + ny * (verts[3 * v0 + 1] - gy) + nz * (verts[3 * v0 + 2] - gz);
     plane[f] = PlaneD{nx, ny, nz, c};
-    const PlaneF F{(float)nx, (float)ny, (float)nz, (float)c};
+    // hi and low parts: the plane = hi + lo to about 2^-48 relative (float-float)
+    PlaneF F, G;
+    split_df(nx, F.x, G.x);
+    split_df(ny, F.y, G.y);
+    split_df(nz, F.z, G.z);
+    split_df(c, F.w, G.w);
     plane_f[f] = F;
-    // low parts: the plane = hi + lo to about 2^-48 relative (float-float)
-    plane_fl[f] = PlaneF{(float)(nx - (double)F.x), (float)(ny - (double)F.y), (float)(nz - (double)F.z),
-                         (float)(c - (double)F.w)};
+    plane_fl[f] = G;
     cell_of_face[f] = (int32_t)j;
     for (int64_t k = v0; k < v1; ++k) face_of_fv[k] = (int32_t)f;
 }
@@ -75,9 +79,10 @@ __global__ void k_prepare_edges(int64_t nfv, const double *__restrict__ gen, con
     double L = sqrt(ex * ex + ey * ey + ez * ez);
     EdgeD E;
     if (L > 0.0) {
-        ex /= L;
-        ey /= L;
-        ez /= L;
+        const double iL = 1.0 / L;
+        ex *= iL;
+        ey *= iL;
+        ez *= iL;
     }
     E.ex = ex;
     E.ey = ey;
@@ -90,30 +95,20 @@ __global__ void k_prepare_edges(int64_t nfv, const double *__restrict__ gen, con
     E.ce = ex * ax + ey * ay + ez * az;
     E.pad = 0.0;
     edge[k] = E;
-    EdgeF F;
-    F.mx = (float)E.mx;
-    F.my = (float)E.my;
-    F.mz = (float)E.mz;
-    F.cm = (float)E.cm;
-    F.ex = (float)E.ex;
-    F.ey = (float)E.ey;
-    F.ez = (float)E.ez;
-    F.ce = (float)E.ce;
-    F.L = (float)E.L;
+    // hi and low parts: E = hi + lo to about 2^-48 relative (float-float)
+    EdgeF F, G;
+    split_df(E.mx, F.mx, G.mx);
+    split_df(E.my, F.my, G.my);
+    split_df(E.mz, F.mz, G.mz);
+    split_df(E.cm, F.cm, G.cm);
+    split_df(E.ex, F.ex, G.ex);
+    split_df(E.ey, F.ey, G.ey);
+    split_df(E.ez, F.ez, G.ez);
+    split_df(E.ce, F.ce, G.ce);
+    split_df(E.L, F.L, G.L);
     F.pad0 = F.pad1 = F.pad2 = 0.f;
-    edge_f[k] = F;
-    // low parts: E = hi + lo to about 2^-48 relative (float-float)
-    EdgeF G;
-    G.mx = (float)(E.mx - (double)F.mx);
-    G.my = (float)(E.my - (double)F.my);
-    G.mz = (float)(E.mz - (double)F.mz);
-    G.cm = (float)(E.cm - (double)F.cm);
-    G.ex = (float)(E.ex - (double)F.ex);
-    G.ey = (float)(E.ey - (double)F.ey);
-    G.ez = (float)(E.ez - (double)F.ez);
-    G.ce = (float)(E.ce - (double)F.ce);
-    G.L = (float)(E.L - (double)F.L);
     G.pad0 = G.pad1 = G.pad2 = 0.f;
+    edge_f[k] = F;
     edge_fl[k] = G;
     atomicMax(r2bits + j, (unsigned long long)__double_as_longlong(q));
 }

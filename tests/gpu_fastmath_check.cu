@@ -2,8 +2,11 @@
 // emq::ex_m1, emq::sqrt_nr) against a double-precision host reference and
 // against CUDA's expm1f / sqrtf, over dense samples of the ranges the pass
 // uses.  Prints, per function, its name, its largest error in ulps against
-// the reference, the CUDA call's on the same inputs, and the sample count;
-// built and run by tests/test_gpu_fastmath.py.
+// the reference, the CUDA call's on the same inputs, and the sample count.
+// Then the integer double -> float-float split (split.cuh: em::split_df)
+// against the conversions (float)x and (float)(x - (double)(float)x) on the
+// host: its name, the number of results that differ in any bit, and the
+// sample count.  Built and run by tests/test_gpu_fastmath.py.
 #include <algorithm>
 #include <cmath>
 #include <cstdio>
@@ -13,6 +16,7 @@
 #include <cuda_runtime.h>
 
 #include "quad32.cuh"
+#include "split.cuh"
 
 __global__ void eval(int n, const float *x, float *own_e, float *lib_e, float *own_s, float *lib_s)
 {
@@ -23,6 +27,13 @@ __global__ void eval(int n, const float *x, float *own_e, float *lib_e, float *o
     const float a = fabsf(x[i]);
     own_s[i] = emq::sqrt_nr(a);
     lib_s[i] = sqrtf(a);
+}
+
+__global__ void split(int n, const double *x, float *hi, float *lo)
+{
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    em::split_df(x[i], hi[i], lo[i]);
 }
 
 // distance in units in the last place of the FP32 rounding of ref
@@ -67,5 +78,52 @@ int main()
     }
     std::printf("ex_m1 %.3f %.3f %d\n", me, mel, n);
     std::printf("sqrt_nr %.3f %.3f %d\n", ms, msl, n);
+
+    // the split: random significands over binades 2^-90 .. 2^60 (both sides
+    // of the 2^-60 switch), exact ties of the rounding with even and odd
+    // kept parts, the carry to the next binade, and zeros
+    std::vector<double> xd;
+    unsigned long long st = 0x9e3779b97f4a7c15ull;
+    auto next = [&]() {
+        st ^= st << 13;
+        st ^= st >> 7;
+        st ^= st << 17;
+        return st;
+    };
+    for (int i = 0; i < 1 << 20; ++i) {
+        const unsigned long long m = next() & 0xfffffffffffffull;
+        const int e = 1023 - 90 + (int)(next() % 151);
+        const unsigned long long s = next() & 1ull;
+        const unsigned long long u = (s << 63) | ((unsigned long long)e << 52) | m;
+        double v;
+        std::memcpy(&v, &u, 8);
+        xd.push_back(v);
+        unsigned long long t = (u & ~0x1fffffffull) | 0x10000000ull;   // a tie
+        std::memcpy(&v, &t, 8);
+        xd.push_back(v);
+        t = u | 0xfffffe0000000ull | 0x1fffffffull;                   // carry to the next binade
+        std::memcpy(&v, &t, 8);
+        xd.push_back(v);
+    }
+    xd.push_back(0.0);
+    xd.push_back(-0.0);
+    const int nd = (int)xd.size();
+    double *dx;
+    float *dh, *dl;
+    if (cudaMalloc(&dx, nd * sizeof(double)) != cudaSuccess || cudaMalloc(&dh, nd * sizeof(float)) != cudaSuccess ||
+        cudaMalloc(&dl, nd * sizeof(float)) != cudaSuccess)
+        return 3;
+    cudaMemcpy(dx, xd.data(), nd * sizeof(double), cudaMemcpyHostToDevice);
+    split<<<(nd + 255) / 256, 256>>>(nd, dx, dh, dl);
+    std::vector<float> hh(nd), hl(nd);
+    cudaMemcpy(hh.data(), dh, nd * sizeof(float), cudaMemcpyDeviceToHost);
+    cudaMemcpy(hl.data(), dl, nd * sizeof(float), cudaMemcpyDeviceToHost);
+    if (cudaGetLastError() != cudaSuccess) return 4;
+    int bad = 0;
+    for (int i = 0; i < nd; ++i) {
+        const float h = (float)xd[i], l = (float)(xd[i] - (double)h);
+        bad += std::memcmp(&h, &hh[i], 4) != 0 || std::memcmp(&l, &hl[i], 4) != 0;
+    }
+    std::printf("split_df %d 0 %d\n", bad, nd);
     return 0;
 }

@@ -1,7 +1,9 @@
 """The FP32 pass's own e^x - 1 and square root (csrc/quad32.cuh: ex_m1,
 sqrt_nr) against a double-precision reference on dense samples of their
 ranges, beside CUDA's expm1f and sqrtf on the same inputs: ex_m1 within 2
-ulp, sqrt_nr within 1 ulp, subnormals and 0 included."""
+ulp, sqrt_nr within 1 ulp, subnormals and 0 included.  The integer
+double -> float-float split of the derived geometry (csrc/split.cuh) equal,
+bit for bit, to the conversions it replaces, ties and carries included."""
 import os
 import shutil
 import subprocess
@@ -27,3 +29,5 @@ def test_ex_m1_and_sqrt_nr_accuracy():
     assert n > 1_000_000 and own <= 2.0, (own, lib)
     own, lib, n = res["sqrt_nr"]
     assert own <= 1.0, (own, lib)
+    bad, _, n = res["split_df"]
+    assert n > 3_000_000 and bad == 0, bad
