@@ -21,6 +21,7 @@
 
 #include <cstdint>
 
+#include "split.cuh"
 #include "tree_util.cuh"
 #include "voronoi_cell.cuh"
 
@@ -247,7 +248,7 @@ __device__ int wclip(C &c, const Frame &F, double nx, double ny, double nz, doub
     // FP64 meet and value) counts as on the plane and is kept, so that a plane
     // through existing vertices, as in degenerate (lattice) site sets, cuts
     // no sliver off.
-    const float4 P = make_float4((float)nx, (float)ny, (float)nz, (float)d);
+    const float4 P = make_float4(em::f32_rn(nx), em::f32_rn(ny), em::f32_rn(nz), em::f32_rn(d));
     const float nsum = fabsf(P.x) + fabsf(P.y) + fabsf(P.z);
     bool any = false;
     for (int base = 0; base < nt; base += 32) {
@@ -647,7 +648,7 @@ __device__ int gather_cutting(C &c, const em::ChunkTree &T, const double *__rest
             if (hit) {
                 int pos = n + __popc(m & lanemask_lt());
                 if (pos < WCAND) {
-                    cd2[pos] = (float)d2;
+                    cd2[pos] = em::f32_rn(d2);
                     cid[pos] = (int)k;
                 }
             }

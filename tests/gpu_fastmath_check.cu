@@ -29,11 +29,16 @@ __global__ void eval(int n, const float *x, float *own_e, float *lib_e, float *o
     lib_s[i] = sqrtf(a);
 }
 
-__global__ void split(int n, const double *x, float *hi, float *lo)
+__global__ void split(int n, const double *x, float *hi, float *lo, float *h32, double *w64, float *rn)
 {
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n) return;
     em::split_df(x[i], hi[i], lo[i]);
+    const double a = fabs(x[i]);
+    const bool in = a >= 0x1p-100 && a < 0x1p100;   // the range of f32_of
+    h32[i] = in ? em::f32_of(x[i]) : 0.f;
+    w64[i] = in ? em::f64_of(hi[i]) : 0.0;
+    rn[i] = em::f32_rn(x[i]);
 }
 
 // distance in units in the last place of the FP32 rounding of ref
@@ -108,22 +113,34 @@ int main()
     xd.push_back(0.0);
     xd.push_back(-0.0);
     const int nd = (int)xd.size();
-    double *dx;
-    float *dh, *dl;
+    double *dx, *dw;
+    float *dh, *dl, *d32, *drn;
     if (cudaMalloc(&dx, nd * sizeof(double)) != cudaSuccess || cudaMalloc(&dh, nd * sizeof(float)) != cudaSuccess ||
-        cudaMalloc(&dl, nd * sizeof(float)) != cudaSuccess)
+        cudaMalloc(&dl, nd * sizeof(float)) != cudaSuccess || cudaMalloc(&d32, nd * sizeof(float)) != cudaSuccess ||
+        cudaMalloc(&dw, nd * sizeof(double)) != cudaSuccess || cudaMalloc(&drn, nd * sizeof(float)) != cudaSuccess)
         return 3;
     cudaMemcpy(dx, xd.data(), nd * sizeof(double), cudaMemcpyHostToDevice);
-    split<<<(nd + 255) / 256, 256>>>(nd, dx, dh, dl);
-    std::vector<float> hh(nd), hl(nd);
+    split<<<(nd + 255) / 256, 256>>>(nd, dx, dh, dl, d32, dw, drn);
+    std::vector<float> hh(nd), hl(nd), h32(nd), hrn(nd);
+    std::vector<double> w64(nd);
     cudaMemcpy(hh.data(), dh, nd * sizeof(float), cudaMemcpyDeviceToHost);
     cudaMemcpy(hl.data(), dl, nd * sizeof(float), cudaMemcpyDeviceToHost);
+    cudaMemcpy(h32.data(), d32, nd * sizeof(float), cudaMemcpyDeviceToHost);
+    cudaMemcpy(w64.data(), dw, nd * sizeof(double), cudaMemcpyDeviceToHost);
+    cudaMemcpy(hrn.data(), drn, nd * sizeof(float), cudaMemcpyDeviceToHost);
     if (cudaGetLastError() != cudaSuccess) return 4;
-    int bad = 0;
+    int bad = 0, bad2 = 0, n2 = 0;
     for (int i = 0; i < nd; ++i) {
         const float h = (float)xd[i], l = (float)(xd[i] - (double)h);
-        bad += std::memcmp(&h, &hh[i], 4) != 0 || std::memcmp(&l, &hl[i], 4) != 0;
+        bad += std::memcmp(&h, &hh[i], 4) != 0 || std::memcmp(&l, &hl[i], 4) != 0 || std::memcmp(&h, &hrn[i], 4) != 0;
+        const double a = std::fabs(xd[i]);
+        if (a >= 0x1p-100 && a < 0x1p100) {
+            const double wd = (double)h;
+            bad2 += std::memcmp(&h, &h32[i], 4) != 0 || std::memcmp(&wd, &w64[i], 8) != 0;
+            ++n2;
+        }
     }
     std::printf("split_df %d 0 %d\n", bad, nd);
+    std::printf("f32_f64_of %d 0 %d\n", bad2, n2);
     return 0;
 }

@@ -2,8 +2,9 @@
 sqrt_nr) against a double-precision reference on dense samples of their
 ranges, beside CUDA's expm1f and sqrtf on the same inputs: ex_m1 within 2
 ulp, sqrt_nr within 1 ulp, subnormals and 0 included.  The integer
-double -> float-float split of the derived geometry (csrc/split.cuh) equal,
-bit for bit, to the conversions it replaces, ties and carries included."""
+double -> float-float split of the derived geometry and the h-solver's
+conversions to and from float (csrc/split.cuh) equal, bit for bit, to the
+conversions they replace, ties and carries included."""
 import os
 import shutil
 import subprocess
@@ -31,3 +32,5 @@ def test_ex_m1_and_sqrt_nr_accuracy():
     assert own <= 1.0, (own, lib)
     bad, _, n = res["split_df"]
     assert n > 3_000_000 and bad == 0, bad
+    bad, _, n = res["f32_f64_of"]
+    assert n > 2_000_000 and bad == 0, bad
