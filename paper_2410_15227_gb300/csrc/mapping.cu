@@ -998,10 +998,11 @@ __global__ void __launch_bounds__(32 * WARPS, MINB) k_map_fp32(int64_t npairs, c
         rad = radius[j];
     }
     const double ih = 1.0 / hh;
-    const float rxf = (float)rx, ryf = (float)ry, rzf = (float)rz, ihf = (float)ih;
-    // float-float copies of r = p - g and 1/h for the plane and edge geometry
+    // float-float copies of r = p - g and 1/h for the plane and edge geometry,
+    // and their FP32 roundings
     const emq::ff rxx = emq::ff_from_double(rx), ryy = emq::ff_from_double(ry), rzz = emq::ff_from_double(rz);
     const emq::ff ihh = emq::ff_from_double(ih);
+    const float rxf = rxx.hi, ryf = ryy.hi, rzf = rzz.hi, ihf = ihh.hi;
     // signed distance c - n.r of P from face g's plane (positive inside), in
     // float-float; the inside test and the faces' orientations below both
     // take their signs from this one value

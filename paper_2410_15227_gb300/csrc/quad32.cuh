@@ -52,6 +52,8 @@
 
 #include <cuda_runtime.h>
 
+#include "split.cuh"
+
 #ifndef EM_NODE_UNROLL
 #define EM_NODE_UNROLL 2   // unroll of the 8-node loop (build-time tuning knob)
 #endif
@@ -235,10 +237,13 @@ __device__ __forceinline__ ff ff_mul(ff x, ff y)
     const ff p = ff_two_prod(x.hi, y.hi);
     return ff_two_sum(p.hi, p.lo + fmaf(x.hi, y.lo, x.lo * y.hi));
 }
+// v as hi = (float)v and lo = (float)(v - hi), formed on the bits
+// (split.cuh): the conversions would issue at the FP64 rate
 __device__ __forceinline__ ff ff_from_double(double v)
 {
-    const float h = (float)v;
-    return ff{h, (float)(v - (double)h)};
+    ff r;
+    em::split_df(v, r.hi, r.lo);
+    return r;
 }
 // c - (mx rx + my ry + mz rz), every operand float-float
 __device__ __forceinline__ ff ff_offset_dot(float ch, float cl, float mxh, float mxl, float myh, float myl, float mzh,
