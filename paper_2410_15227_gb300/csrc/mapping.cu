@@ -1031,7 +1031,12 @@ __global__ void __launch_bounds__(32 * WARPS, MINB) k_map_fp32(int64_t npairs, c
     const int nface = valid ? (int)(f1 - f) : 0;
     // faces and edges in lockstep across the warp: consecutive pairs mostly
     // share their cell, so the per-face geometry runs with the lanes converged
-    for (int fi = 0; __any_sync(FULL_MASK, fi < nface); ++fi) {
+    // One pass more than the warp has faces, with one empty edge, evaluates
+    // what is left: the flush has a single call site, so that a slot's result
+    // cannot depend on which copy of the code (the compiler may round two
+    // copies differently) evaluated it, that is on the other pairs of the warp.
+    for (int fi = 0;; ++fi) {
+        const bool last = !__any_sync(FULL_MASK, fi < nface);
         int64_t e0 = 0;
         int ne = 0;
         FaceState fs{};
@@ -1074,7 +1079,7 @@ __global__ void __launch_bounds__(32 * WARPS, MINB) k_map_fp32(int64_t npairs, c
                 }
             }
         }
-        for (int ei = 0; __any_sync(FULL_MASK, ei < ne); ++ei) {
+        for (int ei = 0; last ? ei == 0 : __any_sync(FULL_MASK, ei < ne); ++ei) {
             if (ei < ne) {
                 // edge geometry in float-float (see quad32.cuh): A, T0, T1 and
                 // B^2 - 1, 4 - B^2, A^2 - rho^2 each rounded once to FP32
@@ -1112,13 +1117,13 @@ __global__ void __launch_bounds__(32 * WARPS, MINB) k_map_fp32(int64_t npairs, c
                 }
             }
             // an edge queues at most four segments
-            if (__any_sync(FULL_MASK, cnt > MQ_SLOTS - 4)) {
+            if (__any_sync(FULL_MASK, cnt > (last ? 0 : MQ_SLOTS - 4))) {
                 mq_flush(q, lane, cnt, acc, mag);
                 cnt = 0;
             }
         }
+        if (last) break;
     }
-    if (__any_sync(FULL_MASK, cnt > 0)) mq_flush(q, lane, cnt, acc, mag);
     bool flag = false;
     if (valid) {
         // the integrals were summed with their signs: w = sum (full kernel) or
