@@ -538,7 +538,7 @@ FP64_FLOPS_PAIR = 30
 # DRAM traffic of one k_map_fp32 launch per pair (ncu, dram__bytes_read.sum +
 # dram__bytes_write.sum over the pairs of the launch), per workload, from a
 # capture of the current kernel (profiles/k_map_fp32_dram_pseudo_1e6.md)
-TRAFFIC_PER_PAIR = {"pseudo_1e6": 108.97}
+TRAFFIC_PER_PAIR = {"pseudo_1e6": 108.84}
 
 
 def nominal_peaks(sm_count, mhz):
