@@ -15,7 +15,6 @@
 #include <vector>
 
 #include "common.cuh"
-#include "split.cuh"
 #include "tree_util.cuh"
 
 namespace {
@@ -165,9 +164,7 @@ __global__ void __launch_bounds__(32 * PAIRS_WARPS)
         if (act) {
             const double rx = xs[k] - gx, ry = ys[k] - gy, rz = zs[k] - gz;
             const double h2 = 2.0 * hs[k];
-            // the FP32 copies on the bits (split.cuh): the conversions would
-            // issue at the FP64 rate
-            const float rxf = em::f32_rn(rx), ryf = em::f32_rn(ry), rzf = em::f32_rn(rz), h2f = em::f32_rn(h2);
+            const float rxf = (float)rx, ryf = (float)ry, rzf = (float)rz, h2f = (float)h2;
             const float rr = sqrtf(rxf * rxf + ryf * ryf + rzf * rzf);
             const float band = 1e-5f * (Rf + rr + h2f);
             // the cell lies inside the ball of radius R_j around g: dist >= |r| - R_j
@@ -206,7 +203,7 @@ __global__ void __launch_bounds__(32 * PAIRS_WARPS)
             const float4 pk = T.pts[k];
             const float ex = pk.x - gxf, ey = pk.y - gyf, ez = pk.z - gzf;
             const float d = sqrtf(ex * ex + ey * ey + ez * ez);
-            const float h2f = 2.f * em::f32_rn(hs[k]);
+            const float h2f = 2.f * (float)hs[k];
             cand = d < Rf + h2f + 1e-5f * (gscale + Rf + d + h2f);
         }
         const unsigned cm = __ballot_sync(0xffffffffu, cand);
