@@ -601,15 +601,26 @@ def run_e2e(args, w, step, device):
     bi = sum(t.numel() * t.element_size() for t in host)
     stream = torch.cuda.current_stream(device)
     reps = max(1, min(args.steps, 3))
+    # the results land in pinned host buffers, allocated once like the inputs;
+    # the copies run on the library's stream (torch's current one), after the
+    # step's kernels, and all of them finish inside the timed region
+    res_h = {"rho": torch.empty(w.ngen, dtype=torch.float64, pin_memory=True),
+             "fp": torch.empty(w.n, dtype=torch.float64, pin_memory=True)}
     torch.cuda.synchronize()
     t0 = time.perf_counter()
     npairs, bo = 0, 0
     for _ in range(reps):
         dev_in = [t.to(device, non_blocking=True) for t in host]
         out = step(*dev_in)
-        rho_h = out["rho"].to("cpu", non_blocking=False)
-        fp_h = out["fp"].to("cpu", non_blocking=False)
-        bo = rho_h.numel() * 8 + fp_h.numel() * 8
+        bo = 0
+        for key in ("rho", "fp"):
+            d = out[key]
+            if d is None:
+                continue
+            if key not in res_h or res_h[key].shape != d.shape:
+                res_h[key] = torch.empty(d.shape, dtype=d.dtype, pin_memory=True)
+            res_h[key].copy_(d, non_blocking=True)
+            bo += d.numel() * d.element_size()
         npairs += out["npairs"]
     stream.synchronize()
     dt = time.perf_counter() - t0

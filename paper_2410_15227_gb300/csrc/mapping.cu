@@ -1169,13 +1169,50 @@ __global__ void k_cell_density(int64_t ncell, const int64_t *__restrict__ off, c
 }
 
 // u_i = sum_j w_ij (ascending j), one thread per particle
+// Sums over a particle's pairs [k0, k1) of the (i, j)-ordered transpose, in
+// ascending j, each product and each sum rounded on its own (no fused
+// multiply-add): den = sum w, and with f given, num = sum w f_j.  The loads of
+// PB pairs are issued before their sums, so that a thread has PB gathers in
+// flight instead of one dependent chain at a time; the order of the sums is
+// unchanged.
+constexpr int PB = 8;
+template <bool WITH_F>
+__device__ __forceinline__ void pair_sums(int64_t k0, int64_t k1, const int32_t *__restrict__ idx,
+                                          const int32_t *__restrict__ pj, const double *__restrict__ w,
+                                          const double *__restrict__ f, double &num, double &den)
+{
+    int64_t k = k0;
+    for (; k + PB <= k1; k += PB) {
+        int32_t q[PB];
+        double wq[PB], fq[PB];
+#pragma unroll
+        for (int u = 0; u < PB; ++u) q[u] = __ldg(idx + k + u);
+#pragma unroll
+        for (int u = 0; u < PB; ++u) {
+            wq[u] = __ldg(w + q[u]);
+            fq[u] = WITH_F ? __ldg(f + __ldg(pj + q[u])) : 0.0;
+        }
+#pragma unroll
+        for (int u = 0; u < PB; ++u) {
+            if (WITH_F) num = __dadd_rn(num, __dmul_rn(wq[u], fq[u]));
+            den = __dadd_rn(den, wq[u]);
+        }
+    }
+    for (; k < k1; ++k) {
+        const int32_t q = idx[k];
+        const double wq = w[q];
+        if (WITH_F) num = __dadd_rn(num, __dmul_rn(wq, f[pj[q]]));
+        den = __dadd_rn(den, wq);
+    }
+}
+
 __global__ void k_particle_wsum(int64_t np, const int64_t *__restrict__ off, const int32_t *__restrict__ idx,
                                 const double *__restrict__ w, double *__restrict__ u)
 {
     int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     if (i >= np) return;
-    double s = 0.0;
-    for (int64_t k = off[i]; k < off[i + 1]; ++k) s += w[idx[k]];
+    double num = 0.0, s = 0.0;
+    pair_sums<false>(off[i], off[i + 1], idx, nullptr, w, nullptr, num, s);
     u[i] = s;
 }
 
@@ -1431,16 +1468,11 @@ __global__ void k_map_back(int64_t np, const int64_t *__restrict__ off, const in
 {
     int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     if (i >= np) return;
-    // ascending j, each product and each sum rounded on its own (no fused
-    // multiply-add), so that equal weights give bit-identical results on any
-    // implementation that sums in the same order
+    // ascending j, each product and each sum rounded on its own (pair_sums),
+    // so that equal weights give bit-identical results on any implementation
+    // that sums in the same order
     double num = 0.0, den = 0.0;
-    for (int64_t k = off[i]; k < off[i + 1]; ++k) {
-        const int32_t q = idx[k];
-        const double wq = w[q];
-        num = __dadd_rn(num, __dmul_rn(wq, f_cell[pj[q]]));
-        den = __dadd_rn(den, wq);
-    }
+    pair_sums<true>(off[i], off[i + 1], idx, pj, w, f_cell, num, den);
     f_out[i] = num / den;
 }
 
@@ -1464,12 +1496,7 @@ __global__ void k_map_back_sums(int64_t np, const int64_t *__restrict__ off, con
     int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     if (i >= np) return;
     double a = 0.0, b = 0.0;
-    for (int64_t k = off[i]; k < off[i + 1]; ++k) {
-        const int32_t q = idx[k];
-        const double wq = w[q];
-        a = __dadd_rn(a, __dmul_rn(wq, f_cell[pj[q]]));
-        b = __dadd_rn(b, wq);
-    }
+    pair_sums<true>(off[i], off[i + 1], idx, pj, w, f_cell, a, b);
     num[i] = __dadd_rn(num[i], a);
     den[i] = __dadd_rn(den[i], b);
 }
