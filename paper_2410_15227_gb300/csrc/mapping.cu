@@ -724,21 +724,29 @@ static_assert(EM_G8_MAXLEN_FAR >= 0.5 && EM_G8_MAXLEN_FAR <= 2.0, "sub-pieces pe
 #define EM_GL4_MAXLEN 0.125   // longest segment (in s) integrated with 4 points
 #endif
 #ifndef EM_MQ_MINB
-#define EM_MQ_MINB 0   // minimum resident blocks per SM asked of the compiler (0: none)
+// minimum resident blocks per SM asked of the compiler (0: none): 12 two-warp
+// blocks, 24 warps, is what the shared memory of 12 queues allows (18.2 KB a
+// block), and caps the registers at 80 without spills
+#define EM_MQ_MINB 12
 #endif
 constexpr int MQ_SLOTS = EM_MQ_SLOTS;   // segments a lane holds between evaluations (>= 5)
 constexpr int MQ_WARPS = EM_MQ_WARPS;   // warps per block
-constexpr int MQ_CHUNK = 128;           // sub-piece results a warp holds between accumulations
+constexpr int MQ_CHUNK = 64;            // sub-piece results a warp holds between accumulations
 static_assert(MQ_SLOTS >= 5, "an edge queues up to four segments");
 static_assert(MQ_CHUNK % 32 == 0, "whole rounds of the warp");
+// a lane holds at most MQ_SLOTS segments of at most 2 x 141 slots each (m <= 141)
+constexpr int MQ_NOSLOT = 4095;
+static_assert(MQ_SLOTS * 282 < MQ_NOSLOT, "slot indices fit in 12 bits");
 constexpr unsigned FULL_MASK = 0xffffffffu;
 
 struct SegQueue {
-    float ts[MQ_SLOTS][32], Sa[MQ_SLOTS][32], Ca[MQ_SLOTS][32], hl[MQ_SLOTS][32], A[MQ_SLOTS][32];
+    float ts[MQ_SLOTS][32], hl[MQ_SLOTS][32], A[MQ_SLOTS][32];
     float B2[MQ_SLOTS][32], c4s[MQ_SLOTS][32], es[MQ_SLOTS][32], Rr[MQ_SLOTS][32], vv[MQ_SLOTS][32];
     float add[MQ_SLOTS][32], scale[MQ_SLOTS][32];
+    // m | piece1 | tilde | gl4 (quad32.cuh) in the low 16 bits; during a
+    // flush, the index of the segment's first 4-node slot among its lane's
+    // in bits 16-27 (MQ_NOSLOT for an empty row)
     int meta[MQ_SLOTS][32];
-    int first[MQ_SLOTS][32];            // index of a segment's first 4-node slot among its lane's (INT_MAX if empty)
     float vhi[MQ_CHUNK], vlo[MQ_CHUNK];   // scale * integral of each evaluated slot (float-float)
     int pre[33];
 };
@@ -759,11 +767,9 @@ __device__ __forceinline__ void mq_flush(SegQueue &q, int lane, int cnt, emq::ff
     int M = 0;
 #pragma unroll
     for (int sl = 0; sl < MQ_SLOTS; ++sl) {
-        q.first[sl][lane] = sl < cnt ? M : INT_MAX;
-        if (sl < cnt) {
-            const int mt = q.meta[sl][lane];
-            M += (mt & emq::SEG_GL4) ? (mt & 255) : 2 * (mt & 255);   // 4-point: 1 slot, 8-point: 2 per sub-piece
-        }
+        const int mt = q.meta[sl][lane] & 0xffff;
+        q.meta[sl][lane] = mt | ((sl < cnt ? M : MQ_NOSLOT) << 16);
+        if (sl < cnt) M += (mt & emq::SEG_GL4) ? (mt & 255) : 2 * (mt & 255);   // 4-point: 1 slot, 8-point: 2 per sub-piece
     }
     int x = M;
 #pragma unroll
@@ -789,15 +795,22 @@ __device__ __forceinline__ void mq_flush(SegQueue &q, int lane, int cnt, emq::ff
             const int r = t - q.pre[lo];
             int sl = 0;
 #pragma unroll
-            for (int k = 1; k < MQ_SLOTS; ++k) sl += q.first[k][lo] <= r ? 1 : 0;
-            const int rr = r - q.first[sl][lo];
-            const int mt = q.meta[sl][lo];
+            for (int k = 1; k < MQ_SLOTS; ++k) sl += (q.meta[k][lo] >> 16) <= r ? 1 : 0;
+            const int mw = q.meta[sl][lo];
+            const int rr = r - (mw >> 16);
+            const int mt = mw & 0xffff;
             const bool gl4 = (mt & emq::SEG_GL4) != 0;
             const int p = gl4 ? rr : rr >> 1;           // the sub-piece
             const int half = gl4 ? 2 : (rr & 1);        // which 4 nodes of its rule
             const float hl = q.hl[sl][lo];
-            const float val = emq::slot_eval((2.f * (float)p + 1.f) * hl, hl, half, q.ts[sl][lo], q.Sa[sl][lo],
-                                             q.Ca[sl][lo], q.A[sl][lo], q.B2[sl][lo], q.c4s[sl][lo], q.es[sl][lo],
+            // sinh and cosh of s at the segment's start, ts / A and
+            // sqrt(1 + (ts / A)^2) (not stored, which keeps the queue small
+            // enough for more warps per SM)
+            const float ts = q.ts[sl][lo], A = q.A[sl][lo];
+            const float Sa = ts * __frcp_rn(A);
+            const float Ca = emq::sqrt_nr(fmaf(Sa, Sa, 1.f));
+            const float val = emq::slot_eval((2.f * (float)p + 1.f) * hl, hl, half, ts, Sa, Ca, A, q.B2[sl][lo],
+                                             q.c4s[sl][lo], q.es[sl][lo],
                                              q.Rr[sl][lo], q.vv[sl][lo], q.add[sl][lo], mt);
             const emq::ff v = emq::ff_two_prod(q.scale[sl][lo], val);
             q.vhi[t - c0] = v.hi;
@@ -893,7 +906,6 @@ __device__ __forceinline__ void mq_push_g(SegQueue &q, int lane, int &cnt, float
     const float c1 = c1x.hi + c1x.lo, c4 = c4x.hi + c4x.lo;
     const float t1 = c1 < 0.f ? emq::sqrt_nr(-c1) : 0.f;
     const float t2 = c4 > 0.f ? emq::sqrt_nr(c4) : 0.f;
-    const float iA = 1.f / A;
     const int tflag = tilde ? emq::SEG_TILDE : 0;
     // a segment of kernel piece `piece` from tau = ts (s-length len)
     auto push = [&](int piece, float ts, float len) {
@@ -909,10 +921,7 @@ __device__ __forceinline__ void mq_push_g(SegQueue &q, int lane, int &cnt, float
         const emq::ff ts2 = emq::ff_two_prod(ts, ts);
         const emq::ff es = emq::ff_add(ref1 ? c1x : ccx, ts2);
         const emq::ff c4s = emq::ff_add(c4x, emq::ff_neg(ts2));
-        const float Sa = ts * iA;
         q.ts[sl][lane] = ts;
-        q.Sa[sl][lane] = Sa;
-        q.Ca[sl][lane] = emq::sqrt_nr(fmaf(Sa, Sa, 1.f));
         q.hl[sl][lane] = 0.5f * len / (float)m;
         q.A[sl][lane] = A;
         q.B2[sl][lane] = B2;
@@ -958,10 +967,11 @@ __device__ __forceinline__ void mq_push_g(SegQueue &q, int lane, int &cnt, float
 
 // Launch shapes of the FP32 pass (em_params.fp32_variant, map_autotune):
 // warps per block and the minimum resident blocks per SM asked of the
-// compiler (0: none).  Variant 0 is the default shape.
+// compiler (0: none).  Variant 0 is the default shape; the others trade
+// registers (no minimum: 92-94) against warps per SM.
 constexpr int MQ_NVARIANT = 4;
 constexpr int MQ_VARIANT_WARPS[MQ_NVARIANT] = {MQ_WARPS, 1, 4, 2};
-constexpr int MQ_VARIANT_MINB[MQ_NVARIANT] = {EM_MQ_MINB, 0, 0, 12};
+constexpr int MQ_VARIANT_MINB[MQ_NVARIANT] = {EM_MQ_MINB, 0, 6, 0};
 
 template <int WARPS, int MINB>
 __global__ void __launch_bounds__(32 * WARPS, MINB) k_map_fp32(int64_t npairs, const int32_t *__restrict__ pi,
