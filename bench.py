@@ -524,21 +524,23 @@ WORK = {
 #    Newton step, Q^2 - R^2 from the offset: 33; the kernel piece's integrand
 #    about 20) and 5 SFU operations (expm1, the reciprocals of 1 + expm1,
 #    Q + R and cosh, and rsqrt for Q);
-#  - per edge of a face within reach 190 FP32 flops of float-float geometry
+#  - per edge of a face within reach 185 FP32 flops of float-float geometry
 #    (two offset dot products, four products, four sums) and segment set-up
-#    (lengths in s from the offsets, the start's sinh, cosh and differences);
+#    (lengths in s from the offsets, the differences at the start);
 #  - per face 60 (float-float plane distance and, for faces within reach,
 #    the face constants), and 18 per edge of a face within reach for the FP32
 #    distance to the polygon;
-#  - per 4-node slot 14 for the float-float accumulation;
+#  - per 4-node slot 14 for the float-float accumulation and 6 for the
+#    segment start's sinh and cosh (ts / A, and sqrt(1 + (ts/A)^2) by rsqrt
+#    and a Newton step), formed where the slot is evaluated;
 #  - per pair about 30 FP64 flops (r = x - g, 1/h, the final sums).
 FP32_FLOPS_NODE, SFU_OPS_NODE = 53, 5
-FP32_FLOPS_EDGE, FP32_FLOPS_FACE, FP32_FLOPS_POLY_EDGE, FP32_FLOPS_SLOT = 190, 60, 18, 14
+FP32_FLOPS_EDGE, FP32_FLOPS_FACE, FP32_FLOPS_POLY_EDGE, FP32_FLOPS_SLOT = 185, 60, 18, 20
 FP64_FLOPS_PAIR = 30
 # DRAM traffic of one k_map_fp32 launch per pair (ncu, dram__bytes_read.sum +
 # dram__bytes_write.sum over the pairs of the launch), per workload, from a
 # capture of the current kernel (profiles/k_map_fp32_dram_pseudo_1e6.md)
-TRAFFIC_PER_PAIR = {"pseudo_1e6": 108.84}
+TRAFFIC_PER_PAIR = {"pseudo_1e6": 108.94}
 
 
 def nominal_peaks(sm_count, mhz):
