@@ -115,6 +115,21 @@ def test_batch_tuned_equals_serial_with_its_variant():
         assert torch.equal(torch.nan_to_num(r["f"], nan=-1.0), torch.nan_to_num(f, nan=-1.0))
 
 
+@pytest.mark.parametrize("variant", range(api.FP32_VARIANTS))
+def test_every_launch_shape_independent_of_warp_neighbours(variant):
+    """In every launch shape of the FP32 pass, a pair's weight does not depend
+    on which pairs share its warp: the batch, where each snapshot's pairs sit
+    at other offsets of the concatenated list, equals the snapshots mapped
+    one at a time with that shape, bit for bit."""
+    P = api.Params(r_part=0.05, r_leaf=0.1, theta=0.3, precision=1, fp32_variant=variant)
+    res, _ = api.map_batch(0, as_dicts(SNAPS[:6], with_f=False), P, nworkers=2)
+    ctx = api.Context(0)
+    for (w, fc), r in zip(SNAPS[:6], res):
+        rho, _, _, npairs, nf = serial(ctx, w, fc, P)
+        assert r["status"] == 0 and (r["npairs"], r["nfp64"]) == (npairs, nf)
+        assert torch.equal(r["rho"], rho)
+
+
 def test_autotune_variants():
     """Every launch shape of the FP32 pass is deterministic (the same bits on
     a second call) and within the mixed mode's tolerance of the default shape
