@@ -688,12 +688,15 @@ __global__ void __launch_bounds__(32 * FW_WARPS) k_map_fp64(
 //
 // Each edge yields up to four quadrature segments, which the lane appends to
 // its column of a per-warp queue in shared memory; whenever a lane's column
-// may overflow, the warp evaluates all queued segments together, one 8-node
-// sub-piece per lane, so that the node loop runs with the warp converged
-// whatever the pairs' geometry.  Each lane then adds its own segments'
-// results in a fixed order, which keeps the result bit-reproducible.  The estimated error 8 eps times the sum of the
-// magnitudes of the non-negative pieces flags the pair for the FP64 pass when
-// it exceeds max(tol |w|, 1e-14) (relative accuracy tol for every weight
+// may overflow, the warp evaluates all queued segments together, one 4-node
+// slot (a 4-point segment, or half of an 8-point sub-piece) per lane, so that
+// the node loop runs with the warp converged whatever the pairs' geometry.
+// Each lane then adds its own segments' results in a fixed order, which keeps
+// the result bit-reproducible.  The queue is small (9.1 KB per warp) so that
+// 12 two-warp blocks fit an SM: the pass is bound by instruction issue, and
+// the warps hide its latencies.  The estimated error 8 eps times the sum of
+// the magnitudes of the non-negative pieces flags the pair for the FP64 pass
+// when it exceeds max(tol |w|, 1e-14) (relative accuracy tol for every weight
 // above 1e-14 / tol, absolute 1e-14 below); so does a face plane through P.
 namespace {
 
