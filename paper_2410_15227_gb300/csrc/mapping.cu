@@ -527,7 +527,7 @@ __device__ __forceinline__ void fp64_pairs_warp(int64_t n, const int32_t *__rest
                 fSg[wi][f] = sd > 0.0 ? 1.f : -1.f;
                 if (keep) cnt = (int)(fvo[f0 + f + 1] - fvo[f0 + f]);
             }
-            int xs = cnt;   // inclusive scan of the edge counts over this round
+            int xs = cnt;   // inclusive scan of the edge counts over these 32 faces
 #pragma unroll
             for (int o = 1; o < 32; o <<= 1) {
                 const int y = __shfl_up_sync(0xffffffffu, xs, o);
