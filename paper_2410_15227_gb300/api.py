@@ -129,6 +129,10 @@ class _Handle:
 
 
 class Tree(_Handle):
+    """The octree of build_tree (Section 2.2.1): info() gives (particles,
+    nodes, depth); get() copies out the Morton permutation and, per node,
+    label, level, parent, first particle, count, first child, children, mass,
+    centre of mass and size."""
     _destroy = "tree_destroy"
 
     def info(self):
@@ -151,6 +155,11 @@ class Tree(_Handle):
 
 
 class Pseudo(_Handle):
+    """The pseudo-particles of make_pseudo_particles (Section 2.4): info()
+    gives (count, the four solver status counts); get() copies out position,
+    h, mass, origin (the node label, > 0, or -(particle index + 1) for an
+    extracted particle), the Morton range of the
+    constituents (first, count) and the solver status."""
     _destroy = "pseudo_destroy"
 
     def info(self):
@@ -171,6 +180,10 @@ class Pseudo(_Handle):
 
 
 class Voronoi(_Handle):
+    """The cells of build_voronoi (Section 2.3), clipped to the box: info()
+    gives (cells, faces, face-vertices); get() copies out the CSR offsets,
+    vertices (counter-clockwise seen from outside), outward normals,
+    neighbours (negative for a box face) and volumes."""
     _destroy = "voronoi_destroy"
 
     def info(self):
@@ -192,6 +205,9 @@ class Voronoi(_Handle):
 
 
 class Pairs(_Handle):
+    """A particle-cell pair list sorted by (cell, particle): info() gives
+    (pairs, particles, cells); get() copies out pair_i, pair_j, the near
+    flags (within 1e-9 h of the 2h boundary) and the cells' pair offsets."""
     _destroy = "pairs_destroy"
 
     def info(self):
@@ -217,6 +233,9 @@ f64 = torch.float64
 
 
 def build_tree(ctx: Context, x, y, z, m, box, leaf_max: int = 8) -> Tree:
+    """Morton octree of the particles (x, y, z, m: FP64 device tensors) in box
+    (xlo, xhi, ylo, yhi, zlo, zhi), at most leaf_max particles per leaf, with
+    node mass, centre of mass and size (Section 2.2.1)."""
     n = x.numel()
     h = C.c_void_p()
     bp, _keep = _box(box)
@@ -286,6 +305,9 @@ def refine(ctx: Context, tree: Tree, h_particle, sources, params: Params, vor: "
 
 
 def build_voronoi(ctx: Context, gx, gy, gz, box, params: Params | None = None) -> Voronoi:
+    """The Voronoi cells of the generators (gx, gy, gz: FP64 device tensors),
+    clipped to box, with the derived geometry map_exact uses (Section 2.3).
+    Generators outside the box, or two at one position, are rejected."""
     n = gx.numel()
     p = (params or Params()).native()
     h = C.c_void_p()
@@ -442,6 +464,8 @@ def map_batch(device: int, snapshots, params: Params, nworkers: int = 4, tune: b
 
 def voronoi_from_cells(ctx: Context, gen, cell_face_off, face_vert_off, verts, normals, nbr,
                        volume) -> Voronoi:
+    """A Voronoi handle from cells built elsewhere (CSR layout as in
+    Voronoi.get; nbr may be None), with the derived geometry map_exact uses."""
     nc = cell_face_off.numel() - 1
     nf = face_vert_off.numel() - 1
     nfv = verts.numel() // 3
@@ -455,6 +479,8 @@ def voronoi_from_cells(ctx: Context, gen, cell_face_off, face_vert_off, verts, n
 
 
 def find_pairs(ctx: Context, x, y, z, h_, vor: Voronoi) -> Pairs:
+    """Every pair (i, j) whose kernel support reaches the cell:
+    dist(x_i, V_j) < 2 h_i (Section 2.3), sorted by (j, i)."""
     n = x.numel()
     h = C.c_void_p()
     npairs = C.c_int64()
@@ -490,6 +516,9 @@ def find_pairs_cells(ctx: Context, x, y, z, h_, vor: Voronoi, cell_begin: int, c
 
 
 def pairs_from_list(ctx: Context, pair_i, pair_j, np_: int, vor: Voronoi) -> Pairs:
+    """A pair handle from a given list (int32 device tensors, sorted by
+    (pair_j, pair_i)) over np_ particles and vor's cells; an unsorted list or
+    an index out of range is rejected."""
     n = pair_i.numel()
     h = C.c_void_p()
     N.call("pairs_from_list", ctx.handle, n, _ptr(pair_i, torch.int32, n, "pair_i"),
