@@ -181,16 +181,17 @@ __device__ __forceinline__ void shift32(int32_t *buf, int &nb)
     nb -= 32;
 }
 
-// q = sqrt(q2) from an FP32 reciprocal square root and two FP64 Newton steps
-// (about 1 ulp, several FP64 instructions fewer than the FP64 square root);
-// below 1e-30 q is 0 (W then differs from W(0) by about 1e-30).  The
-// conversions to and from float are done on the bits (split.cuh), which
-// gives the same values off the FP64 pipe; q2 < 4 here.
+// q = sqrt(q2) from an FP32 reciprocal square root (within 2^-22 relative)
+// and one FP64 Newton step, which squares that error: within about 1e-13
+// relative, far below the solver's tolerance on h and the 1e-12 to which h is
+// held, at four FP64 instructions fewer than a second step; below 1e-30 q is 0
+// (W then differs from W(0) by about 1e-30).  The conversions to and from
+// float are done on the bits (split.cuh), which gives the same values off the
+// FP64 pipe; q2 < 4 here.
 __device__ __forceinline__ double q_of(double q2)
 {
     if (!(q2 > 1e-30)) return 0.0;
     double r = em::f64_of(rsqrtf(em::f32_of(q2)));
-    r = r * (1.5 - 0.5 * q2 * r * r);
     r = r * (1.5 - 0.5 * q2 * r * r);
     return q2 * r;
 }
