@@ -76,13 +76,25 @@ __global__ void k_prepare_edges(int64_t nfv, const double *__restrict__ gen, con
     double bx = verts[3 * k1] - gx, by = verts[3 * k1 + 1] - gy, bz = verts[3 * k1 + 2] - gz;
     double q = ax * ax + ay * ay + az * az;
     double ex = bx - ax, ey = by - ay, ez = bz - az;
-    double L = sqrt(ex * ex + ey * ey + ez * ez);
+    // L and 1/L from one reciprocal square root: an FP32 seed (on the bits,
+    // split.cuh) and two FP64 Newton steps, within about an ulp, for fewer
+    // FP64 instructions than a square root and a division
+    const double s2 = ex * ex + ey * ey + ez * ez;
+    double L = 0.0;
     EdgeD E;
-    if (L > 0.0) {
-        const double iL = 1.0 / L;
-        ex *= iL;
-        ey *= iL;
-        ez *= iL;
+    if (s2 > 1e-30 && s2 < 1e30) {   // the seed in float's normal range
+        double r = f64_of(rsqrtf(f32_rn(s2)));
+        r = r * (1.5 - 0.5 * s2 * r * r);
+        r = r * (1.5 - 0.5 * s2 * r * r);
+        L = s2 * r;
+        ex *= r;
+        ey *= r;
+        ez *= r;
+    } else if (s2 > 0.0) {   // outside it: the plain operations
+        L = sqrt(s2);
+        ex /= L;
+        ey /= L;
+        ez /= L;
     }
     E.ex = ex;
     E.ey = ey;
