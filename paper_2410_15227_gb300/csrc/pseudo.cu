@@ -303,7 +303,7 @@ __device__ int warp_f_sign(const em::ChunkTree &T, const double *__restrict__ qx
     __syncwarp();
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
-    const double f = h_fact * pow(s * norm, -1.0 / 3.0) - h;
+    const double f = h_fact * rcbrt(s * norm) - h;   // n^(-1/3) as a reciprocal cube root
     return f > 0.0 ? 1 : (f < 0.0 ? -1 : 0);
 }
 
@@ -325,8 +325,13 @@ __global__ void k_h_solve(int64_t npseudo, em::ChunkTree T, const double *__rest
     bool ok = false;
     for (int it = 0; it < max_newton; ++it) {
         Density d = warp_density(T, qx, qy, qz, xa, ya, za, h, margin, buf);
-        double f = h_fact * pow(d.n, -1.0 / 3.0) - h;                      // Eq. 8
-        double fp = -h_fact * d.dn * pow(d.n, -4.0 / 3.0) / 3.0 - 1.0;      // Eq. 9
+        // n^(-1/3) as a reciprocal cube root and n^(-4/3) as its fourth power:
+        // the same values to an ulp or two, for a fraction of the FP64 work of
+        // two general powers (every lane computes them, so each FP64
+        // instruction costs the pipe a full warp)
+        const double c = rcbrt(d.n);
+        double f = h_fact * c - h;                                          // Eq. 8
+        double fp = -h_fact * d.dn * ((c * c) * (c * c)) / 3.0 - 1.0;       // Eq. 9
         double hn = h - f / fp;                                             // Eq. 10
         if (!(hn >= 1e-2 * h0 && hn <= 1e2 * h0)) break;   // left the bracket: Newton failed
         double step = fabs(hn - h) / h0;
