@@ -196,6 +196,23 @@ __device__ __forceinline__ double q_of(double q2)
     return q2 * r;
 }
 
+// 1/x for 2^-100 <= |x| < 2^100 (h and f' here): an FP32 reciprocal (its
+// conversions on the bits, split.cuh) and two FP64 Newton steps, within about
+// an ulp.  The solver's divisions have the same operands on every lane, so
+// each FP64 instruction costs the pipe a full warp; this takes about half the
+// FP64 instructions of a division.
+__device__ __forceinline__ double rcp64(double x)
+{
+    // outside that range (zero, infinities, NaN included) the plain division;
+    // the test reads the exponent's bits, off the FP64 pipe
+    const int e = (int)(((unsigned long long)__double_as_longlong(x) >> 52) & 0x7ff);
+    if (e < 923 || e >= 1123) return 1.0 / x;
+    double r = em::f64_of(__frcp_rn(em::f32_of(x)));
+    r = fma(r, fma(-x, r, 1.0), r);
+    r = fma(r, fma(-x, r, 1.0), r);
+    return r;
+}
+
 // The M4 spline w(q) and g(q) = 3 w(q) + q w'(q), the two sums of the
 // solver, for q < 2 (q2 = q^2).
 __device__ __forceinline__ void m4_wg(double q, double q2, double &w, double &g)
@@ -218,7 +235,7 @@ __device__ Density warp_density(const em::ChunkTree &T, const double *__restrict
 {
     const int lane = threadIdx.x & 31;
     double s = 0.0, ds = 0.0;
-    const double ih = 1.0 / h;
+    const double ih = rcp64(h);
     const double norm = ih * ih * ih * 0.31830988618379067154;   // 1/(pi h^3)
     float R = (float)(2.0 * h) + margin;
     const float xaf = (float)xa, yaf = (float)ya, zaf = (float)za, h2f = (float)(2.0 * h);
@@ -268,7 +285,7 @@ __device__ int warp_f_sign(const em::ChunkTree &T, const double *__restrict__ qx
 {
     const int lane = threadIdx.x & 31;
     double s = 0.0;
-    const double ih = 1.0 / h;
+    const double ih = rcp64(h);
     const double norm = ih * ih * ih * 0.31830988618379067154;   // 1/(pi h^3)
     const double t = h_fact * ih;
     const double thr = t * t * t * (1.0 + 1e-9);
@@ -321,6 +338,7 @@ __global__ void k_h_solve(int64_t npseudo, em::ChunkTree T, const double *__rest
     if (status[a] != -1) return;   // extracted particles keep their own h
     const double xa = px[a], ya = py[a], za = pz[a];
     const double h0 = ph[a];
+    const double ih0 = rcp64(h0);
     double h = h0;
     bool ok = false;
     for (int it = 0; it < max_newton; ++it) {
@@ -332,9 +350,9 @@ __global__ void k_h_solve(int64_t npseudo, em::ChunkTree T, const double *__rest
         const double c = rcbrt(d.n);
         double f = h_fact * c - h;                                          // Eq. 8
         double fp = -h_fact * d.dn * ((c * c) * (c * c)) / 3.0 - 1.0;       // Eq. 9
-        double hn = h - f / fp;                                             // Eq. 10
+        double hn = h - f * rcp64(fp);                                      // Eq. 10
         if (!(hn >= 1e-2 * h0 && hn <= 1e2 * h0)) break;   // left the bracket: Newton failed
-        double step = fabs(hn - h) / h0;
+        double step = fabs(hn - h) * ih0;   // |dh| / h_0
         h = hn;
         if (step < tol) {
             ok = true;
