@@ -294,7 +294,7 @@ __device__ int warp_f_sign(const em::ChunkTree &T, const double *__restrict__ qx
     const float lim = h2f + 1e-5f * (fabsf(xaf) + fabsf(yaf) + fabsf(zaf) + h2f);
     const float lim2 = lim * lim;
     // the sum of w; the walk stops once norm sum w exceeds thr
-    const double ih2 = ih * ih, thrw = thr / norm;
+    const double ih2 = ih * ih, thrw = thr * (3.14159265358979323846 * h * h * h);   // thr / norm
     auto sum_one = [&](int64_t k) {
         const double dx = qx[k] - xa, dy = qy[k] - ya, dz = qz[k] - za;
         const double q2 = (dx * dx + dy * dy + dz * dz) * ih2;
@@ -338,7 +338,7 @@ __global__ void k_h_solve(int64_t npseudo, em::ChunkTree T, const double *__rest
     if (status[a] != -1) return;   // extracted particles keep their own h
     const double xa = px[a], ya = py[a], za = pz[a];
     const double h0 = ph[a];
-    const double ih0 = rcp64(h0);
+    const double ih0 = rcp64(h0), blo = 1e-2 * h0, bhi = 1e2 * h0;
     double h = h0;
     bool ok = false;
     for (int it = 0; it < max_newton; ++it) {
@@ -349,9 +349,9 @@ __global__ void k_h_solve(int64_t npseudo, em::ChunkTree T, const double *__rest
         // instruction costs the pipe a full warp)
         const double c = rcbrt(d.n);
         double f = h_fact * c - h;                                          // Eq. 8
-        double fp = -h_fact * d.dn * ((c * c) * (c * c)) / 3.0 - 1.0;       // Eq. 9
+        double fp = -h_fact * d.dn * ((c * c) * (c * c)) * (1.0 / 3.0) - 1.0;   // Eq. 9 (a product, not a division)
         double hn = h - f * rcp64(fp);                                      // Eq. 10
-        if (!(hn >= 1e-2 * h0 && hn <= 1e2 * h0)) break;   // left the bracket: Newton failed
+        if (!(hn >= blo && hn <= bhi)) break;   // left the bracket [1e-2 h0, 1e2 h0]: Newton failed
         double step = fabs(hn - h) * ih0;   // |dh| / h_0
         h = hn;
         if (step < tol) {
